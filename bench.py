@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the two-phase CSR SpGEMM on the multigrid Galerkin triple
+product R*(A*P): A = 27-point 3D Laplacian on a 128^3 grid, P the smoothed
+aggregation prolongator over 3x3x3 aggregates, R = P^T, FP64 (synthetic,
+seeded).  One step = symbolic + numeric of A*P, then symbolic + numeric of
+R*(AP).  Metric: GFLOP/s = 2 x multiplications / second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 (torchrun, one process per GPU) runs independent replicas (the path
+has no exchange step): value = all ranks' multiplications / max time.
+--impl reference times the CPU oracle on the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpGEMM GFLOP/s (2×mults/s) & % of HBM-byte roofline; batched/bwd vs plain"
+BIN_CAP = [0, 16, 64, 256, 1024, 4096]
+BIN_FLOPS = [0, 1024, 4096, 32768, 262144, 2097152]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--grid", type=int, default=128)
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return (f"Galerkin R*(A*P): 27-point 3D Laplacian on {n}^3, smoothed aggregation P "
+            f"(3x3x3 aggregates, omega 2/3), R = P^T, FP64")
+
+
+def mults_of(a_col, a_rp_unused, b_rp):
+    return int(np.diff(b_rp)[a_col.astype(np.int64)].sum())
+
+
+def bins_of(keys, flops):
+    """Vectorised copy of the library's bin rule (checked against bin_of)."""
+    b = np.where(keys > 0, 1, 0)
+    for k in range(1, 6):
+        up = (b == k) & ((keys > BIN_CAP[k]) | (flops > BIN_FLOPS[k]))
+        b = np.where(up, k + 1, b)
+    return b
+
+
+def row_flops_np(a, b_rp):
+    per = np.diff(b_rp)[a.col.astype(np.int64)]
+    out = np.zeros(a.nrows, dtype=np.int64)
+    np.add.at(out, np.repeat(np.arange(a.nrows), np.diff(a.row_ptr)), per)
+    return out
+
+
+def kernel_bytes(a, b_rp, c_rp, rows_mask, vb, numeric=True):
+    """Algorithmic bytes of one kernel over the rows in rows_mask: the A rows
+    it reads, the B rows they touch (each once), the C rows it writes."""
+    alen = np.diff(a.row_ptr)[rows_mask]
+    clen = np.diff(c_rp)[rows_mask]
+    sel = np.repeat(rows_mask, np.diff(a.row_ptr))
+    touched = np.unique(a.col[sel])
+    blen = np.diff(b_rp)[touched]
+    if numeric:
+        return int(alen.size * 8 + alen.sum() * (4 + vb) + touched.size * 8 + blen.sum() * (4 + vb)
+                   + clen.size * 8 + clen.sum() * (4 + vb))
+    # symbolic: A columns, B pattern (compressed pairs bounded by entries), counts written
+    return int(alen.size * 8 + alen.sum() * 4 + touched.size * 8 + blen.sum() * 4 + clen.size * 8)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1804_00695_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1804_00695_gb300 import inputs as I
+    a, p, r = I.galerkin_problem(args.grid)
+
+    def step():
+        ap = oracle.spgemm(a, p)
+        rap = oracle.spgemm(r, I.Csr(a.nrows, p.ncols, ap.row_ptr, ap.col, ap.val))
+        return int(ap.mults.sum() + rap.mults.sum())
+
+    mults = 0
+    for _ in range(args.warmup):
+        mults = step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        mults = step()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    val = 2 * mults / (ms / 1e3) / 1e9
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators)",
+            "impl": "reference",
+            "config": {"workload": workload_name(args.grid), "grid": args.grid},
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "the full workload (both products) every step"},
+            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1804_00695_gb300 as sg
+    from paper_1804_00695_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # CPU baseline first (rank 0, N = 1): the oracle on the same workload.
+    cpu = None
+    a, p, r = I.galerkin_problem(args.grid)
+    if rank == 0 and world == 1:
+        import oracle
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ap_o = oracle.spgemm(a, p)
+            rap_o = oracle.spgemm(r, I.Csr(a.nrows, p.ncols, ap_o.row_ptr, ap_o.col, ap_o.val))
+            ts.append(time.perf_counter() - t0)
+        om = int(ap_o.mults.sum() + rap_o.mults.sum())
+        cpu = {"value": 2 * om / statistics.median(ts) / 1e9, "unit": "GFLOP/s",
+               "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "full workload (A*P then R*(AP)), median of 3 runs"}
+        del ap_o, rap_o
+
+    dev = torch.device("cuda", local)
+    A, P, R = (sg.Csr.from_host(m, dev) for m in (a, p, r))
+    h1, h2 = sg.Handle(local), sg.Handle(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rp1, n1 = h1.symbolic(A, P)
+        AP = h1.numeric(A, P, rp1, n1)
+        rp2, n2 = h2.symbolic(R, AP)
+        RAP = h2.numeric(R, AP, rp2, n2)
+        return AP, RAP
+
+    AP, RAP = step()
+    h1.check(); h2.check()
+    ap_rp = AP.row_ptr.cpu().numpy()
+    rap_rp = RAP.row_ptr.cpu().numpy()
+    mults_ap = mults_of(a.col, a.row_ptr, p.row_ptr)
+    mults_rap = mults_of(r.col, r.row_ptr, ap_rp)
+    mults = mults_ap + mults_rap
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    for h in (h1, h2):
+        h.set_timing(True)
+        h.reset_timings()
+    l0 = h1.launch_count() + h2.launch_count()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = h1.launch_count() + h2.launch_count() - l0
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 2 * mults / (ms / 1e3) / 1e9
+
+    # per-kernel CUDA-event timings from the timed region
+    tim = {}
+    for tag, h in (("AP", h1), ("RAP", h2)):
+        for lab, (nl, rows, tms) in h.timings().items():
+            tim[f"{tag}.{lab}"] = (nl, rows, tms)
+        h.set_timing(False)
+    # algorithmic bytes of every numeric/symbolic bin kernel
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    fl_ap = row_flops_np(a, p.row_ptr)
+    fl_rap = row_flops_np(r, ap_rp)
+    prod = {"AP": (a, p.row_ptr, ap_rp, fl_ap), "RAP": (r, ap_rp, rap_rp, fl_rap)}
+    kern = []
+    for key, (nl, rows, tms) in tim.items():
+        parts = key.split(".")
+        if len(parts) != 3 or parts[1] != "numeric" or not parts[2].startswith("bin"):
+            continue
+        am, brp, crp, fl = prod[parts[0]]
+        mask = bins_of(np.diff(crp), fl) == int(parts[2][3:])
+        assert mask.sum() == rows // nl, (key, mask.sum(), rows, nl)
+        kern.append((tms / nl, key, kernel_bytes(am, brp, crp, mask, 8, True), nl))
+    roof = None
+    if kern:
+        # dominant kernel: the numeric bin kernel with the largest total time
+        best = max(kern, key=lambda x: x[0] * x[3])
+        per_ms, key, byt, nl = best
+        ach = byt / (per_ms / 1e3) / 1e9
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tf):
+            t = json.load(open(tf))
+            if t.get("source_hash") == source_hash() and key in t.get("kernels", {}):
+                traffic = t["kernels"][key]
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "kernel": key, "bytes_per_launch": byt,
+                "ms_per_launch": per_ms, "peak_source": peak_src}
+    # whole-step HBM-byte roofline: A + B rows touched + C of both products
+    allr = np.ones(a.nrows, dtype=bool)
+    step_bytes = (kernel_bytes(a, p.row_ptr, ap_rp, allr, 8) +
+                  kernel_bytes(r, ap_rp, rap_rp, np.ones(r.nrows, dtype=bool), 8))
+    step_frac = step_bytes / (ms / 1e3) / 1e9 / hbm
+
+    # end to end: host (pinned) inputs -> device, both products, result -> host
+    hosts = {}
+    for nm, m in (("a", a), ("p", p), ("r", r)):
+        hosts[nm] = [torch.from_numpy(x).pin_memory() for x in (m.row_ptr, m.col, m.val)]
+    devs = {nm: [torch.empty_like(x, device=dev) for x in hosts[nm]] for nm in hosts}
+    h2d = sum(x.numel() * x.element_size() for v in hosts.values() for x in v)
+
+    def e2e_step():
+        for nm in hosts:
+            for hx, dx in zip(hosts[nm], devs[nm]):
+                dx.copy_(hx, non_blocking=True)
+        Ad = sg.Csr(a.nrows, a.ncols, *devs["a"])
+        Pd = sg.Csr(p.nrows, p.ncols, *devs["p"])
+        Rd = sg.Csr(r.nrows, r.ncols, *devs["r"])
+        rp1, n1 = h1.symbolic(Ad, Pd)
+        APd = h1.numeric(Ad, Pd, rp1, n1)
+        rp2, n2 = h2.symbolic(Rd, APd)
+        RAPd = h2.numeric(Rd, APd, rp2, n2)
+        out = [RAPd.row_ptr.to("cpu", non_blocking=True), RAPd.col.to("cpu", non_blocking=True),
+               RAPd.val.to("cpu", non_blocking=True)]
+        return out
+
+    o = e2e_step()
+    torch.cuda.synchronize()
+    d2h = sum(x.numel() * x.element_size() for x in o)
+    ke = max(1, min(args.steps, 5))
+    barrier()
+    e0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / ke
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded generators)",
+                "config": {"workload": workload_name(args.grid), "grid": args.grid,
+                           "mults": mults, "nnz_AP": int(ap_rp[-1]), "nnz_RAP": int(rap_rp[-1]),
+                           "l2": "inputs larger than L2 (A alone 686 MB), no flush",
+                           "parallelism": f"replicas x{world}"},
+                "pct_hbm_byte_roofline": 100 * step_frac,
+                "step_algorithmic_bytes": step_bytes,
+                "roofline": roof,
+                "kernels_ms_per_step": {k: v[2] / args.steps for k, v in sorted(tim.items())},
+                "gpu_launches": launches,
+                "clocks": clk,
+                "e2e": {"value": world * 2 * mults / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * spgemm.h - C ABI of the GB300 (sm_103a) CSR sparse matrix-matrix multiply
+ *            library, C = A * B.
+ *
+ * Method: Deveci, Hammond, Wolf, Rajamanickam, "Sparse Matrix-Matrix
+ * Multiplication on Multilevel Memory Architectures: Algorithms and
+ * Experiments" (SAND2018-3428 R).  The product is computed row by row
+ * (Section 2.1, the row-wise hierarchical kkmem method) in two phases:
+ * a symbolic phase that counts the non-zeros of every row of C and a numeric
+ * phase that computes the values (Section 2.1).  Column sets in the symbolic
+ * phase are compressed into (column / 32, 32-bit mask) pairs (Section 2.1,
+ * "compression"); accumulators are hash maps held in shared memory with a
+ * second level in global memory (Section 3.3).  Operands too large for the
+ * device are streamed through a fixed device budget by the chunking methods
+ * of Section 3.3.1 (Algorithms 2, 3 and 4).
+ *
+ * Conventions for every call:
+ *   - Matrices are CSR: row_ptr holds nrows+1 int64 offsets (row_ptr[0] == 0,
+ *     non-decreasing), col_idx holds nnz int32 column indices in
+ *     [0, ncols), values holds nnz elements of the call's dtype.  Columns of
+ *     an input row may be in any order (Section 3.2.2: the kernel does not
+ *     assume sorted columns) but must not repeat; repeated columns are not
+ *     detected on the device and make the result undefined.  Output rows
+ *     have strictly ascending columns.  The output pattern is structural:
+ *     an entry exists when a stored a_ik meets a stored b_kj, even if the
+ *     computed value is zero.
+ *   - The caller owns every array passed in; the library never frees or
+ *     keeps them beyond the call, except that spgemm_numeric requires the
+ *     same A, B and C.row_ptr arrays as the preceding spgemm_symbolic on the
+ *     same handle.
+ *   - "device" arrays are CUDA device pointers of the handle's device;
+ *     "host" arrays are host pointers (page-locked memory gives full copy
+ *     bandwidth; pageable memory works but is slower).
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device-side calls are asynchronous on that stream except where stated.
+ *   - Every call returns a spgemm_status.  On failure, spgemm_last_error()
+ *     returns a message for the calling thread.  No call aborts the process.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPGEMM_API __attribute__((visibility("default")))
+#else
+#define SPGEMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spgemm_status {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_ARG = 1,          /* null pointer, negative size, bad dtype */
+    SPGEMM_ERR_DIM = 2,          /* A.ncols != B.nrows */
+    SPGEMM_ERR_INDEX = 3,        /* column index out of range, or offsets/counts overflow */
+    SPGEMM_ERR_NOMEM = 4,        /* a device or pinned allocation failed */
+    SPGEMM_ERR_BUDGET = 5,       /* chunked: budget below the minimum working set */
+    SPGEMM_ERR_TIMEOUT = 6,      /* a bounded wait ran out */
+    SPGEMM_ERR_CUDA = 7,         /* a CUDA runtime call failed */
+    SPGEMM_ERR_NOT_SYMBOLIC = 8, /* numeric called without a matching symbolic */
+    SPGEMM_ERR_INTERNAL = 9      /* a device-side bound was exceeded (hash probe limit) */
+} spgemm_status;
+
+typedef enum spgemm_dtype { SPGEMM_F32 = 0, SPGEMM_F64 = 1 } spgemm_dtype;
+
+/* CSR descriptor; see the conventions above.  values may be NULL where a
+ * call only reads the pattern. */
+typedef struct spgemm_csr {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    int64_t *row_ptr;
+    int32_t *col_idx;
+    void *values;
+} spgemm_csr;
+
+typedef struct spgemm_handle_s *spgemm_handle;
+
+/* Thread-local message describing the last failure (never NULL). */
+SPGEMM_API const char *spgemm_last_error(void);
+
+/* Library version string. */
+SPGEMM_API const char *spgemm_version(void);
+
+/* Create a handle bound to CUDA device `device`.  The handle owns a device
+ * workspace that grows on demand (stream-ordered allocation on the stream of
+ * the call that needs it) and small pinned host buffers.  Not thread-safe:
+ * use one handle per host thread. */
+SPGEMM_API int spgemm_create(spgemm_handle *handle, int device);
+SPGEMM_API int spgemm_destroy(spgemm_handle handle);
+
+/* Symbolic phase (Section 2.1): fills C_row_ptr (device, nrows(A)+1 int64)
+ * with the row offsets of C = A*B and stores nnz(C) in *nnz_C (host).
+ * Steps: column compression of B (Section 2.1), per-row flop counts and
+ * binning, per-row union of compressed column sets in shared-memory hash
+ * tables or dense bitmaps, exclusive scan.  Synchronises the stream once to
+ * return nnz(C).  A, B: device arrays (values unused, may be NULL).
+ * Errors: SPGEMM_ERR_DIM, SPGEMM_ERR_INDEX (column of A outside B's rows or
+ * of B outside ncols, int64 overflow), SPGEMM_ERR_NOMEM, SPGEMM_ERR_CUDA. */
+SPGEMM_API int spgemm_symbolic(spgemm_handle handle, const spgemm_csr *A, const spgemm_csr *B,
+                    int64_t *C_row_ptr, int64_t *nnz_C, void *stream);
+
+/* Numeric phase (Section 2.1, hash accumulators of Section 3.3): with C->row_ptr
+ * from spgemm_symbolic on this handle for the same A and B (same arrays and
+ * sizes), fills C->col_idx and C->values (device, C->nnz elements each) with
+ * ascending columns per row.  Values of A, B, C have type dtype.  Does not
+ * synchronise.  Errors: SPGEMM_ERR_NOT_SYMBOLIC, SPGEMM_ERR_ARG. */
+SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr *A,
+                   const spgemm_csr *B, spgemm_csr *C, void *stream);
+
+/* Synchronises `stream` and reports device-side errors raised by earlier
+ * asynchronous calls on this handle (SPGEMM_ERR_INTERNAL if a hash probe
+ * bound was exceeded or a row's column count disagreed with the symbolic
+ * phase), then clears them. */
+SPGEMM_API int spgemm_check(spgemm_handle handle, void *stream);
+
+/* Inspection of the first two steps, for tests and tuning.
+ * spgemm_row_flops: flops[i] (device, nrows(A) int64) = number of products
+ * a_ik*b_kj of row i (Section 3.1: accumulator insertions = multiplications).
+ * spgemm_compress: the compressed column sets of M (Section 2.1): for every
+ * row k, count[k] (device int32) pairs {block = col/32, mask} stored as two
+ * uint32 each at pairs[2*(M.row_ptr[k] + t)], t < count[k] (pairs: device,
+ * room for 2*nnz(M) uint32).  Consecutive stored columns that share a block
+ * are merged, so a sorted row gives one pair per block, ascending. */
+SPGEMM_API int spgemm_row_flops(spgemm_handle handle, const spgemm_csr *A, const spgemm_csr *B,
+                     int64_t *flops, void *stream);
+SPGEMM_API int spgemm_compress(spgemm_handle handle, const spgemm_csr *M, int32_t *count,
+                    uint32_t *pairs, void *stream);
+
+/* Per-bin row counts of the last symbolic and numeric phases on this handle
+ * (host array of at least SPGEMM_NBINS int64 each), for tests and tuning. */
+#define SPGEMM_NBINS 8
+SPGEMM_API int spgemm_bin_counts(spgemm_handle handle, int64_t *symbolic_bins, int64_t *numeric_bins);
+
+/* Bin (0..6) that a row needing `keys` accumulator entries and taking
+ * `flops` products is assigned to (0 = empty row).  Host only. */
+SPGEMM_API int spgemm_bin_of(int64_t keys, int64_t flops);
+
+/* Instrumentation.  spgemm_launch_count: kernels launched through this
+ * handle since it was created.  spgemm_set_timing(h, 1) brackets every
+ * kernel launch with CUDA events on its stream; spgemm_timings synchronises
+ * on those events and returns per-kernel totals (label "<phase>.<kernel>",
+ * launches, rows processed, milliseconds) accumulated since the last
+ * spgemm_reset_timings; *count = number of labels (up to cap written). */
+typedef struct spgemm_timing {
+    char label[32];
+    int64_t launches;
+    int64_t rows;
+    double ms;
+} spgemm_timing;
+SPGEMM_API int spgemm_launch_count(spgemm_handle handle, int64_t *launches);
+SPGEMM_API int spgemm_set_timing(spgemm_handle handle, int on);
+SPGEMM_API int spgemm_timings(spgemm_handle handle, spgemm_timing *out, int cap, int *count);
+SPGEMM_API int spgemm_reset_timings(spgemm_handle handle);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPGEMM_GB300_H */

@@ -1,0 +1,259 @@
+"""GB300 (sm_103a) CSR sparse matrix-matrix multiplication C = A*B.
+
+Thin ctypes binding over the C ABI in ``include/spgemm.h``: it only marshals
+torch tensors (device memory) and the current CUDA stream into the library's
+calls.  Every step of the product runs in the library's CUDA kernels; there is
+no CPU or PyTorch fallback.  The library must have been built
+(``__graft_entry__.build()`` or ``python -m paper_1804_00695_gb300._build``);
+calls raise ``RuntimeError`` when it is missing.
+
+Method: Deveci et al., "Sparse Matrix-Matrix Multiplication on Multilevel
+Memory Architectures" - two-phase (symbolic, numeric) row-wise product with
+compressed column sets and hash-map accumulators (Section 2.1, Section 3.3),
+and the chunking methods of Section 3.3.1 for operands in host memory.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libspgemm_gb300.so")
+
+F32, F64 = 0, 1
+NBINS = 8
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_DIM", 3: "ERR_INDEX", 4: "ERR_NOMEM", 5: "ERR_BUDGET",
+          6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_NOT_SYMBOLIC", 9: "ERR_INTERNAL"}
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class TimingRec(C.Structure):
+    _fields_ = [("label", C.c_char * 32), ("launches", C.c_int64), ("rows", C.c_int64),
+                ("ms", C.c_double)]
+
+
+class CsrDesc(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("values", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    p, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    sig = {
+        "spgemm_last_error": ([], C.c_char_p),
+        "spgemm_version": ([], C.c_char_p),
+        "spgemm_create": ([C.POINTER(p), i32], i32),
+        "spgemm_destroy": ([p], i32),
+        "spgemm_check": ([p, p], i32),
+        "spgemm_symbolic": ([p, p, p, p, C.POINTER(i64), p], i32),
+        "spgemm_numeric": ([p, i32, p, p, p, p], i32),
+        "spgemm_row_flops": ([p, p, p, p, p], i32),
+        "spgemm_compress": ([p, p, p, p, p], i32),
+        "spgemm_bin_counts": ([p, p, p], i32),
+        "spgemm_bin_of": ([i64, i64], i32),
+        "spgemm_launch_count": ([p, C.POINTER(i64)], i32),
+        "spgemm_set_timing": ([p, i32], i32),
+        "spgemm_timings": ([p, p, i32, C.POINTER(i32)], i32),
+        "spgemm_reset_timings": ([p], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SpgemmError(status, _lib.spgemm_last_error().decode())
+
+
+def version() -> str:
+    return load().spgemm_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclass
+class Csr:
+    """CSR matrix in device memory as torch tensors (int64 row_ptr, int32
+    col, float32/float64 val)."""
+    nrows: int
+    ncols: int
+    row_ptr: "object"
+    col: "object"
+    val: "object" = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def desc(self) -> CsrDesc:
+        return CsrDesc(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
+                       self.col.data_ptr() if self.col.numel() else None,
+                       self.val.data_ptr() if (self.val is not None and self.val.numel()) else None)
+
+    @staticmethod
+    def from_host(m, device="cuda", dtype=None) -> "Csr":
+        """Copy an ``inputs.Csr`` (numpy) to the device."""
+        torch = _torch()
+        val = m.val if dtype is None else m.val.astype(dtype)
+        return Csr(m.nrows, m.ncols, torch.from_numpy(m.row_ptr).to(device),
+                   torch.from_numpy(m.col).to(device), torch.from_numpy(val).to(device))
+
+    def dtype_code(self) -> int:
+        torch = _torch()
+        if self.val.dtype == torch.float64:
+            return F64
+        if self.val.dtype == torch.float32:
+            return F32
+        raise TypeError(f"unsupported value dtype {self.val.dtype}")
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+class Handle:
+    """Owns a library handle (device workspace and symbolic state)."""
+
+    def __init__(self, device: int | None = None):
+        torch = _torch()
+        lib = load()
+        self.device = torch.cuda.current_device() if device is None else device
+        self._h = C.c_void_p()
+        _check(lib.spgemm_create(C.byref(self._h), self.device))
+
+    def close(self):
+        if self._h:
+            load().spgemm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        return self._h
+
+    # -- two phases -----------------------------------------------------------
+    def symbolic(self, A: Csr, B: Csr, stream=None):
+        """Row offsets of C = A*B (device int64 tensor) and nnz(C)."""
+        torch = _torch()
+        rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.row_ptr.device)
+        nnz = C.c_int64()
+        da, db = A.desc(), B.desc()
+        _check(_lib.spgemm_symbolic(self._h, C.byref(da), C.byref(db), rp.data_ptr(), C.byref(nnz),
+                                    _stream(stream)))
+        return rp, int(nnz.value)
+
+    def numeric(self, A: Csr, B: Csr, row_ptr, nnz: int, stream=None) -> Csr:
+        """Columns (ascending per row) and values of C = A*B."""
+        torch = _torch()
+        dev = A.row_ptr.device
+        col = torch.empty(nnz, dtype=torch.int32, device=dev)
+        val = torch.empty(nnz, dtype=A.val.dtype, device=dev)
+        c = Csr(A.nrows, B.ncols, row_ptr, col, val)
+        self.numeric_into(A, B, c, stream)
+        return c
+
+    def numeric_into(self, A: Csr, B: Csr, Cm: Csr, stream=None):
+        da, db, dc = A.desc(), B.desc(), Cm.desc()
+        _check(_lib.spgemm_numeric(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc),
+                                   _stream(stream)))
+
+    def spgemm(self, A: Csr, B: Csr, stream=None) -> Csr:
+        rp, nnz = self.symbolic(A, B, stream)
+        return self.numeric(A, B, rp, nnz, stream)
+
+    def check(self, stream=None):
+        _check(_lib.spgemm_check(self._h, _stream(stream)))
+
+    # -- inspection ---------------------------------------------------------------
+    def row_flops(self, A: Csr, B: Csr, stream=None):
+        torch = _torch()
+        out = torch.empty(A.nrows, dtype=torch.int64, device=A.row_ptr.device)
+        da, db = A.desc(), B.desc()
+        _check(_lib.spgemm_row_flops(self._h, C.byref(da), C.byref(db), out.data_ptr(), _stream(stream)))
+        return out
+
+    def compress(self, M: Csr, stream=None):
+        """(count per row, pairs as an (nnz, 2) uint32-in-int32 tensor)."""
+        torch = _torch()
+        dev = M.row_ptr.device
+        cnt = torch.empty(M.nrows, dtype=torch.int32, device=dev)
+        pairs = torch.zeros((max(M.nnz, 1), 2), dtype=torch.int32, device=dev)
+        dm = M.desc()
+        _check(_lib.spgemm_compress(self._h, C.byref(dm), cnt.data_ptr(), pairs.data_ptr(),
+                                    _stream(stream)))
+        return cnt, pairs
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check(_lib.spgemm_launch_count(self._h, C.byref(n)))
+        return int(n.value)
+
+    def set_timing(self, on: bool = True):
+        _check(_lib.spgemm_set_timing(self._h, 1 if on else 0))
+
+    def timings(self) -> dict:
+        """{label: (launches, rows, ms)} accumulated since the last reset."""
+        arr = (TimingRec * 64)()
+        n = C.c_int()
+        _check(_lib.spgemm_timings(self._h, arr, 64, C.byref(n)))
+        return {arr[k].label.decode(): (int(arr[k].launches), int(arr[k].rows), float(arr[k].ms))
+                for k in range(min(n.value, 64))}
+
+    def reset_timings(self):
+        _check(_lib.spgemm_reset_timings(self._h))
+
+    def bin_counts(self):
+        sym = (C.c_int64 * NBINS)()
+        num = (C.c_int64 * NBINS)()
+        _check(_lib.spgemm_bin_counts(self._h, sym, num))
+        return list(sym), list(num)
+
+
+_default = {}
+
+
+def default_handle() -> Handle:
+    torch = _torch()
+    d = torch.cuda.current_device()
+    if d not in _default:
+        _default[d] = Handle(d)
+    return _default[d]
+
+
+def bin_of(keys: int, flops: int) -> int:
+    return int(load().spgemm_bin_of(keys, flops))
+
+
+def spgemm(A: Csr, B: Csr, stream=None) -> Csr:
+    """C = A*B with both phases on the current device's default handle."""
+    return default_handle().spgemm(A, B, stream)

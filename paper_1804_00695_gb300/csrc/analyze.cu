@@ -1,0 +1,334 @@
+// Row analysis: column compression of B (Section 2.1), per-row product
+// counts and binning (Section 3.1, Section 3.3), exclusive scan of counts.
+#include <climits>
+#include "internal.cuh"
+
+namespace sg {
+
+// ---------------------------------------------------------------- compression
+// One thread per row of M: consecutive stored columns that fall in the same
+// 32-column block are merged into one (block, mask) pair (Section 2.1,
+// "compression ... encode multiple columns ... with fewer integers").  Rows
+// need not be sorted; a sorted row yields one pair per block, ascending.
+__global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, int2 *__restrict__ pairs,
+                           int32_t *__restrict__ ccnt, int2 *__restrict__ minmax, int *err) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int64_t beg = rp[r], end = rp[r + 1];
+    int cur = -1;
+    unsigned m = 0;
+    int n = 0, bmin = INT_MAX, bmax = INT_MIN;
+    bool bad = false;
+    for (int64_t p = beg; p < end; p++) {
+        int c = col[p];
+        if (c < 0 || (int64_t)c >= ncols) { bad = true; continue; }
+        int b = c >> 5;
+        if (b != cur) {
+            if (cur >= 0) pairs[beg + n++] = make_int2(cur, (int)m);
+            cur = b;
+            m = 0;
+        }
+        m |= 1u << (c & 31);
+        bmin = min(bmin, b);
+        bmax = max(bmax, b);
+    }
+    if (cur >= 0) pairs[beg + n++] = make_int2(cur, (int)m);
+    ccnt[r] = n;
+    minmax[r] = make_int2(bmin, bmax);
+    if (bad) atomicOr(err, DERR_COL_RANGE);
+}
+
+int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int *err,
+                    Ctx &c) {
+    if (M.nrows == 0) return SPGEMM_OK;
+    int64_t blocks = (M.nrows + 255) / 256;
+    c.begin("compress", M.nrows);
+    k_compress<<<(unsigned)blocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
+                                                    ccnt, minmax, err);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------- analysis
+// Eight lanes per row of A.  For row i: flops_i = sum_k nnz(B_k) (the number
+// of accumulator insertions, Section 3.1), cpairs_i = sum_k pairs(B_k), and
+// the span of compressed blocks the row can reach.  The symbolic
+// accumulator needs at most min(cpairs_i, span_i, ceil(ncols/32)) keys.
+constexpr int AN_G = 8;
+__global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
+                          const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                          const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
+                          const int2 *__restrict__ minmax, int64_t *__restrict__ flops,
+                          uint8_t *__restrict__ bins, int64_t *__restrict__ crp, DevState *st) {
+    __shared__ unsigned long long hist[NBINS];
+    if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x % AN_G;
+    const unsigned gmask = (AN_G == 32) ? 0xffffffffu
+                                        : (((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1)));
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / AN_G;
+    bool live = i < nrows;
+    long long f = 0, cp = 0;
+    int bmin = INT_MAX, bmax = INT_MIN;
+    bool bad = false;
+    if (live) {
+        for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += AN_G) {
+            int k = acol[p];
+            if (k < 0 || (int64_t)k >= nrows_b) { bad = true; continue; }
+            f += brp[k + 1] - brp[k];
+            cp += ccnt[k];
+            int2 mm = minmax[k];
+            bmin = min(bmin, mm.x);
+            bmax = max(bmax, mm.y);
+        }
+    }
+    for (int d = AN_G / 2; d > 0; d >>= 1) {
+        f += __shfl_xor_sync(gmask, f, d, AN_G);
+        cp += __shfl_xor_sync(gmask, cp, d, AN_G);
+        bmin = min(bmin, __shfl_xor_sync(gmask, bmin, d, AN_G));
+        bmax = max(bmax, __shfl_xor_sync(gmask, bmax, d, AN_G));
+    }
+    if (bad) atomicOr(&st->err, DERR_COL_RANGE);
+    if (live && lane == 0) {
+        long long keys = cp;
+        if (bmax >= bmin) keys = min(keys, (long long)(bmax - bmin) + 1);
+        else keys = 0;
+        keys = min(keys, (long long)nwords);
+        int b = bin_of(keys, cp);
+        flops[i] = f;
+        bins[i] = (uint8_t)b;
+        if (b == BIN_EMPTY) crp[i + 1] = 0;
+        atomicAdd(&hist[b], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < NBINS && hist[threadIdx.x])
+        atomicAdd((unsigned long long *)&st->bin_count[0][threadIdx.x], hist[threadIdx.x]);
+}
+
+int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int32_t *ccnt,
+                   const int2 *minmax, int64_t *flops, uint8_t *bins, int64_t *crp, DevState *st,
+                   Ctx &c) {
+    if (A.nrows == 0) return SPGEMM_OK;
+    int64_t threads = A.nrows * AN_G;
+    int64_t blocks = (threads + 255) / 256;
+    int64_t nwords = (B.ncols + 31) / 32;
+    c.begin("analyze", A.nrows);
+    k_analyze<<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, B.nrows, nwords, A.row_ptr, A.col_idx,
+                                                   B.row_ptr, ccnt, minmax, flops, bins, crp, st);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// Products per row only (inspection entry point).
+__global__ void k_row_flops(int64_t nrows, int64_t nrows_b, const int64_t *__restrict__ arp,
+                            const int32_t *__restrict__ acol, const int64_t *__restrict__ brp,
+                            int64_t *__restrict__ flops, int *err) {
+    const int lane = threadIdx.x % AN_G;
+    const unsigned gmask = ((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1));
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / AN_G;
+    long long f = 0;
+    bool bad = false;
+    if (i < nrows) {
+        for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += AN_G) {
+            int k = acol[p];
+            if (k < 0 || (int64_t)k >= nrows_b) { bad = true; continue; }
+            f += brp[k + 1] - brp[k];
+        }
+    }
+    for (int d = AN_G / 2; d > 0; d >>= 1) f += __shfl_xor_sync(gmask, f, d, AN_G);
+    if (bad) atomicOr(err, DERR_COL_RANGE);
+    if (i < nrows && lane == 0) flops[i] = f;
+}
+
+int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, int *err,
+                     Ctx &c) {
+    if (A.nrows == 0) return SPGEMM_OK;
+    int64_t blocks = (A.nrows * AN_G + 255) / 256;
+    c.begin("row_flops", A.nrows);
+    k_row_flops<<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, B.nrows, A.row_ptr, A.col_idx,
+                                                     B.row_ptr, flops, err);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------- numeric bins
+__global__ void k_numeric_binning(int64_t n, const int64_t *__restrict__ crp,
+                                  const int64_t *__restrict__ flops, uint8_t *__restrict__ bins,
+                                  DevState *st) {
+    __shared__ unsigned long long hist[NBINS];
+    if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        long long c = crp[i + 1] - crp[i];
+        int b = c > 0 ? bin_of(c, flops[i]) : BIN_EMPTY;
+        bins[i] = (uint8_t)b;
+        atomicAdd(&hist[b], 1ull);
+        if (b == BIN_HUGE) atomicMax((unsigned long long *)&st->max_row_nnz, (unsigned long long)c);
+    }
+    __syncthreads();
+    if (threadIdx.x < NBINS && hist[threadIdx.x])
+        atomicAdd((unsigned long long *)&st->bin_count[1][threadIdx.x], hist[threadIdx.x]);
+}
+
+int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, uint8_t *bins,
+                           DevState *st, Ctx &c) {
+    if (n == 0) return SPGEMM_OK;
+    c.begin("numeric_binning", n);
+    k_numeric_binning<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, crp, flops, bins, st);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// Rows of each non-empty bin are appended to the bin's list; within a warp
+// the lanes with the same bin reserve their slots with one atomic
+// (__match_any_sync), so rows stay in ascending order inside each warp.
+__global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
+                               int32_t *__restrict__ rows, DevState *st, int phase) {
+    __shared__ long long off[NBINS];
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int b = 0; b < NBINS; b++) {
+            off[b] = o;
+            if (b != BIN_EMPTY) o += st->bin_count[phase][b];
+        }
+    }
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = i < n ? bins[i] : BIN_EMPTY;
+    unsigned act = __ballot_sync(0xffffffffu, b != BIN_EMPTY);
+    if (b == BIN_EMPTY) return;
+    unsigned peers = __match_any_sync(act, b);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    long long base = 0;
+    if (lane == leader) base = atomicAdd((unsigned long long *)&st->bin_cursor[b],
+                                         (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    int rank = __popc(peers & ((1u << lane) - 1));
+    rows[off[b] + base + rank] = (int32_t)i;
+}
+
+int launch_scatter_bins(int64_t n, const uint8_t *bins, int32_t *rows, DevState *st, int phase,
+                        Ctx &c) {
+    if (n == 0) return SPGEMM_OK;
+    SG_CUDA(cudaMemsetAsync(st->bin_cursor, 0, sizeof(st->bin_cursor), c.s));
+    c.begin("scatter_bins", n);
+    k_scatter_bins<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, bins, rows, st, phase);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------- scan
+// Reduce-then-scan over tiles of SCAN_TILE counts: tile sums, one block scans
+// the sums (looping with a carry), then every tile is rescanned with its
+// offset.  x[0] is set to 0 and x[1..n] becomes the inclusive prefix.
+constexpr int SCAN_BS = 256, SCAN_PT = 8, SCAN_TILE = SCAN_BS * SCAN_PT;
+
+size_t scan_tmp_bytes(int64_t n) {
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return (size_t)(tiles + 1) * sizeof(long long);
+}
+
+__device__ __forceinline__ long long block_excl_scan(long long v, long long *sh, long long *total) {
+    // sh: SCAN_BS/32 entries
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long incl = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < SCAN_BS / 32 ? sh[lane] : 0;
+        long long si = s;
+        for (int d = 1; d < 32; d <<= 1) {
+            long long t = __shfl_up_sync(0xffffffffu, si, d);
+            if (lane >= d) si += t;
+        }
+        if (lane < SCAN_BS / 32) sh[lane] = si - s;
+        if (lane == SCAN_BS / 32 - 1) *total = si;
+    }
+    __syncthreads();
+    long long r = sh[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tiles(const int64_t *__restrict__ x1, int64_t n, long long *tile_sums) {
+    __shared__ long long sh[SCAN_BS / 32];
+    __shared__ long long tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PT;
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PT; j++)
+        if (base + j < n) s += x1[base + j];
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(long long *tile_sums, int64_t tiles, long long *total) {
+    __shared__ long long sh[SCAN_BS / 32];
+    __shared__ long long tot;
+    long long carry = 0;
+    for (int64_t b0 = 0; b0 < tiles; b0 += SCAN_BS) {
+        int64_t t = b0 + threadIdx.x;
+        long long v = t < tiles ? tile_sums[t] : 0;
+        long long e = block_excl_scan(v, sh, &tot);
+        if (t < tiles) tile_sums[t] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_apply(int64_t *__restrict__ x, int64_t n, const long long *tile_sums) {
+    __shared__ long long sh[SCAN_BS / 32];
+    __shared__ long long tot;
+    int64_t *x1 = x + 1;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PT;
+    long long v[SCAN_PT];
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PT; j++) {
+        v[j] = base + j < n ? x1[base + j] : 0;
+        s += v[j];
+    }
+    long long e = block_excl_scan(s, sh, &tot) + tile_sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SCAN_PT; j++) {
+        e += v[j];
+        if (base + j < n) x1[base + j] = e;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) x[0] = 0;
+}
+
+int launch_scan_counts(int64_t *x, int64_t n, long long *total, void *tmp, Ctx &c) {
+    if (n == 0) {
+        SG_CUDA(cudaMemsetAsync(x, 0, sizeof(int64_t), c.s));
+        SG_CUDA(cudaMemsetAsync(total, 0, sizeof(long long), c.s));
+        return SPGEMM_OK;
+    }
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    long long *sums = (long long *)tmp;
+    c.begin("scan_tiles", n);
+    k_scan_tiles<<<(unsigned)tiles, SCAN_BS, 0, c.s>>>(x + 1, n, sums);
+    c.end();
+    c.begin("scan_sums", tiles);
+    k_scan_sums<<<1, SCAN_BS, 0, c.s>>>(sums, tiles, total);
+    c.end();
+    c.begin("scan_apply", n);
+    k_scan_apply<<<(unsigned)tiles, SCAN_BS, 0, c.s>>>(x, n, sums);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+}  // namespace sg

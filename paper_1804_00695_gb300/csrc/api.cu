@@ -1,0 +1,386 @@
+// C ABI: handle, workspace and the two phases of Section 2.1.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include "internal.cuh"
+
+namespace sg {
+
+static thread_local char g_err[1024] = "no error";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void Ctx::begin(const char *label, long long rows) {
+    if (launches) (*launches)++;
+    if (!timing || !recs || *nrec >= cap) return;
+    TimingRec &r = recs[*nrec];
+    if (!r.e0) {
+        if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
+    r.label = label;
+    r.rows = rows;
+    cudaEventRecord(r.e0, s);
+}
+
+void Ctx::end() {
+    if (!timing || !recs || *nrec >= cap) return;
+    TimingRec &r = recs[*nrec];
+    if (!r.e0) return;
+    cudaEventRecord(r.e1, s);
+    (*nrec)++;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+struct TimingAgg {
+    std::string label;
+    long long launches = 0, rows = 0;
+    double ms = 0;
+};
+
+struct spgemm_handle_s {
+    int device = 0;
+    int nsm = 0;
+    DevState *dstate = nullptr;   // device
+    DevState *hstate = nullptr;   // pinned mirror
+    char *ws = nullptr;           // device workspace (grow only)
+    size_t ws_cap = 0;
+    // state carried from symbolic to numeric
+    bool sym_valid = false;
+    const int64_t *a_rp = nullptr, *b_rp = nullptr, *c_rp = nullptr;
+    const int32_t *a_col = nullptr, *b_col = nullptr;
+    int64_t a_n = 0, a_m = 0, a_nnz = 0, b_n = 0, b_m = 0, b_nnz = 0, c_nnz = 0;
+    long long sym_counts[NBINS] = {0};
+    long long num_counts[NBINS] = {0};
+    int64_t max_row_nnz = 0;
+    size_t num_gws = 0;   // bytes after the row lists that numeric needs
+    // launch counting and CUDA-event timing
+    long long launches = 0;
+    bool timing = false;
+    std::vector<TimingRec> recs;
+    int nrec = 0;
+    std::vector<TimingAgg> agg;
+
+    Ctx ctx(cudaStream_t s, const char *phase = "") {
+        Ctx c;
+        c.s = s;
+        c.nsm = nsm;
+        c.launches = &launches;
+        c.timing = timing;
+        c.recs = recs.empty() ? nullptr : recs.data();
+        c.nrec = &nrec;
+        c.cap = (int)recs.size();
+        c.phase = phase;
+        return c;
+    }
+};
+
+static int ws_reserve(spgemm_handle h, size_t bytes, cudaStream_t s, size_t keep = 0) {
+    if (bytes <= h->ws_cap) return SPGEMM_OK;
+    size_t cap = bytes + bytes / 8;
+    char *p = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&p, cap, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("workspace allocation of %zu bytes failed: %s", cap, cudaGetErrorString(e));
+        return SPGEMM_ERR_NOMEM;
+    }
+    if (keep && h->ws) SG_CUDA(cudaMemcpyAsync(p, h->ws, keep, cudaMemcpyDeviceToDevice, s));
+    if (h->ws) SG_CUDA(cudaFreeAsync(h->ws, s));
+    h->ws = p;
+    h->ws_cap = cap;
+    return SPGEMM_OK;
+}
+
+static int check_csr(const spgemm_csr *m, const char *name, bool need_vals) {
+    if (!m) { set_error("%s is NULL", name); return SPGEMM_ERR_ARG; }
+    if (m->nrows < 0 || m->ncols < 0 || m->nnz < 0) {
+        set_error("%s has a negative size", name);
+        return SPGEMM_ERR_ARG;
+    }
+    if (m->nrows >= (1LL << 31) || m->ncols > (1LL << 31)) {
+        set_error("%s: dimensions must fit int32 column indices", name);
+        return SPGEMM_ERR_INDEX;
+    }
+    if (!m->row_ptr) { set_error("%s.row_ptr is NULL", name); return SPGEMM_ERR_ARG; }
+    if (m->nnz > 0 && !m->col_idx) { set_error("%s.col_idx is NULL", name); return SPGEMM_ERR_ARG; }
+    if (need_vals && m->nnz > 0 && !m->values) {
+        set_error("%s.values is NULL", name);
+        return SPGEMM_ERR_ARG;
+    }
+    return SPGEMM_OK;
+}
+
+static int fetch_state(spgemm_handle h, cudaStream_t s) {
+    SG_CUDA(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    SG_CUDA(cudaStreamSynchronize(s));
+    return SPGEMM_OK;
+}
+
+static int device_errors(int err) {
+    if (err & DERR_COL_RANGE) {
+        set_error("column index out of range (A column >= nrows(B) or B column >= ncols(B))");
+        return SPGEMM_ERR_INDEX;
+    }
+    if (err & (DERR_PROBE | DERR_COUNT)) {
+        set_error("device bound exceeded (hash probe limit or row count mismatch), code %d", err);
+        return SPGEMM_ERR_INTERNAL;
+    }
+    return SPGEMM_OK;
+}
+
+extern "C" {
+
+const char *spgemm_last_error(void) { return g_err; }
+
+const char *spgemm_version(void) { return "gb300-spgemm 0.1 (sm_103a)"; }
+
+int spgemm_create(spgemm_handle *handle, int device) {
+    if (!handle) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    *handle = nullptr;
+    SG_CUDA(cudaSetDevice(device));
+    spgemm_handle h = new spgemm_handle_s();
+    h->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dstate, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hstate, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMemset(h->dstate, 0, sizeof(DevState));
+    if (e != cudaSuccess) {
+        set_error("spgemm_create: %s", cudaGetErrorString(e));
+        if (h->dstate) cudaFree(h->dstate);
+        if (h->hstate) cudaFreeHost(h->hstate);
+        delete h;
+        return SPGEMM_ERR_CUDA;
+    }
+    memset(h->hstate, 0, sizeof(DevState));
+    *handle = h;
+    return SPGEMM_OK;
+}
+
+int spgemm_destroy(spgemm_handle h) {
+    if (!h) return SPGEMM_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    for (auto &r : h->recs) {
+        if (r.e0) cudaEventDestroy(r.e0);
+        if (r.e1) cudaEventDestroy(r.e1);
+    }
+    if (h->dstate) cudaFree(h->dstate);
+    if (h->hstate) cudaFreeHost(h->hstate);
+    delete h;
+    return SPGEMM_OK;
+}
+
+int spgemm_check(spgemm_handle h, void *stream) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    SG_TRY(fetch_state(h, s));
+    int err = h->hstate->err;
+    if (err) SG_CUDA(cudaMemsetAsync(&h->dstate->err, 0, sizeof(int), s));
+    SG_CUDA(cudaStreamSynchronize(s));
+    return device_errors(err);
+}
+
+int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *C_row_ptr,
+                    int64_t *nnz_C, void *stream) {
+    if (!h || !C_row_ptr || !nnz_C) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", false));
+    SG_TRY(check_csr(B, "B", false));
+    if (A->ncols != B->nrows) {
+        set_error("dimension mismatch: A is %lld x %lld, B is %lld x %lld", (long long)A->nrows,
+                  (long long)A->ncols, (long long)B->nrows, (long long)B->ncols);
+        return SPGEMM_ERR_DIM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    h->sym_valid = false;
+    const int64_t n = A->nrows;
+    SG_CUDA(cudaMemsetAsync(h->dstate, 0, sizeof(DevState), s));
+    if (n == 0) {
+        SG_CUDA(cudaMemsetAsync(C_row_ptr, 0, sizeof(int64_t), s));
+        *nnz_C = 0;
+    } else {
+        // workspace: [rows | flops | bins | pairs | ccnt | minmax | scan tmp | global bitmap]
+        size_t o_rows = 0;
+        size_t o_flops = o_rows + align_up((size_t)n * 4);
+        size_t o_bins = o_flops + align_up((size_t)n * 8);
+        size_t o_pairs = o_bins + align_up((size_t)n);
+        size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
+        size_t o_mm = o_ccnt + align_up((size_t)B->nrows * 4);
+        size_t o_tmp = o_mm + align_up((size_t)B->nrows * 8);
+        size_t o_gws = o_tmp + align_up(scan_tmp_bytes(n));
+        size_t gws_bytes = symbolic_global_ws(B->ncols, h->nsm);
+        SG_TRY(ws_reserve(h, o_gws + gws_bytes, s));
+        char *w = h->ws;
+        int32_t *rows = (int32_t *)(w + o_rows);
+        int64_t *flops = (int64_t *)(w + o_flops);
+        uint8_t *bins = (uint8_t *)(w + o_bins);
+        int2 *pairs = (int2 *)(w + o_pairs);
+        int32_t *ccnt = (int32_t *)(w + o_ccnt);
+        int2 *minmax = (int2 *)(w + o_mm);
+        Ctx c = h->ctx(s);
+        SG_TRY(launch_compress(*B, pairs, ccnt, minmax, &h->dstate->err, c));
+        SG_TRY(launch_analyze(*A, *B, ccnt, minmax, flops, bins, C_row_ptr, h->dstate, c));
+        SG_TRY(fetch_state(h, s));
+        SG_TRY(device_errors(h->hstate->err));
+        memcpy(h->sym_counts, h->hstate->bin_count[0], sizeof(h->sym_counts));
+        SG_TRY(launch_scatter_bins(n, bins, rows, h->dstate, 0, c));
+        SG_TRY(launch_symbolic(*A, *B, pairs, ccnt, rows, h->sym_counts, C_row_ptr, &h->dstate->err,
+                               w + o_gws, gws_bytes, c));
+        SG_TRY(launch_scan_counts(C_row_ptr, n, &h->dstate->nnz, w + o_tmp, c));
+        SG_TRY(launch_numeric_binning(n, C_row_ptr, flops, bins, h->dstate, c));
+        SG_TRY(launch_scatter_bins(n, bins, rows, h->dstate, 1, c));
+        SG_TRY(fetch_state(h, s));
+        SG_TRY(device_errors(h->hstate->err));
+        *nnz_C = h->hstate->nnz;
+        memcpy(h->num_counts, h->hstate->bin_count[1], sizeof(h->num_counts));
+        h->max_row_nnz = h->hstate->max_row_nnz;
+        // numeric needs the row lists (kept at the front) and its global map space
+        size_t num_ws = h->num_counts[BIN_HUGE]
+                            ? numeric_global_ws(h->max_row_nnz, B->ncols, h->nsm, SPGEMM_F64)
+                            : 0;
+        h->num_gws = num_ws;
+        SG_TRY(ws_reserve(h, align_up((size_t)n * 4) + num_ws, s, (size_t)n * 4));
+    }
+    h->a_rp = A->row_ptr; h->a_col = A->col_idx; h->a_n = A->nrows; h->a_m = A->ncols;
+    h->a_nnz = A->nnz;
+    h->b_rp = B->row_ptr; h->b_col = B->col_idx; h->b_n = B->nrows; h->b_m = B->ncols;
+    h->b_nnz = B->nnz;
+    h->c_rp = C_row_ptr;
+    h->c_nnz = *nnz_C;
+    h->sym_valid = true;
+    return SPGEMM_OK;
+}
+
+int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_csr *B,
+                   spgemm_csr *C, void *stream) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) { set_error("bad dtype %d", dtype); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", true));
+    SG_TRY(check_csr(B, "B", true));
+    SG_TRY(check_csr(C, "C", true));
+    if (!h->sym_valid || A->row_ptr != h->a_rp || A->col_idx != h->a_col || A->nrows != h->a_n ||
+        A->ncols != h->a_m || A->nnz != h->a_nnz || B->row_ptr != h->b_rp || B->col_idx != h->b_col ||
+        B->nrows != h->b_n || B->ncols != h->b_m || B->nnz != h->b_nnz || C->row_ptr != h->c_rp ||
+        C->nnz != h->c_nnz || C->nrows != A->nrows || C->ncols != B->ncols) {
+        set_error("spgemm_numeric: no matching spgemm_symbolic on this handle");
+        return SPGEMM_ERR_NOT_SYMBOLIC;
+    }
+    if (A->nrows == 0 || C->nnz == 0) return SPGEMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    const int32_t *rows = (const int32_t *)h->ws;
+    char *gws = h->ws + align_up((size_t)A->nrows * 4);
+    Ctx c = h->ctx(s);
+    return launch_numeric(dtype, *A, *B, *C, rows, h->num_counts, &h->dstate->err, gws, h->num_gws,
+                          h->max_row_nnz, c);
+}
+
+int spgemm_row_flops(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *flops,
+                     void *stream) {
+    if (!h || !flops) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", false));
+    SG_TRY(check_csr(B, "B", false));
+    if (A->ncols != B->nrows) { set_error("dimension mismatch"); return SPGEMM_ERR_DIM; }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    Ctx c = h->ctx(s);
+    SG_TRY(launch_row_flops(*A, *B, flops, &h->dstate->err, c));
+    return SPGEMM_OK;
+}
+
+int spgemm_compress(spgemm_handle h, const spgemm_csr *M, int32_t *count, uint32_t *pairs,
+                    void *stream) {
+    if (!h || !count || (!pairs && M && M->nnz)) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(M, "M", false));
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    size_t need = align_up((size_t)M->nrows * 8);
+    SG_TRY(ws_reserve(h, need, s));
+    h->sym_valid = false;
+    Ctx c = h->ctx(s);
+    SG_TRY(launch_compress(*M, (int2 *)pairs, count, (int2 *)h->ws, &h->dstate->err, c));
+    return SPGEMM_OK;
+}
+
+int spgemm_set_timing(spgemm_handle h, int on) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    h->timing = on != 0;
+    if (h->timing && h->recs.empty()) h->recs.resize(8192, TimingRec{nullptr, 0, nullptr, nullptr});
+    return SPGEMM_OK;
+}
+
+int spgemm_timings(spgemm_handle h, spgemm_timing *out, int cap, int *count) {
+    if (!h || !count) { set_error("NULL handle or count"); return SPGEMM_ERR_ARG; }
+    SG_CUDA(cudaSetDevice(h->device));
+    for (int k = 0; k < h->nrec; k++) {
+        TimingRec &r = h->recs[k];
+        SG_CUDA(cudaEventSynchronize(r.e1));
+        float ms = 0;
+        SG_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+        TimingAgg *a = nullptr;
+        for (auto &x : h->agg)
+            if (x.label == r.label) a = &x;
+        if (!a) {
+            h->agg.push_back(TimingAgg());
+            a = &h->agg.back();
+            a->label = r.label;
+        }
+        a->launches++;
+        a->rows += r.rows;
+        a->ms += ms;
+    }
+    h->nrec = 0;
+    int n = (int)h->agg.size();
+    for (int k = 0; k < n && k < cap && out; k++) {
+        memset(out[k].label, 0, sizeof(out[k].label));
+        strncpy(out[k].label, h->agg[k].label.c_str(), sizeof(out[k].label) - 1);
+        out[k].launches = h->agg[k].launches;
+        out[k].rows = h->agg[k].rows;
+        out[k].ms = h->agg[k].ms;
+    }
+    *count = n;
+    return SPGEMM_OK;
+}
+
+int spgemm_reset_timings(spgemm_handle h) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    h->agg.clear();
+    h->nrec = 0;
+    return SPGEMM_OK;
+}
+
+int spgemm_launch_count(spgemm_handle h, int64_t *launches) {
+    if (!h || !launches) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    *launches = h->launches;
+    return SPGEMM_OK;
+}
+
+int spgemm_bin_of(int64_t keys, int64_t flops) { return bin_of(keys, flops); }
+
+int spgemm_bin_counts(spgemm_handle h, int64_t *symbolic_bins, int64_t *numeric_bins) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    for (int b = 0; b < NBINS; b++) {
+        if (symbolic_bins) symbolic_bins[b] = h->sym_counts[b];
+        if (numeric_bins) numeric_bins[b] = h->num_counts[b];
+    }
+    return SPGEMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""GPU parity of the two-phase SpGEMM (symbolic + numeric) against the CPU
+oracle, through the C ABI: pattern bit-exact, values within the stated
+tolerance, on the workloads' generators at several sizes and on edge cases."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1804_00695_gb300 as sg
+from paper_1804_00695_gb300 import inputs as I
+from gpu_helpers import assert_matches, oracle_product, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run(h, a, b, dtype=np.float64):
+    A, B = to_dev(a, dtype), to_dev(b, dtype)
+    c = h.spgemm(A, B)
+    h.check()
+    return c
+
+
+@pytest.fixture(scope="module")
+def h(cuda_lib):
+    return sg.Handle()
+
+
+def test_laplace2d_64_squared(h):
+    a = I.laplace2d_5pt(64)
+    c = run(h, a, a)
+    ref = oracle.spgemm(a, a)
+    assert c.nnz == 51972
+    assert_matches(c, ref, "f64")
+    # closed form: exact integers
+    assert np.array_equal(c.val.cpu().numpy(), ref.val)
+
+
+@pytest.mark.parametrize("n", [9, 16, 29])
+def test_galerkin_small(h, n):
+    a, p, r = I.galerkin_problem(n)
+    ap = run(h, a, p)
+    ref_ap = oracle.spgemm(a, p)
+    assert_matches(ap, ref_ap, "f64")
+    apm = I.Csr(a.nrows, p.ncols, ref_ap.row_ptr, ref_ap.col, ref_ap.val)
+    rap_ref = oracle.spgemm(r, apm)
+    R = to_dev(r)
+    rap = h.spgemm(R, ap)
+    h.check()
+    # second product uses the device AP; compare against the oracle on the oracle AP
+    assert np.array_equal(rap.row_ptr.cpu().numpy(), rap_ref.row_ptr)
+    assert np.array_equal(rap.col.cpu().numpy(), rap_ref.col)
+    err = np.abs(rap.val.cpu().numpy() - rap_ref.val)
+    assert np.all(err <= 1e-12 * rap_ref.bound + 1e-13 * np.abs(rap_ref.val))
+
+
+def test_galerkin_128_full(h):
+    """The 128^3 Galerkin product at full size, every entry."""
+    a, p, r = I.galerkin_problem(128)
+    A, P, R = to_dev(a), to_dev(p), to_dev(r)
+    ap = h.spgemm(A, P)
+    h.check()
+    ref_ap = oracle.spgemm(a, p)
+    assert ap.nnz == 25934336
+    assert_matches(ap, ref_ap, "f64")
+    rap = h.spgemm(R, ap)
+    h.check()
+    apm = I.Csr(a.nrows, p.ncols, ref_ap.row_ptr, ref_ap.col, ref_ap.val)
+    rap_ref = oracle.spgemm(r, apm)
+    assert rap.nnz == 2048383
+    assert np.array_equal(rap.col.cpu().numpy(), rap_ref.col)
+    err = np.abs(rap.val.cpu().numpy() - rap_ref.val)
+    assert np.all(err <= 1e-12 * rap_ref.bound + 1e-13 * np.abs(rap_ref.val))
+
+
+@pytest.mark.parametrize("scale", [8, 11])
+def test_rmat_f32(h, scale):
+    g = I.rmat_symmetric(scale, 16, seed=1)
+    c = run(h, g, g, np.float32)
+    ref = oracle_product(g, g, np.float32)
+    assert_matches(c, ref, "f32")
+    assert np.array_equal(c.val.double().cpu().numpy(), ref.val)  # integer counts: exact
+
+
+@pytest.mark.parametrize("dtype,tag", [(np.float64, "f64"), (np.float32, "f32")])
+@pytest.mark.parametrize("shape,dens,seed", [((50, 70, 40), 0.1, 1), ((300, 200, 500), 0.03, 2),
+                                             ((1, 1000, 1), 0.9, 3), ((257, 64, 3000), 0.02, 4)])
+def test_random_unsorted(h, dtype, tag, shape, dens, seed):
+    m, k, n = shape
+    a = I.random_csr(m, k, dens, seed, shuffle_cols=True)
+    b = I.random_csr(k, n, dens, seed + 50, shuffle_cols=True)
+    c = run(h, a, b, dtype)
+    assert_matches(c, oracle_product(a, b, dtype), tag)
+
+
+def _spread_rows(widths, ncols, seed):
+    rows, cols = [], []
+    for i, w in enumerate(widths):
+        stride = max(1, ncols // w)
+        cols.extend(((np.arange(w) * stride + i * 13) % ncols).tolist())
+        rows.extend([i] * w)
+    key = np.unique(np.array(rows, dtype=np.int64) * ncols + np.array(cols))
+    rp = np.zeros(len(widths) + 1, dtype=np.int64)
+    np.cumsum(np.bincount(key // ncols, minlength=len(widths)), out=rp[1:])
+    return I.Csr(len(widths), ncols, rp, (key % ncols).astype(np.int32),
+                 I.uniform01(np.arange(len(key), dtype=np.uint64), seed) - 0.5)
+
+
+def _eye(n):
+    return I.Csr(n, n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n))
+
+
+@pytest.mark.parametrize("ncols", [300000, 2000000])
+def test_every_bin_both_phases(h, ncols):
+    """Rows sized to land in every bin (1..6) of both phases: the shared-memory
+    maps, the global second-level map, and the shared (300k columns) or global
+    (2M columns) symbolic bitmap."""
+    widths = [3, 12, 40, 150, 600, 2500, 9000, 30000]
+    a = _spread_rows(widths, ncols, 5)
+    eye = _eye(ncols)
+    c = run(h, a, eye)
+    assert_matches(c, oracle.spgemm(a, eye), "f64")
+    sym, num = h.bin_counts()
+    assert all(num[b] > 0 for b in range(1, 7)), num
+    assert all(sym[b] > 0 for b in range(1, 7)), sym
+    c = run(h, a, eye, np.float32)
+    assert_matches(c, oracle_product(a, eye, np.float32), "f32")
+
+
+def test_heavy_rows_random(h):
+    """Rows whose products overlap heavily (many insertions per key)."""
+    a = _spread_rows([5, 50, 500, 5000], 6000, 7)
+    b = I.random_csr(6000, 3000, 0.01, 8)
+    for dt, tag in ((np.float64, "f64"), (np.float32, "f32")):
+        c = run(h, a, b, dt)
+        assert_matches(c, oracle_product(a, b, dt), tag)
+
+
+def test_edge_cases(h):
+    # empty A (no rows)
+    e = I.Csr(0, 5, np.zeros(1, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0))
+    b = I.random_csr(5, 7, 0.5, 9)
+    c = run(h, e, b)
+    assert c.nnz == 0 and c.row_ptr.cpu().tolist() == [0]
+    # all rows empty
+    z = I.Csr(6, 5, np.zeros(7, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0))
+    c = run(h, z, b)
+    assert c.nnz == 0 and c.row_ptr.cpu().tolist() == [0] * 7
+    # B with a single column, ncols = 1
+    a = I.random_csr(40, 30, 0.3, 10)
+    b1 = I.random_csr(30, 1, 0.6, 11)
+    c = run(h, a, b1)
+    assert_matches(c, oracle.spgemm(a, b1), "f64")
+    # A * I = A (sorted)
+    eye = I.Csr(30, 30, np.arange(31, dtype=np.int64), np.arange(30, dtype=np.int32), np.ones(30))
+    c = run(h, a, eye)
+    assert np.array_equal(c.col.cpu().numpy(), a.col) and np.array_equal(c.val.cpu().numpy(), a.val)
+    # explicit zeros stay in the pattern
+    az = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.zeros(a.nnz))
+    c = run(h, az, eye)
+    assert c.nnz == a.nnz and not c.val.any()
+
+
+def test_errors(h):
+    a = I.random_csr(10, 8, 0.3, 12)
+    b = I.random_csr(9, 8, 0.3, 13)
+    with pytest.raises(sg.SpgemmError) as ei:
+        h.symbolic(to_dev(a), to_dev(b))
+    assert ei.value.status == 2  # dimension mismatch
+    bad = I.Csr(10, 8, a.row_ptr, a.col.copy(), a.val)
+    bad.col[3] = 8 if bad.nnz > 3 else 0
+    b8 = I.random_csr(8, 8, 0.3, 14)
+    with pytest.raises(sg.SpgemmError) as ei:
+        h.symbolic(to_dev(bad), to_dev(b8))
+    assert ei.value.status == 3  # index out of range
+    A, B = to_dev(a), to_dev(b8)
+    rp, nnz = h.symbolic(A, B)
+    A2 = to_dev(a)
+    with pytest.raises(sg.SpgemmError) as ei:
+        h.numeric(A2, B, rp, nnz)
+    assert ei.value.status == 8  # numeric without matching symbolic
+    h.numeric(A, B, rp, nnz)
+    h.check()
+
+
+def test_row_flops_and_compression(h):
+    a = I.random_csr(200, 300, 0.05, 15, shuffle_cols=True)
+    b = I.laplace2d_5pt(int(np.sqrt(300)) + 1)
+    b = I.random_csr(300, 900, 0.05, 16)
+    A, B = to_dev(a), to_dev(b)
+    assert np.array_equal(h.row_flops(A, B).cpu().numpy(), oracle.row_flops(a, b))
+    cnt, pairs = h.compress(B)
+    rp, blk, mask = oracle.compress_rows(b)          # sorted input: canonical form
+    cnt = cnt.cpu().numpy()
+    pairs = pairs.cpu().numpy().view(np.uint32)
+    assert np.array_equal(cnt, np.diff(rp))
+    for k in range(b.nrows):
+        got = pairs[b.row_ptr[k]:b.row_ptr[k] + cnt[k]]
+        assert np.array_equal(got[:, 0], blk[rp[k]:rp[k + 1]].astype(np.uint32))
+        assert np.array_equal(got[:, 1], mask[rp[k]:rp[k + 1]])
+    # unsorted rows: the decoded sets still equal the column sets
+    cnt2, pairs2 = h.compress(A)
+    cnt2 = cnt2.cpu().numpy(); pairs2 = pairs2.cpu().numpy().view(np.uint32)
+    for i in range(a.nrows):
+        s = set(a.col[a.row_ptr[i]:a.row_ptr[i + 1]].tolist())
+        dec = set()
+        for kb, mk in pairs2[a.row_ptr[i]:a.row_ptr[i] + cnt2[i]]:
+            dec.update(32 * int(kb) + t for t in range(32) if (int(mk) >> t) & 1)
+        assert dec == s
