@@ -349,9 +349,11 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
     if (flag) atomicOr(err, flag);
 }
 
+// Opt in to the dynamic shared memory a launch needs (static shared memory
+// comes on top, so the attribute is set for every non-trivial size).
 template <typename K>
 static int prep(K kern, size_t smem) {
-    if (smem > 48 * 1024)
+    if (smem > 16 * 1024)
         SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return SPGEMM_OK;
 }

@@ -174,9 +174,12 @@ size_t symbolic_global_ws(int64_t ncols_b, int nsm) {
     return (size_t)nwords * 4 * (size_t)nsm;
 }
 
+// Opt in to the dynamic shared memory a launch needs (static shared memory
+// comes on top, so the attribute is set for every non-trivial size).
 template <typename K>
 static int prep(K kern, size_t smem) {
-    if (smem > 48 * 1024) SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 16 * 1024)
+        SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return SPGEMM_OK;
 }
 
