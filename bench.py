@@ -29,8 +29,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SpGEMM GFLOP/s (2×mults/s) & % of HBM-byte roofline; batched/bwd vs plain"
-BIN_CAP = [0, 16, 64, 256, 1024, 4096]
-BIN_FLOPS = [0, 1024, 4096, 32768, 262144, 2097152]
+BIN_CAP = [0, 16, 32, 128, 1024, 4096]
+BIN_FLOPS = [0, 8192, 8192, 65536, 1048576, 16777216]
 
 
 def parse():
@@ -274,11 +274,17 @@ def main():
     kern = []
     for key, (nl, rows, tms) in tim.items():
         parts = key.split(".")
-        if len(parts) != 3 or parts[1] != "numeric" or not parts[2].startswith("bin"):
+        if len(parts) != 3 or parts[1] != "numeric":
             continue
         am, brp, crp, fl = prod[parts[0]]
-        mask = bins_of(np.diff(crp), fl) == int(parts[2][3:])
-        assert mask.sum() == rows // nl, (key, mask.sum(), rows, nl)
+        bb = bins_of(np.diff(crp), fl)
+        if parts[2] == "small":
+            mask = (bb == 1) | (bb == 2)
+        elif parts[2].startswith("bin"):
+            mask = bb == int(parts[2][3:])
+            assert mask.sum() == rows // nl, (key, mask.sum(), rows, nl)
+        else:
+            continue
         kern.append((tms / nl, key, kernel_bytes(am, brp, crp, mask, 8, True), nl))
     roof = None
     if kern:

@@ -112,6 +112,23 @@ SPGEMM_API int spgemm_symbolic(spgemm_handle handle, const spgemm_csr *A, const 
 SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr *A,
                    const spgemm_csr *B, spgemm_csr *C, void *stream);
 
+/* Options of a handle.
+ *  SPGEMM_OPT_F64_NATIVE (0/1, default 0): FP64 products are accumulated as
+ *    double-words (a pair of floats, 48 significand bits) in the FP32 units,
+ *    which meets |c - c_exact| <= (7 + 5n) 2^-48 sum|a_ik||b_kj| for an entry
+ *    with n terms; rows whose inputs lie outside [2^-60, 2^60] in magnitude
+ *    (zeros excepted) and rows wider than 128 entries accumulate in native
+ *    FP64.  1 = native FP64 everywhere.
+ *  SPGEMM_OPT_LANES_NUMERIC / SPGEMM_OPT_LANES_SYMBOLIC (0, 4, 8, 16, 32;
+ *    default 0 = from the mean row length of B): lanes that share a row in
+ *    the kernels for rows with few outputs. */
+typedef enum spgemm_option {
+    SPGEMM_OPT_F64_NATIVE = 1,
+    SPGEMM_OPT_LANES_NUMERIC = 2,
+    SPGEMM_OPT_LANES_SYMBOLIC = 3
+} spgemm_option;
+SPGEMM_API int spgemm_set_option(spgemm_handle handle, int option, int64_t value);
+
 /* Synchronises `stream` and reports device-side errors raised by earlier
  * asynchronous calls on this handle (SPGEMM_ERR_INTERNAL if a hash probe
  * bound was exceeded or a row's column count disagreed with the symbolic
@@ -136,8 +153,10 @@ SPGEMM_API int spgemm_compress(spgemm_handle handle, const spgemm_csr *M, int32_
 #define SPGEMM_NBINS 8
 SPGEMM_API int spgemm_bin_counts(spgemm_handle handle, int64_t *symbolic_bins, int64_t *numeric_bins);
 
-/* Bin (0..6) that a row needing `keys` accumulator entries and taking
- * `flops` products is assigned to (0 = empty row).  Host only. */
+/* Numeric bin (0..6) of a row with `keys` output entries taking `flops`
+ * products (0 = empty row): 1 <= 16 entries, 2 <= 32, 3 <= 128, 4 <= 1024,
+ * 5 <= 4096, 6 larger; rows with many products move to wider bins.  Host
+ * only. */
 SPGEMM_API int spgemm_bin_of(int64_t keys, int64_t flops);
 
 /* Instrumentation.  spgemm_launch_count: kernels launched through this

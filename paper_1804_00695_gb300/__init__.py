@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libspgemm_gb300.so")
 
 F32, F64 = 0, 1
 NBINS = 8
+OPT_F64_NATIVE, OPT_LANES_NUMERIC, OPT_LANES_SYMBOLIC = 1, 2, 3
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_DIM", 3: "ERR_INDEX", 4: "ERR_NOMEM", 5: "ERR_BUDGET",
           6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_NOT_SYMBOLIC", 9: "ERR_INTERNAL"}
 
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         "spgemm_set_timing": ([p, i32], i32),
         "spgemm_timings": ([p, p, i32, C.POINTER(i32)], i32),
         "spgemm_reset_timings": ([p], i32),
+        "spgemm_set_option": ([p, i32, i64], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +214,9 @@ class Handle:
         _check(_lib.spgemm_compress(self._h, C.byref(dm), cnt.data_ptr(), pairs.data_ptr(),
                                     _stream(stream)))
         return cnt, pairs
+
+    def set_option(self, option: int, value: int):
+        _check(_lib.spgemm_set_option(self._h, option, value))
 
     def launch_count(self) -> int:
         n = C.c_int64()

@@ -52,10 +52,23 @@ int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minma
 }
 
 // ---------------------------------------------------------------- analysis
+// Adds this warp's per-bin row counts (bins held by the lanes where `has`)
+// to a shared histogram with one ballot per bin.
+__device__ __forceinline__ void warp_hist(unsigned long long *hist, bool has, int bin) {
+    const unsigned have = __ballot_sync(0xffffffffu, has);
+    if (!have) return;
+    for (int b = 0; b < NBINS; b++) {
+        unsigned m = __ballot_sync(0xffffffffu, has && bin == b);
+        if (m && (threadIdx.x & 31) == 0) atomicAdd(&hist[b], (unsigned long long)__popc(m));
+    }
+}
+
 // Eight lanes per row of A.  For row i: flops_i = sum_k nnz(B_k) (the number
 // of accumulator insertions, Section 3.1), cpairs_i = sum_k pairs(B_k), and
 // the span of compressed blocks the row can reach.  The symbolic
 // accumulator needs at most min(cpairs_i, span_i, ceil(ncols/32)) keys.
+// Empty rows get their count (0) here; rows for the dense bitmap (bin 6)
+// are marked -1 for the second pass.
 constexpr int AN_G = 8;
 __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
                           const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
@@ -66,8 +79,7 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
     if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x % AN_G;
-    const unsigned gmask = (AN_G == 32) ? 0xffffffffu
-                                        : (((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1)));
+    const unsigned gmask = ((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1));
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / AN_G;
     bool live = i < nrows;
     long long f = 0, cp = 0;
@@ -91,20 +103,26 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
         bmax = max(bmax, __shfl_xor_sync(gmask, bmax, d, AN_G));
     }
     if (bad) atomicOr(&st->err, DERR_COL_RANGE);
-    if (live && lane == 0) {
+    int b = BIN_EMPTY;
+    const bool lead = live && lane == 0;
+    if (lead) {
         long long keys = cp;
         if (bmax >= bmin) keys = min(keys, (long long)(bmax - bmin) + 1);
         else keys = 0;
         keys = min(keys, (long long)nwords);
-        int b = bin_of(keys, cp);
+        b = sym_bin(keys, cp);
         flops[i] = f;
         bins[i] = (uint8_t)b;
         if (b == BIN_EMPTY) crp[i + 1] = 0;
-        atomicAdd(&hist[b], 1ull);
+        if (b == BIN_HUGE) crp[i + 1] = -1;
     }
+    warp_hist(hist, lead, b);
     __syncthreads();
-    if (threadIdx.x < NBINS && hist[threadIdx.x])
-        atomicAdd((unsigned long long *)&st->bin_count[0][threadIdx.x], hist[threadIdx.x]);
+    if (threadIdx.x < NBINS && hist[threadIdx.x]) {
+        atomicAdd((unsigned long long *)&st->sym_hist[threadIdx.x], hist[threadIdx.x]);
+        if (threadIdx.x == BIN_HUGE)
+            atomicAdd((unsigned long long *)&st->bin_count[0][BIN_HUGE], hist[threadIdx.x]);
+    }
 }
 
 int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int32_t *ccnt,
@@ -163,13 +181,14 @@ __global__ void k_numeric_binning(int64_t n, const int64_t *__restrict__ crp,
     if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = BIN_EMPTY;
     if (i < n) {
         long long c = crp[i + 1] - crp[i];
-        int b = c > 0 ? bin_of(c, flops[i]) : BIN_EMPTY;
+        b = c > 0 ? num_bin(c, flops[i]) : BIN_EMPTY;
         bins[i] = (uint8_t)b;
-        atomicAdd(&hist[b], 1ull);
         if (b == BIN_HUGE) atomicMax((unsigned long long *)&st->max_row_nnz, (unsigned long long)c);
     }
+    warp_hist(hist, i < n, b);
     __syncthreads();
     if (threadIdx.x < NBINS && hist[threadIdx.x])
         atomicAdd((unsigned long long *)&st->bin_count[1][threadIdx.x], hist[threadIdx.x]);
@@ -185,22 +204,33 @@ int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, 
     return SPGEMM_OK;
 }
 
-// Rows of each non-empty bin are appended to the bin's list; within a warp
-// the lanes with the same bin reserve their slots with one atomic
+// Row lists for the list-driven kernels.  phase 0 (symbolic second pass):
+// rows marked -1 in crp[i+1] (overflowed the first pass, or bin 6), listed by
+// max(bins[i], 2).  phase 1 (numeric): rows of bins 3..6.  Within a warp the
+// lanes with the same bin reserve their slots with one atomic
 // (__match_any_sync), so rows stay in ascending order inside each warp.
 __global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
-                               int32_t *__restrict__ rows, DevState *st, int phase) {
+                               const int64_t *__restrict__ crp, int32_t *__restrict__ rows,
+                               DevState *st, int phase) {
     __shared__ long long off[NBINS];
     if (threadIdx.x == 0) {
         long long o = 0;
         for (int b = 0; b < NBINS; b++) {
             off[b] = o;
-            if (b != BIN_EMPTY) o += st->bin_count[phase][b];
+            if (b >= (phase == 0 ? 2 : 3) && b <= BIN_HUGE) o += st->bin_count[phase][b];
         }
     }
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int b = i < n ? bins[i] : BIN_EMPTY;
+    int b = BIN_EMPTY;
+    if (i < n) {
+        if (phase == 0) {
+            if (crp[i + 1] < 0) b = max((int)bins[i], 2);
+        } else {
+            int x = bins[i];
+            if (x >= 3) b = x;
+        }
+    }
     unsigned act = __ballot_sync(0xffffffffu, b != BIN_EMPTY);
     if (b == BIN_EMPTY) return;
     unsigned peers = __match_any_sync(act, b);
@@ -214,12 +244,12 @@ __global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
     rows[off[b] + base + rank] = (int32_t)i;
 }
 
-int launch_scatter_bins(int64_t n, const uint8_t *bins, int32_t *rows, DevState *st, int phase,
-                        Ctx &c) {
+int launch_scatter_bins(int64_t n, const uint8_t *bins, const int64_t *crp, int32_t *rows,
+                        DevState *st, int phase, Ctx &c) {
     if (n == 0) return SPGEMM_OK;
     SG_CUDA(cudaMemsetAsync(st->bin_cursor, 0, sizeof(st->bin_cursor), c.s));
     c.begin("scatter_bins", n);
-    k_scatter_bins<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, bins, rows, st, phase);
+    k_scatter_bins<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, bins, crp, rows, st, phase);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;

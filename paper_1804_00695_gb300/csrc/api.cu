@@ -67,7 +67,11 @@ struct spgemm_handle_s {
     long long sym_counts[NBINS] = {0};
     long long num_counts[NBINS] = {0};
     int64_t max_row_nnz = 0;
-    size_t num_gws = 0;   // bytes after the row lists that numeric needs
+    size_t num_gws = 0;   // bytes of the second-level maps numeric needs
+    bool num_lists = false;   // numeric row lists built for this symbolic result
+    // options
+    bool f64_native = false;
+    int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from B's row length)
     // launch counting and CUDA-event timing
     long long launches = 0;
     bool timing = false;
@@ -197,6 +201,17 @@ int spgemm_check(spgemm_handle h, void *stream) {
     return device_errors(err);
 }
 
+// Largest power of two <= x, clamped to [4, 32].
+static int lanes_for(double x) {
+    int g = 4;
+    while (g < 32 && 2 * g <= x) g *= 2;
+    return g;
+}
+
+// Workspace: [bins | rows] persist from symbolic to numeric; after them the
+// symbolic scratch, or (later) the numeric scratch, which may overlap it.
+static size_t ws_persist(int64_t n) { return align_up((size_t)n) + align_up((size_t)n * 4); }
+
 int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *C_row_ptr,
                     int64_t *nnz_C, void *stream) {
     if (!h || !C_row_ptr || !nnz_C) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
@@ -215,48 +230,60 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
     if (n == 0) {
         SG_CUDA(cudaMemsetAsync(C_row_ptr, 0, sizeof(int64_t), s));
         *nnz_C = 0;
+        memset(h->sym_counts, 0, sizeof(h->sym_counts));
+        memset(h->num_counts, 0, sizeof(h->num_counts));
     } else {
-        // workspace: [rows | flops | bins | pairs | ccnt | minmax | scan tmp | global bitmap]
-        size_t o_rows = 0;
-        size_t o_flops = o_rows + align_up((size_t)n * 4);
-        size_t o_bins = o_flops + align_up((size_t)n * 8);
-        size_t o_pairs = o_bins + align_up((size_t)n);
-        size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
-        size_t o_mm = o_ccnt + align_up((size_t)B->nrows * 4);
-        size_t o_tmp = o_mm + align_up((size_t)B->nrows * 8);
-        size_t o_gws = o_tmp + align_up(scan_tmp_bytes(n));
-        size_t gws_bytes = symbolic_global_ws(B->ncols, h->nsm);
+        const size_t o_bins = 0;
+        const size_t o_rows = align_up((size_t)n);
+        const size_t o_flops = ws_persist(n);
+        const size_t o_pairs = o_flops + align_up((size_t)n * 8);
+        const size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
+        const size_t o_mm = o_ccnt + align_up((size_t)B->nrows * 4);
+        const size_t o_tmp = o_mm + align_up((size_t)B->nrows * 8);
+        const size_t o_gws = o_tmp + align_up(scan_tmp_bytes(n));
+        const size_t gws_bytes = symbolic_global_ws(B->ncols, h->nsm);
         SG_TRY(ws_reserve(h, o_gws + gws_bytes, s));
         char *w = h->ws;
+        uint8_t *bins = (uint8_t *)(w + o_bins);
         int32_t *rows = (int32_t *)(w + o_rows);
         int64_t *flops = (int64_t *)(w + o_flops);
-        uint8_t *bins = (uint8_t *)(w + o_bins);
         int2 *pairs = (int2 *)(w + o_pairs);
         int32_t *ccnt = (int32_t *)(w + o_ccnt);
         int2 *minmax = (int2 *)(w + o_mm);
         Ctx c = h->ctx(s);
+        const int gs = h->g_symbolic ? h->g_symbolic
+                                     : lanes_for((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1) / 2.0);
         SG_TRY(launch_compress(*B, pairs, ccnt, minmax, &h->dstate->err, c));
         SG_TRY(launch_analyze(*A, *B, ccnt, minmax, flops, bins, C_row_ptr, h->dstate, c));
+        SG_TRY(launch_symbolic_first(*A, *B, bins, ccnt, pairs, C_row_ptr, h->dstate, gs, c));
         SG_TRY(fetch_state(h, s));
         SG_TRY(device_errors(h->hstate->err));
-        memcpy(h->sym_counts, h->hstate->bin_count[0], sizeof(h->sym_counts));
-        SG_TRY(launch_scatter_bins(n, bins, rows, h->dstate, 0, c));
-        SG_TRY(launch_symbolic(*A, *B, pairs, ccnt, rows, h->sym_counts, C_row_ptr, &h->dstate->err,
-                               w + o_gws, gws_bytes, c));
+        long long second = 0;
+        for (int b = 2; b <= BIN_HUGE; b++) second += h->hstate->bin_count[0][b];
+        long long first = 0;
+        for (int b = 1; b < BIN_HUGE; b++) first += h->hstate->sym_hist[b];
+        h->sym_counts[0] = h->hstate->sym_hist[0];
+        h->sym_counts[1] = first - (second - h->hstate->bin_count[0][BIN_HUGE]);
+        for (int b = 2; b < NBINS; b++) h->sym_counts[b] = h->hstate->bin_count[0][b];
+        if (second > 0) {
+            SG_TRY(launch_scatter_bins(n, bins, C_row_ptr, rows, h->dstate, 0, c));
+            SG_TRY(launch_symbolic(*A, *B, pairs, ccnt, rows, h->hstate->bin_count[0], C_row_ptr,
+                                   &h->dstate->err, w + o_gws, gws_bytes, c));
+        }
         SG_TRY(launch_scan_counts(C_row_ptr, n, &h->dstate->nnz, w + o_tmp, c));
         SG_TRY(launch_numeric_binning(n, C_row_ptr, flops, bins, h->dstate, c));
-        SG_TRY(launch_scatter_bins(n, bins, rows, h->dstate, 1, c));
         SG_TRY(fetch_state(h, s));
         SG_TRY(device_errors(h->hstate->err));
         *nnz_C = h->hstate->nnz;
         memcpy(h->num_counts, h->hstate->bin_count[1], sizeof(h->num_counts));
         h->max_row_nnz = h->hstate->max_row_nnz;
-        // numeric needs the row lists (kept at the front) and its global map space
-        size_t num_ws = h->num_counts[BIN_HUGE]
-                            ? numeric_global_ws(h->max_row_nnz, B->ncols, h->nsm, SPGEMM_F64)
-                            : 0;
-        h->num_gws = num_ws;
-        SG_TRY(ws_reserve(h, align_up((size_t)n * 4) + num_ws, s, (size_t)n * 4));
+        h->num_gws = h->num_counts[BIN_HUGE]
+                         ? numeric_global_ws(h->max_row_nnz, B->ncols, h->nsm, SPGEMM_F64)
+                         : 0;
+        h->num_lists = false;
+        // numeric scratch: B split into double-words, then the second-level maps
+        SG_TRY(ws_reserve(h, ws_persist(n) + align_up((size_t)B->nnz * 8) + h->num_gws, s,
+                          ws_persist(n)));
     }
     h->a_rp = A->row_ptr; h->a_col = A->col_idx; h->a_n = A->nrows; h->a_m = A->ncols;
     h->a_nnz = A->nnz;
@@ -285,11 +312,38 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     if (A->nrows == 0 || C->nnz == 0) return SPGEMM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     SG_CUDA(cudaSetDevice(h->device));
-    const int32_t *rows = (const int32_t *)h->ws;
-    char *gws = h->ws + align_up((size_t)A->nrows * 4);
+    const int64_t n = A->nrows;
+    uint8_t *bins = (uint8_t *)h->ws;
+    int32_t *rows = (int32_t *)(h->ws + align_up((size_t)n));
+    float2 *bsplit = (float2 *)(h->ws + ws_persist(n));
+    char *gws = h->ws + ws_persist(n) + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
-    return launch_numeric(dtype, *A, *B, *C, rows, h->num_counts, &h->dstate->err, gws, h->num_gws,
-                          h->max_row_nnz, c);
+    long long listed = 0;
+    for (int b = 3; b <= BIN_HUGE; b++) listed += h->num_counts[b];
+    if (listed > 0 && !h->num_lists) {
+        SG_TRY(launch_scatter_bins(n, bins, C->row_ptr, rows, h->dstate, 1, c));
+        h->num_lists = true;
+    }
+    const int gn = h->g_numeric ? h->g_numeric
+                                : lanes_for((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1));
+    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, rows, h->num_counts, h->dstate,
+                          bsplit, gws, h->num_gws, h->max_row_nnz, gn, c);
+}
+
+int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    switch (option) {
+        case SPGEMM_OPT_F64_NATIVE: h->f64_native = value != 0; return SPGEMM_OK;
+        case SPGEMM_OPT_LANES_NUMERIC:
+        case SPGEMM_OPT_LANES_SYMBOLIC:
+            if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32) {
+                set_error("lanes per row must be 0 (automatic), 4, 8, 16 or 32");
+                return SPGEMM_ERR_ARG;
+            }
+            (option == SPGEMM_OPT_LANES_NUMERIC ? h->g_numeric : h->g_symbolic) = (int)value;
+            return SPGEMM_OK;
+        default: set_error("unknown option %d", option); return SPGEMM_ERR_ARG;
+    }
 }
 
 int spgemm_row_flops(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *flops,
@@ -372,7 +426,7 @@ int spgemm_launch_count(spgemm_handle h, int64_t *launches) {
     return SPGEMM_OK;
 }
 
-int spgemm_bin_of(int64_t keys, int64_t flops) { return bin_of(keys, flops); }
+int spgemm_bin_of(int64_t keys, int64_t flops) { return num_bin(keys, flops); }
 
 int spgemm_bin_counts(spgemm_handle h, int64_t *symbolic_bins, int64_t *numeric_bins) {
     if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }

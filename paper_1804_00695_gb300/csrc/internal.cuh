@@ -33,7 +33,8 @@ enum : int {
 
 struct DevState {          // lives in device memory, one per handle
     int err;
-    int pad;
+    int b_out_of_range;    // B holds values outside the double-word range
+    long long sym_hist[SPGEMM_NBINS];   // rows per symbolic bin (by bound)
     long long nnz;         // nnz(C) written by the scan
     long long bin_count[2][SPGEMM_NBINS];   // [0] symbolic, [1] numeric
     long long bin_cursor[SPGEMM_NBINS];
@@ -42,26 +43,42 @@ struct DevState {          // lives in device memory, one per handle
 
 // ---------------------------------------------------------------- bins
 // Rows are binned by the size of the accumulator they need and by their
-// product count; each bin has its own kernel shape (Section 3.3: a half,
-// quarter or whole warp per row, or a whole block).
+// product count; each bin has its own kernel shape (Section 3.3: a part of a
+// warp, a whole warp or a whole block per row).
 constexpr int BIN_EMPTY = 0;
 constexpr int BIN_HUGE = 6;     // widest bin: unbounded accumulator
-constexpr int NBINS = SPGEMM_NBINS;   // bins 1..6 used, 7 spare
-// Accumulator capacity of bins 1..5 (distinct keys; bin b's map has
-// 2*cap slots); bin 6 is unbounded.
-__host__ __device__ constexpr long long bin_cap(int b) {
-    return b == 1 ? 16 : b == 2 ? 64 : b == 3 ? 256 : b == 4 ? 1024 : b == 5 ? 4096 : (1LL << 40);
+constexpr int NBINS = SPGEMM_NBINS;
+
+// Numeric bins by exact output count (and product count):
+//   1: <= 16 entries, 2: <= 32 (both: lanes of a warp, map in shared memory,
+//   rows taken in order), 3: <= 128 (a warp), 4: <= 1024, 5: <= 4096 (a
+//   block), 6: larger (a block with a global second-level map).
+__host__ __device__ constexpr long long num_cap(int b) {
+    return b == 1 ? 16 : b == 2 ? 32 : b == 3 ? 128 : b == 4 ? 1024 : b == 5 ? 4096 : (1LL << 40);
 }
-// Product counts that promote a row to a wider bin.
-__host__ __device__ constexpr long long bin_flops(int b) {
-    return b == 1 ? 1024 : b == 2 ? 4096 : b == 3 ? 32768 : b == 4 ? 262144 : b == 5 ? 2097152
-                                                                               : (1LL << 62);
+__host__ __device__ constexpr long long num_flops(int b) {
+    return b <= 2 ? 8192 : b == 3 ? 65536 : b == 4 ? 1048576 : b == 5 ? 16777216 : (1LL << 62);
+}
+__host__ __device__ inline int num_bin(long long nnz, long long flops) {
+    if (nnz <= 0) return BIN_EMPTY;
+    int b = 1;
+    while (b < BIN_HUGE && (nnz > num_cap(b) || flops > num_flops(b))) b++;
+    return b;
 }
 
-__host__ __device__ inline int bin_of(long long keys, long long flops) {
+// Symbolic bins by an upper bound on the row's distinct column blocks:
+// every row with bound <= 4096 is first tried with a 32-slot map (most rows
+// of sparse products have few blocks); rows that overflow it, and rows with
+// a larger bound, go to 2: <= 64 keys, 3: <= 256 (a warp), 4: <= 1024,
+// 5: <= 4096 (a block), 6: dense bitmap of all blocks (a block).
+constexpr int SYM_FIRST_SLOTS = 32;
+__host__ __device__ constexpr long long sym_cap(int b) {
+    return b == 1 ? 16 : b == 2 ? 64 : b == 3 ? 256 : b == 4 ? 1024 : b == 5 ? 4096 : (1LL << 40);
+}
+__host__ __device__ inline int sym_bin(long long keys, long long cpairs) {
     if (keys <= 0) return BIN_EMPTY;
     int b = 1;
-    while (b < BIN_HUGE && (keys > bin_cap(b) || flops > bin_flops(b))) b++;
+    while (b < BIN_HUGE && (keys > sym_cap(b) || cpairs > 64 * sym_cap(b))) b++;
     return b;
 }
 
@@ -111,13 +128,18 @@ int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int32_t *ccnt
 // Numeric bin of every row from its output count crp[i+1]-crp[i] and flops.
 int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, uint8_t *bins,
                            DevState *st, Ctx &c);
-// Row lists per bin: rows[offset(b) + t]; offsets from st->bin_count[phase].
-int launch_scatter_bins(int64_t n, const uint8_t *bins, int32_t *rows, DevState *st, int phase,
-                        Ctx &c);
+// Row lists per bin: rows[offset(b) + t]; offsets from st->bin_count[phase]
+// (phase 0: symbolic second pass, phase 1: numeric bins 3..6).
+int launch_scatter_bins(int64_t n, const uint8_t *bins, const int64_t *crp, int32_t *rows,
+                        DevState *st, int phase, Ctx &c);
 int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, int *err, Ctx &c);
 
 // symbolic.cu
-// Runs the symbolic kernels of bins 1..6; counts[b] = rows in bin b (host),
+// First pass over all rows with a 32-slot map and G lanes per row.
+int launch_symbolic_first(const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
+                          const int32_t *ccnt, const int2 *pairs, int64_t *crp, DevState *st,
+                          int G, Ctx &c);
+// Second pass: kernels of bins 2..6; counts[b] = rows in bin b (host),
 // rows = concatenated bin lists.  Writes nnz(C_i) to crp[i+1].
 int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
                     const int32_t *ccnt, const int32_t *rows, const long long *counts,
@@ -125,10 +147,13 @@ int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
 size_t symbolic_global_ws(int64_t ncols_b, int nsm);
 
 // numeric.cu
-// Runs the numeric kernels of bins 1..6 (counts[b] rows in bin b, host).
-int launch_numeric(int dtype, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
-                   const int32_t *rows, const long long *counts, int *err, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, Ctx &c);
+// Runs the numeric kernels: bins 1-2 over all rows in order (bins[i]), bins
+// 3..6 from the row lists (counts[b] rows in bin b, host).  FP64 uses
+// double-word accumulation unless f64_native; bsplit: room for nnz(B) float2.
+int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B,
+                   spgemm_csr &C, const uint8_t *bins, const int32_t *rows, const long long *counts,
+                   DevState *st, float2 *bsplit, void *gws, size_t gws_bytes, int64_t max_row_nnz,
+                   int G, Ctx &c);
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype);
 
 }  // namespace sg

@@ -1,60 +1,257 @@
 // Numeric phase (Section 2.1): C_i = sum over stored a_ik of a_ik * B_k,
 // accumulated in hash maps from column to value (Section 2.1, "sparse
-// hashmap-based accumulators"); the first level lives in shared memory and,
-// for the largest rows, a second level in global memory takes what the first
-// cannot hold (Section 3.3).  Every row's map is sized from its exact count
-// (known from the symbolic phase), so bins 1-5 never overflow.  Output rows
-// are written with ascending columns: small rows are ranked by counting,
-// larger ones sorted with a bitonic network in shared memory, and the
-// largest ranked through a bitmap of their columns.
+// hashmap-based accumulators"); maps live in shared memory and, for the
+// largest rows, a second level in global memory takes what the first cannot
+// hold (Section 3.3).  Every map is sized from the row's exact count, known
+// from the symbolic phase.  Output rows have ascending columns.
+//
+// Rows with at most 32 outputs (bins 1, 2) are taken in row order by groups
+// of G lanes; the lanes of a group walk one row of B at a time (coalesced
+// loads), so within a step they touch distinct columns and update their
+// accumulators without atomics; a __syncwarp separates the rows of B.
+// Bin 3 (<= 128 outputs) gives a warp per row the same way; bins 4-6 give a
+// block per row with atomic updates.
+//
+// FP64 values are accumulated as double-words (two floats, 48 significand
+// bits: dword.cuh) in the FP32 pipeline unless an input lies outside the
+// double-word range, in which case that row (or, for B, the whole call) uses
+// native FP64; the block kernels accumulate in native precision.
 #include <climits>
+#include <type_traits>
+#include "dword.cuh"
 #include "internal.cuh"
 
 namespace sg {
 
-template <typename V>
-__device__ __forceinline__ void atomic_add_v(V *p, V v) { atomicAdd(p, v); }
+enum { MODE_F32 = 0, MODE_DW = 1, MODE_F64 = 2 };
 
-// Insert (col, v) into a map of 2^L slots; returns false when `limit`
-// probes found neither the key nor a free slot.
-template <typename V>
-__device__ __forceinline__ bool num_insert(int *keys, V *vals, int L, int limit, int col, V v) {
+struct NumP {
+    const int64_t *arp; const int32_t *acol; const void *aval;
+    const int64_t *brp; const int32_t *bcol; const void *bval; const float2 *bsplit;
+    const int64_t *crp; int32_t *ccol; void *cval;
+};
+
+// Find or insert `col` in a map of 2^L slots (keys only); -1 if full.
+__device__ __forceinline__ int map_slot(int *keys, int L, int col) {
     const unsigned msk = (1u << L) - 1;
     unsigned h = hash_slot(col, L);
 #pragma unroll 1
-    for (int probe = 0; probe < limit; probe++) {
+    for (int probe = 0; probe <= (int)msk; probe++) {
         int k = ((volatile int *)keys)[h];
-        if (k == col) {
-            atomic_add_v(&vals[h], v);
-            return true;
-        }
+        if (k == col) return (int)h;
         if (k == -1) {
             int old = atomicCAS(&keys[h], -1, col);
-            if (old == -1 || old == col) {
-                atomic_add_v(&vals[h], v);
-                return true;
-            }
+            if (old == -1 || old == col) return (int)h;
         }
         h = (h + 1) & msk;
     }
-    return false;
+    return -1;
 }
 
-// Bitonic sort of P (power of two) keys with values, in shared memory, by
-// NT cooperating threads (tid in [0, NT)); sync() separates the stages.
+__device__ __forceinline__ int next_pow2(int n) { return n <= 1 ? 1 : 1 << (32 - __clz(n - 1)); }
+
+// B values split once into double-words; flags the call if any value is
+// outside the double-word range.
+__global__ void k_split_values(int64_t nnz, const double *__restrict__ v, float2 *__restrict__ out,
+                               DevState *st) {
+    bool ok = true;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dw_split(v[i], ok);
+    if (!ok) atomicOr(&st->b_out_of_range, 1);
+}
+
+// Accumulator slot: 4 bytes (FP32) or 8 bytes (a double or a double-word).
+template <int MODE>
+using SlotT = typename std::conditional<MODE == MODE_F32, float, double>::type;
+
+// Value type of A and B elements.
+template <int MODE>
+using ValT = typename std::conditional<MODE == MODE_F32, float, double>::type;
+
+template <int MODE>
+__device__ __forceinline__ void acc_update(SlotT<MODE> *acc, int slot, bool nat, const void *bval,
+                                           const float2 *bsplit, int64_t q, ValT<MODE> av, float2 a2) {
+    if (MODE == MODE_F32) {
+        acc[slot] += av * ((const float *)bval)[q];
+    } else if (MODE == MODE_DW && !nat) {
+        float2 *a = (float2 *)acc;
+        a[slot] = dw_add(a[slot], dw_mul(a2, bsplit[q]));
+    } else {
+        acc[slot] += av * ((const double *)bval)[q];
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_out(void *cval, int64_t pos, SlotT<MODE> v, bool nat) {
+    if (MODE == MODE_F32) {
+        ((float *)cval)[pos] = v;
+    } else if (MODE == MODE_DW && !nat) {
+        // the slot holds a double-word: hi in the low 32 bits, lo in the high 32
+        const unsigned long long bits = (unsigned long long)__double_as_longlong((double)v);
+        ((double *)cval)[pos] = dw_to_double(__uint_as_float((unsigned)bits),
+                                             __uint_as_float((unsigned)(bits >> 32)));
+    } else {
+        ((double *)cval)[pos] = v;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ ValT<MODE> load_a(const void *aval, int64_t p) {
+    return ((const ValT<MODE> *)aval)[p];
+}
+
+// Bins 1-2: a warp takes 32/G consecutive rows, G lanes per row, map of up
+// to 64 slots per row.  All lanes of the warp stay converged: the loops run
+// to the warp-wide maximum (row length, chunks of the current B row) and
+// idle lanes are predicated off, so the rows of a warp advance in lockstep.
+// The stored a_ik of a row are loaded a batch at a time into registers
+// (entry p held by lane p % G, slot p / G) and broadcast with shuffles, so
+// only the loads of B_k sit on the path of each step.
+template <int G, int MODE>
+__global__ void __launch_bounds__(256) k_num_small(NumP a, int64_t n, const uint8_t *__restrict__ bins,
+                                                   const DevState *st, int *err) {
+    constexpr int SMAX = 64, RPW = 32 / G, WPB = 8, PER = SMAX / G, R = (G >= 16 ? 2 : 32 / G);
+    using Slot = SlotT<MODE>;
+    using V = ValT<MODE>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / G, gl = lane % G, gbase = g * G;
+    Slot *acc = (Slot *)smem_raw + (w * RPW + g) * SMAX;
+    int *keys = (int *)((Slot *)smem_raw + WPB * RPW * SMAX) + (w * RPW + g) * SMAX;
+    const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
+    int flag = 0;
+    const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
+    for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
+        const int64_t i = base + g;
+        int bi = i < n ? bins[i] : 0;
+        const bool active = bi == 1 || bi == 2;
+        const int64_t p0 = active ? a.arp[i] : 0;
+        const int plen = active ? (int)(a.arp[i + 1] - p0) : 0;
+        const int64_t out = active ? a.crp[i] : 0;
+        const int nn = active ? (int)(a.crp[i + 1] - out) : 0;
+        int S = next_pow2(2 * nn);
+        S = S < G ? G : (S > SMAX ? SMAX : S);
+        const int L = __ffs(S) - 1;
+#pragma unroll
+        for (int t = 0; t < PER; t++) {
+            const int sidx = gl + t * G;
+            if (sidx < S) {
+                keys[sidx] = -1;
+                acc[sidx] = Slot(0);
+            }
+        }
+        const int maxlen = __reduce_max_sync(0xffffffffu, plen);
+        bool nat = MODE == MODE_F64 || b_bad;
+        if (MODE == MODE_DW && !nat) {
+            bool ok = true;
+            for (int p = gl; p < maxlen; p += G)
+                if (p < plen) dw_split(((const double *)a.aval)[p0 + p], ok);
+            const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+            nat = ((bad >> gbase) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1))) != 0;
+        }
+        __syncwarp();
+        for (int pb = 0; pb < maxlen; pb += G * R) {
+            int kk[R];
+            V av[R];
+            int64_t q0[R];
+            int blen[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int p = pb + gl + G * r;
+                const bool has = p < plen;
+                kk[r] = has ? a.acol[p0 + p] : 0;
+                av[r] = has ? ((const V *)a.aval)[p0 + p] : V(0);
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int p = pb + gl + G * r;
+                const bool has = p < plen;
+                q0[r] = has ? a.brp[kk[r]] : 0;
+                blen[r] = has ? (int)(a.brp[kk[r] + 1] - q0[r]) : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+#pragma unroll 1
+                for (int src = 0; src < G; src++) {
+                    if (pb + G * r + src >= maxlen) break;
+                    const int sl = gbase + src;
+                    const int64_t qb = __shfl_sync(0xffffffffu, q0[r], sl);
+                    const int bl = __shfl_sync(0xffffffffu, blen[r], sl);
+                    const V avv = __shfl_sync(0xffffffffu, av[r], sl);
+                    bool dummy = true;
+                    const float2 a2 = MODE == MODE_DW ? dw_split((double)avv, dummy) : make_float2(0.f, 0.f);
+                    const int nch = __reduce_max_sync(0xffffffffu, (bl + G - 1) / G);
+                    for (int ch = 0; ch < nch; ch++) {
+                        const int off = ch * G + gl;
+                        if (off < bl) {
+                            const int64_t q = qb + off;
+                            const int slot = map_slot(keys, L, a.bcol[q]);
+                            if (slot >= 0) acc_update<MODE>(acc, slot, nat, a.bval, a.bsplit, q, avv, a2);
+                            else flag |= DERR_PROBE;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        // compact the occupied slots of each row to the front (read all, then write)
+        int kq[PER];
+        Slot vq[PER];
+#pragma unroll
+        for (int t = 0; t < PER; t++) {
+            const int sidx = gl + t * G;
+            kq[t] = sidx < S ? keys[sidx] : -1;
+            vq[t] = sidx < S ? acc[sidx] : Slot(0);
+        }
+        __syncwarp();
+        int cnt = 0;
+        const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
+#pragma unroll
+        for (int t = 0; t < PER; t++) {
+            const bool occ = kq[t] != -1;
+            const unsigned m = (__ballot_sync(0xffffffffu, occ) >> gbase) & lmask;
+            if (occ) {
+                const int pos = cnt + __popc(m & ((1u << gl) - 1));
+                keys[pos] = kq[t];
+                acc[pos] = vq[t];
+            }
+            cnt += __popc(m);
+        }
+        __syncwarp();
+        if (active && cnt != nn) {
+            flag |= DERR_COUNT;
+            cnt = min(cnt, nn);
+        }
+        if (!active) cnt = 0;
+        // rank by counting smaller keys; write each row in ascending order
+        for (int e = gl; e < cnt; e += G) {
+            const int key = keys[e];
+            int r = 0;
+            for (int u = 0; u < cnt; u++) r += keys[u] < key;
+            a.ccol[out + r] = key;
+            store_out<MODE>(a.cval, out + r, acc[e], nat);
+        }
+        __syncwarp();
+    }
+    if (flag) atomicOr(err, flag);
+}
+
+// Bitonic sort of P (power of two) keys with values in shared memory by NT
+// cooperating threads; sync() separates the stages.
 template <typename V, typename Sync>
 __device__ __forceinline__ void bitonic(int *k, V *v, int P, int tid, int NT, Sync sync) {
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int t = tid; t < P / 2; t += NT) {
-                int lo = 2 * t - (t & (stride - 1));
-                int hi = lo + stride;
-                bool asc = (lo & size) == 0;
-                int a = k[lo], b = k[hi];
-                if ((a > b) == asc) {
-                    k[lo] = b;
-                    k[hi] = a;
-                    V tv = v[lo];
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const int x = k[lo], y = k[hi];
+                if ((x > y) == asc) {
+                    k[lo] = y;
+                    k[hi] = x;
+                    const V tv = v[lo];
                     v[lo] = v[hi];
                     v[hi] = tv;
                 }
@@ -64,95 +261,119 @@ __device__ __forceinline__ void bitonic(int *k, V *v, int P, int tid, int NT, Sy
     }
 }
 
-__device__ __forceinline__ int next_pow2(int n) { return n <= 1 ? 1 : 1 << (32 - __clz(n - 1)); }
-
-// G lanes per row, S map slots, S/2 compacted entries.  RANK selects
-// ranking by counting (cheap for a handful of entries) over bitonic sorting.
-template <int G, int S, bool RANK, typename V>
-__global__ void __launch_bounds__(256) k_num_group(
-    const int64_t *__restrict__ arp, const int32_t *__restrict__ acol, const V *__restrict__ aval,
-    const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, const V *__restrict__ bval,
-    const int64_t *__restrict__ crp, int32_t *__restrict__ ccol, V *__restrict__ cval,
-    const int32_t *__restrict__ rows, int64_t count, int *err) {
-    constexpr int GPB = 256 / G;
-    constexpr int L = __builtin_ctz(S);
+// Bin 3: a warp per listed row, map of up to 256 slots, bitonic output sort.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_num_warp(NumP a, const int32_t *__restrict__ rows,
+                                                  int64_t count, const DevState *st, int *err) {
+    constexpr int SMAX = 256, WPB = 8, PER = SMAX / 32;
+    using Slot = SlotT<MODE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *vals_all = (V *)smem_raw;                                   // GPB*S
-    V *cv_all = vals_all + GPB * S;                                // GPB*S/2
-    int *keys_all = (int *)(cv_all + GPB * S / 2);                 // GPB*S
-    int *ck_all = keys_all + GPB * S;                              // GPB*S/2
-    const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    int *keys = keys_all + g * S;
-    V *vals = vals_all + g * S;
-    int *ck = ck_all + g * (S / 2);
-    V *cv = cv_all + g * (S / 2);
-    const int gbase = (threadIdx.x & 31) & ~(G - 1);
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1) << gbase);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Slot *acc = (Slot *)smem_raw + w * SMAX;
+    int *keys = (int *)((Slot *)smem_raw + WPB * SMAX) + w * SMAX;
+    const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
     int flag = 0;
-    for (int64_t t = (int64_t)blockIdx.x * GPB + g; t < count; t += (int64_t)gridDim.x * GPB) {
+    for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
-        for (int s = lane; s < S; s += G) {
+        const int64_t out = a.crp[i];
+        const int nn = (int)(a.crp[i + 1] - out);
+        int S = next_pow2(2 * nn);
+        S = S < 32 ? 32 : (S > SMAX ? SMAX : S);
+        const int L = __ffs(S) - 1;
+        for (int s = lane; s < S; s += 32) {
             keys[s] = -1;
-            vals[s] = V(0);
+            acc[s] = Slot(0);
         }
-        __syncwarp(gmask);
-        const int64_t pe = arp[i + 1];
-        for (int64_t p = arp[i] + lane; p < pe; p += G) {
-            const int k = acol[p];
-            const V a = aval[p];
-            const int64_t q1 = brp[k + 1];
-            for (int64_t q = brp[k]; q < q1; q++) {
-                if (!num_insert<V>(keys, vals, L, S, bcol[q], a * bval[q])) flag |= DERR_PROBE;
-            }
+        const int64_t p0 = a.arp[i], pe = a.arp[i + 1];
+        bool nat = MODE == MODE_F64 || b_bad;
+        if (MODE == MODE_DW && !nat) {
+            bool ok = true;
+            for (int64_t p = p0 + lane; p < pe; p += 32) dw_split(((const double *)a.aval)[p], ok);
+            nat = !__all_sync(0xffffffffu, ok);
         }
-        __syncwarp(gmask);
-        // Compact the occupied slots (slot order).
-        int n = 0;
-        for (int s0 = 0; s0 < S; s0 += G) {
-            int s = s0 + lane;
-            int key = keys[s];
-            bool occ = key != -1;
-            unsigned b = __ballot_sync(gmask, occ) >> gbase;
-            if (occ) {
-                int pos = n + __popc(b & ((1u << lane) - 1));
-                if (pos < S / 2) {
-                    ck[pos] = key;
-                    cv[pos] = vals[s];
+        __syncwarp();
+        for (int64_t p = p0; p < pe; p++) {
+            const int k = a.acol[p];
+            const ValT<MODE> av = load_a<MODE>(a.aval, p);
+            bool dummy = true;
+            const float2 a2 = MODE == MODE_DW ? dw_split((double)av, dummy) : make_float2(0.f, 0.f);
+            const int64_t q1 = a.brp[k + 1];
+            for (int64_t q = a.brp[k] + lane; q - lane < q1; q += 32) {
+                if (q < q1) {
+                    const int slot = map_slot(keys, L, a.bcol[q]);
+                    if (slot >= 0) acc_update<MODE>(acc, slot, nat, a.bval, a.bsplit, q, av, a2);
+                    else flag |= DERR_PROBE;
                 }
             }
-            n += __popc(b);
+            __syncwarp();
         }
-        const int64_t out = crp[i];
-        const int expect = (int)(crp[i + 1] - out);
-        if (n != expect) {
+        int kk[PER];
+        Slot vv[PER];
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int s = lane + u * 32;
+            kk[u] = s < S ? keys[s] : -1;
+            vv[u] = s < S ? acc[s] : Slot(0);
+        }
+        __syncwarp();
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const bool occ = kk[u] != -1;
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
+            if (occ) {
+                const int pos = cnt + __popc(m & ((1u << lane) - 1));
+                keys[pos] = kk[u];
+                acc[pos] = vv[u];
+            }
+            cnt += __popc(m);
+        }
+        if (cnt != nn) {
             flag |= DERR_COUNT;
-            n = min(min(n, expect), S / 2);
+            cnt = min(cnt, nn);
         }
-        __syncwarp(gmask);
-        if (RANK) {
-            for (int e = lane; e < n; e += G) {
-                int key = ck[e];
-                int r = 0;
-                for (int u = 0; u < n; u++) r += ck[u] < key;
-                ccol[out + r] = key;
-                cval[out + r] = cv[e];
-            }
-        } else {
-            int P = next_pow2(n);
-            for (int e = n + lane; e < P; e += G) ck[e] = INT_MAX;
-            __syncwarp(gmask);
-            bitonic<V>(ck, cv, P, lane, G, [&] { __syncwarp(gmask); });
-            for (int e = lane; e < n; e += G) {
-                ccol[out + e] = ck[e];
-                cval[out + e] = cv[e];
-            }
+        const int P = next_pow2(cnt);
+        for (int e = cnt + lane; e < P; e += 32) keys[e] = INT_MAX;
+        __syncwarp();
+        bitonic<Slot>(keys, acc, P, lane, 32, [] { __syncwarp(); });
+        for (int e = lane; e < cnt; e += 32) {
+            a.ccol[out + e] = keys[e];
+            store_out<MODE>(a.cval, out + e, acc[e], nat);
         }
-        __syncwarp(gmask);
+        __syncwarp();
     }
     if (flag) atomicOr(err, flag);
 }
 
-// A whole block per row, map of S slots in shared memory.
+// ------------------------------------------------------------------ block kernels
+// Insert (col, v) with atomic accumulation into a map of 2^L slots; false
+// when `limit` probes found neither the key nor a free slot.
+template <typename V>
+__device__ __forceinline__ bool map_add(int *keys, V *vals, int L, int limit, int col, V v) {
+    const unsigned msk = (1u << L) - 1;
+    unsigned h = hash_slot(col, L);
+#pragma unroll 1
+    for (int probe = 0; probe < limit; probe++) {
+        int k = ((volatile int *)keys)[h];
+        if (k == col) {
+            atomicAdd(&vals[h], v);
+            return true;
+        }
+        if (k == -1) {
+            int old = atomicCAS(&keys[h], -1, col);
+            if (old == -1 || old == col) {
+                atomicAdd(&vals[h], v);
+                return true;
+            }
+        }
+        h = (h + 1) & msk;
+    }
+    return false;
+}
+
+// Bins 4-5: a block per listed row, map of S slots in shared memory; warps
+// take stored a_ik in turn and their lanes walk B_k; atomic accumulation in
+// the value type (FP64 rows accumulate natively).
 template <int BS, int S, typename V>
 __global__ void __launch_bounds__(BS) k_num_block(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol, const V *__restrict__ aval,
@@ -179,22 +400,21 @@ __global__ void __launch_bounds__(BS) k_num_block(
         const int64_t pe = arp[i + 1];
         for (int64_t p = arp[i] + w; p < pe; p += BS / 32) {
             const int k = acol[p];
-            const V a = aval[p];
+            const V av = aval[p];
             const int64_t q1 = brp[k + 1];
-            for (int64_t q = brp[k] + lane; q < q1; q += 32) {
-                if (!num_insert<V>(keys, vals, L, S, bcol[q], a * bval[q])) flag |= DERR_PROBE;
-            }
+            for (int64_t q = brp[k] + lane; q < q1; q += 32)
+                if (!map_add<V>(keys, vals, L, S, bcol[q], av * bval[q])) flag |= DERR_PROBE;
         }
         __syncthreads();
         for (int s = threadIdx.x; s < S; s += BS) {
-            int key = keys[s];
-            bool occ = key != -1;
-            unsigned b = __ballot_sync(0xffffffffu, occ);
+            const int key = keys[s];
+            const bool occ = key != -1;
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
             int base = 0;
-            if (lane == 0 && b) base = atomicAdd(&nsh, __popc(b));
+            if (lane == 0 && m) base = atomicAdd(&nsh, __popc(m));
             base = __shfl_sync(0xffffffffu, base, 0);
             if (occ) {
-                int pos = base + __popc(b & ((1u << lane) - 1));
+                const int pos = base + __popc(m & ((1u << lane) - 1));
                 if (pos < S / 2) {
                     ck[pos] = key;
                     cv[pos] = vals[s];
@@ -209,7 +429,7 @@ __global__ void __launch_bounds__(BS) k_num_block(
             flag |= DERR_COUNT;
             n = min(min(n, expect), S / 2);
         }
-        int P = next_pow2(n);
+        const int P = next_pow2(n);
         for (int e = n + threadIdx.x; e < P; e += BS) ck[e] = INT_MAX;
         __syncthreads();
         bitonic<V>(ck, cv, P, threadIdx.x, BS, [] { __syncthreads(); });
@@ -222,11 +442,11 @@ __global__ void __launch_bounds__(BS) k_num_block(
     if (flag) atomicOr(err, flag);
 }
 
-// Largest rows: first-level map in shared memory (bounded probing), second
-// level in global memory sized for the row (Section 3.3); then the row's
-// columns are marked in a bitmap whose word prefix counts give every entry
-// its rank.  Global memory per block: L2 keys/values (l2cap slots), bitmap
-// and prefix (nwords words each); each row clears the L2 slots it uses.
+// Bin 6: first-level map in shared memory (bounded probing), second level in
+// global memory sized for the row (Section 3.3); the row's columns are then
+// marked in a bitmap whose word prefix counts give each entry its rank.
+// Global memory per block: L2 keys/values (l2cap slots), bitmap and prefix
+// (nwords words each); every row clears the L2 slots it uses.
 constexpr int HUGE_BS = 512, HUGE_L1 = 4096, HUGE_PROBES = 16;
 
 template <typename V>
@@ -273,36 +493,36 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
         const int64_t pe = arp[i + 1];
         for (int64_t p = arp[i] + w; p < pe; p += HUGE_BS / 32) {
             const int k = acol[p];
-            const V a = aval[p];
+            const V av = aval[p];
             const int64_t q1 = brp[k + 1];
             for (int64_t q = brp[k] + lane; q < q1; q += 32) {
                 const int c = bcol[q];
-                const V v = a * bval[q];
+                const V v = av * bval[q];
                 lmin = min(lmin, c);
                 lmax = max(lmax, c);
-                if (!num_insert<V>(keys, vals, L1, HUGE_PROBES, c, v))
-                    if (!num_insert<V>(g_keys, g_vals, L2, 1 << L2, c, v)) flag |= DERR_PROBE;
+                if (!map_add<V>(keys, vals, L1, HUGE_PROBES, c, v))
+                    if (!map_add<V>(g_keys, g_vals, L2, 1 << L2, c, v)) flag |= DERR_PROBE;
             }
         }
         atomicMin(&cmin, lmin);
         atomicMax(&cmax, lmax);
         __syncthreads();
         for (int s = threadIdx.x; s < HUGE_L1; s += HUGE_BS) {
-            int key = keys[s];
+            const int key = keys[s];
             if (key != -1)
-                if (!num_insert<V>(g_keys, g_vals, L2, 1 << L2, key, vals[s])) flag |= DERR_PROBE;
+                if (!map_add<V>(g_keys, g_vals, L2, 1 << L2, key, vals[s])) flag |= DERR_PROBE;
         }
-        const int64_t w0 = cmin >= 0 && cmin != INT_MAX ? (cmin >> 5) : 0;
-        const int64_t w1 = cmax >= 0 ? (cmax >> 5) + 1 : 0;
+        const int64_t w0 = (cmax >= 0) ? (cmin >> 5) : 0;
+        const int64_t w1 = (cmax >= 0) ? (cmax >> 5) + 1 : 0;
         for (int64_t x = w0 + threadIdx.x; x < w1; x += HUGE_BS) bits[x] = 0;
         __syncthreads();
         const int64_t slots = 1LL << L2;
         for (int64_t s = threadIdx.x; s < slots; s += HUGE_BS) {
-            int key = g_keys[s];
+            const int key = g_keys[s];
             if (key != -1) atomicOr(&bits[key >> 5], 1u << (key & 31));
         }
         __syncthreads();
-        // word prefix: contiguous chunk per thread, block scan of chunk sums
+        // word prefix: a contiguous chunk per thread, block scan of chunk sums
         const int64_t nw = w1 - w0;
         const int64_t chunk = (nw + HUGE_BS - 1) / HUGE_BS;
         const int64_t c0 = w0 + threadIdx.x * chunk;
@@ -311,15 +531,16 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
         for (int64_t x = c0; x < c1; x++) sum += __popc(bits[x]);
         long long incl = sum;
         for (int d = 1; d < 32; d <<= 1) {
-            long long tt = __shfl_up_sync(0xffffffffu, incl, d);
+            const long long tt = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += tt;
         }
         if (lane == 31) red[w] = incl;
         __syncthreads();
         if (w == 0) {
-            long long v = lane < HUGE_BS / 32 ? red[lane] : 0, vi = v;
+            const long long v = lane < HUGE_BS / 32 ? red[lane] : 0;
+            long long vi = v;
             for (int d = 1; d < 32; d <<= 1) {
-                long long tt = __shfl_up_sync(0xffffffffu, vi, d);
+                const long long tt = __shfl_up_sync(0xffffffffu, vi, d);
                 if (lane >= d) vi += tt;
             }
             if (lane < HUGE_BS / 32) red[lane] = vi - v;
@@ -332,10 +553,10 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
         }
         __syncthreads();
         for (int64_t s = threadIdx.x; s < slots; s += HUGE_BS) {
-            int key = g_keys[s];
+            const int key = g_keys[s];
             if (key != -1) {
-                int64_t x = key >> 5;
-                int64_t r = (int64_t)pref[x] + __popc(bits[x] & ((1u << (key & 31)) - 1));
+                const int64_t x = key >> 5;
+                const int64_t r = (int64_t)pref[x] + __popc(bits[x] & ((1u << (key & 31)) - 1));
                 if (r < expect) {
                     ccol[out + r] = key;
                     cval[out + r] = g_vals[s];
@@ -349,8 +570,7 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
     if (flag) atomicOr(err, flag);
 }
 
-// Opt in to the dynamic shared memory a launch needs (static shared memory
-// comes on top, so the attribute is set for every non-trivial size).
+// ------------------------------------------------------------------ host side
 template <typename K>
 static int prep(K kern, size_t smem) {
     if (smem > 16 * 1024)
@@ -358,41 +578,57 @@ static int prep(K kern, size_t smem) {
     return SPGEMM_OK;
 }
 
-template <typename V>
-struct NumArgs {
-    const int64_t *arp; const int32_t *acol; const V *aval;
-    const int64_t *brp; const int32_t *bcol; const V *bval;
-    const int64_t *crp; int32_t *ccol; V *cval;
-};
-
-static const char *NUM_LABEL[NBINS] = {"", "numeric.bin1", "numeric.bin2", "numeric.bin3",
+static const char *NUM_LABEL[NBINS] = {"", "numeric.small", "numeric.small", "numeric.bin3",
                                        "numeric.bin4", "numeric.bin5", "numeric.bin6", ""};
 
-template <int G, int S, bool RANK, typename V>
-static int run_group(const NumArgs<V> &a, const int32_t *rows, int64_t count, int *err, int b,
-                     Ctx &c) {
-    constexpr int GPB = 256 / G;
-    size_t smem = (size_t)GPB * S * (sizeof(V) + 4) * 3 / 2;
-    SG_TRY(prep(k_num_group<G, S, RANK, V>, smem));
-    int64_t blocks = (count + GPB - 1) / GPB;
-    blocks = blocks < (int64_t)c.nsm * 64 ? blocks : (int64_t)c.nsm * 64;
-    c.begin(NUM_LABEL[b], count);
-    k_num_group<G, S, RANK, V><<<(unsigned)blocks, 256, smem, c.s>>>(
-        a.arp, a.acol, a.aval, a.brp, a.bcol, a.bval, a.crp, a.ccol, a.cval, rows, count, err);
+template <int G, int MODE>
+static int run_small(const NumP &a, int64_t n, const uint8_t *bins, DevState *st, int *err, Ctx &c) {
+    constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
+    const size_t smem = (size_t)GPB * 64 * (sizeof(SlotT<MODE>) + 4);
+    SG_TRY(prep(k_num_small<G, MODE>, smem));
+    int64_t blocks = (n + GPB - 1) / GPB;
+    const int64_t cap = (int64_t)c.nsm * 32;
+    blocks = blocks < cap ? blocks : cap;
+    c.begin("numeric.small", n);
+    k_num_small<G, MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, n, bins, st, err);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+template <int MODE>
+static int run_small_g(int G, const NumP &a, int64_t n, const uint8_t *bins, DevState *st, int *err,
+                       Ctx &c) {
+    switch (G) {
+        case 4: return run_small<4, MODE>(a, n, bins, st, err, c);
+        case 8: return run_small<8, MODE>(a, n, bins, st, err, c);
+        case 16: return run_small<16, MODE>(a, n, bins, st, err, c);
+        default: return run_small<32, MODE>(a, n, bins, st, err, c);
+    }
+}
+
+template <int MODE>
+static int run_warp(const NumP &a, const int32_t *rows, int64_t count, DevState *st, int *err, Ctx &c) {
+    const size_t smem = (size_t)8 * 256 * (sizeof(SlotT<MODE>) + 4);
+    SG_TRY(prep(k_num_warp<MODE>, smem));
+    int64_t blocks = (count + 7) / 8;
+    blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
+    c.begin("numeric.bin3", count);
+    k_num_warp<MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, rows, count, st, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
 }
 
 template <int BS, int S, typename V>
-static int run_block(const NumArgs<V> &a, const int32_t *rows, int64_t count, int *err, int b,
-                     Ctx &c) {
-    size_t smem = (size_t)S * (sizeof(V) + 4) * 3 / 2;
+static int run_block(const NumP &a, const int32_t *rows, int64_t count, int *err, int b, Ctx &c) {
+    const size_t smem = (size_t)S * (sizeof(V) + 4) * 3 / 2;
     SG_TRY(prep(k_num_block<BS, S, V>, smem));
     int64_t blocks = count < (int64_t)c.nsm * 16 ? count : (int64_t)c.nsm * 16;
     c.begin(NUM_LABEL[b], count);
     k_num_block<BS, S, V><<<(unsigned)blocks, BS, smem, c.s>>>(
-        a.arp, a.acol, a.aval, a.brp, a.bcol, a.bval, a.crp, a.ccol, a.cval, rows, count, err);
+        a.arp, a.acol, (const V *)a.aval, a.brp, a.bcol, (const V *)a.bval, a.crp, a.ccol,
+        (V *)a.cval, rows, count, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -405,64 +641,76 @@ static int64_t huge_l2cap(int64_t max_row_nnz) {
 }
 
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype) {
-    int64_t l2 = huge_l2cap(max_row_nnz);
-    int64_t nwords = (ncols_b + 31) / 32;
-    size_t vb = dtype == SPGEMM_F64 ? 8 : 4;
+    const int64_t l2 = huge_l2cap(max_row_nnz);
+    const int64_t nwords = (ncols_b + 31) / 32;
+    const size_t vb = dtype == SPGEMM_F64 ? 8 : 4;
     return ((size_t)l2 * (4 + vb) + (size_t)nwords * 8) * (size_t)nsm;
 }
 
 template <typename V>
-static int run_all(const NumArgs<V> &a, const spgemm_csr &B, const int32_t *rows,
-                   const long long *counts, int *err, void *gws, size_t gws_bytes,
-                   int64_t max_row_nnz, Ctx &c) {
-    const int nsm = c.nsm;
+static int run_huge(const NumP &a, const spgemm_csr &B, const int32_t *rows, int64_t cnt, int *err,
+                    void *gws, size_t gws_bytes, int64_t max_row_nnz, Ctx &c) {
+    const int64_t l2 = huge_l2cap(max_row_nnz);
+    const int64_t nwords = (B.ncols + 31) / 32;
+    const int64_t blocks = cnt < (int64_t)c.nsm ? cnt : (int64_t)c.nsm;
+    const size_t need = ((size_t)l2 * (4 + sizeof(V)) + (size_t)nwords * 8) * (size_t)blocks;
+    if (need > gws_bytes) {
+        set_error("numeric: global map workspace too small");
+        return SPGEMM_ERR_INTERNAL;
+    }
+    const size_t smem = (size_t)HUGE_L1 * (sizeof(V) + 4);
+    SG_TRY(prep(k_num_huge<V>, smem));
+    c.begin("numeric.bin6", cnt);
+    k_num_huge<V><<<(unsigned)blocks, HUGE_BS, smem, c.s>>>(
+        a.arp, a.acol, (const V *)a.aval, a.brp, a.bcol, (const V *)a.bval, a.crp, a.ccol, (V *)a.cval,
+        rows, cnt, err, l2, nwords, (unsigned char *)gws);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+template <int MODE>
+static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
+                   const int32_t *rows, const long long *counts, DevState *st, void *gws,
+                   size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
+    using V = typename std::conditional<MODE == MODE_F32, float, double>::type;
+    int *err = &st->err;
+    if (counts[1] + counts[2] > 0) SG_TRY(run_small_g<MODE>(G, a, A.nrows, bins, st, err, c));
     int64_t off = 0;
-    for (int b = 1; b < NBINS; b++) {
-        int64_t cnt = counts[b];
+    for (int b = 3; b <= BIN_HUGE; b++) {
+        const int64_t cnt = counts[b];
         const int32_t *r = rows + off;
         off += cnt;
         if (cnt == 0) continue;
         switch (b) {
-            case 1: SG_TRY((run_group<8, 32, true, V>(a, r, cnt, err, b, c))); break;
-            case 2: SG_TRY((run_group<16, 128, false, V>(a, r, cnt, err, b, c))); break;
-            case 3: SG_TRY((run_group<32, 512, false, V>(a, r, cnt, err, b, c))); break;
+            case 3: SG_TRY(run_warp<MODE>(a, r, cnt, st, err, c)); break;
             case 4: SG_TRY((run_block<128, 2048, V>(a, r, cnt, err, b, c))); break;
             case 5: SG_TRY((run_block<256, 8192, V>(a, r, cnt, err, b, c))); break;
-            default: {
-                int64_t l2 = huge_l2cap(max_row_nnz);
-                int64_t nwords = (B.ncols + 31) / 32;
-                int64_t blocks = cnt < (int64_t)nsm ? cnt : (int64_t)nsm;
-                size_t need = ((size_t)l2 * (4 + sizeof(V)) + (size_t)nwords * 8) * (size_t)blocks;
-                if (need > gws_bytes) {
-                    set_error("numeric: global map workspace too small");
-                    return SPGEMM_ERR_INTERNAL;
-                }
-                size_t smem = (size_t)HUGE_L1 * (sizeof(V) + 4);
-                SG_TRY(prep(k_num_huge<V>, smem));
-                c.begin(NUM_LABEL[b], cnt);
-                k_num_huge<V><<<(unsigned)blocks, HUGE_BS, smem, c.s>>>(
-                    a.arp, a.acol, a.aval, a.brp, a.bcol, a.bval, a.crp, a.ccol, a.cval, r, cnt, err,
-                    l2, nwords, (unsigned char *)gws);
-                c.end();
-                SG_CUDA(cudaGetLastError());
-            }
+            default: SG_TRY(run_huge<V>(a, B, r, cnt, err, gws, gws_bytes, max_row_nnz, c));
         }
     }
     return SPGEMM_OK;
 }
 
-int launch_numeric(int dtype, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
-                   const int32_t *rows, const long long *counts, int *err, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, Ctx &c) {
-    if (dtype == SPGEMM_F64) {
-        NumArgs<double> a{A.row_ptr, A.col_idx, (const double *)A.values, B.row_ptr, B.col_idx,
-                          (const double *)B.values, C.row_ptr, C.col_idx, (double *)C.values};
-        return run_all<double>(a, B, rows, counts, err, gws, gws_bytes, max_row_nnz, c);
-    } else {
-        NumArgs<float> a{A.row_ptr, A.col_idx, (const float *)A.values, B.row_ptr, B.col_idx,
-                         (const float *)B.values, C.row_ptr, C.col_idx, (float *)C.values};
-        return run_all<float>(a, B, rows, counts, err, gws, gws_bytes, max_row_nnz, c);
+int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
+                   const uint8_t *bins, const int32_t *rows, const long long *counts, DevState *st,
+                   float2 *bsplit, void *gws, size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
+    NumP a{A.row_ptr, A.col_idx, A.values, B.row_ptr, B.col_idx, B.values, bsplit,
+           C.row_ptr, C.col_idx, C.values};
+    if (dtype == SPGEMM_F32)
+        return run_all<MODE_F32>(a, A, B, bins, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+    if (f64_native)
+        return run_all<MODE_F64>(a, A, B, bins, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+    SG_CUDA(cudaMemsetAsync(&st->b_out_of_range, 0, sizeof(int), c.s));
+    if (B.nnz > 0) {
+        int64_t blocks = (B.nnz + 255) / 256;
+        blocks = blocks < (int64_t)c.nsm * 16 ? blocks : (int64_t)c.nsm * 16;
+        c.begin("numeric.split_b", B.nnz);
+        k_split_values<<<(unsigned)blocks, 256, 0, c.s>>>(B.nnz, (const double *)B.values, bsplit, st);
+        c.end();
+        SG_CUDA(cudaGetLastError());
     }
+    return run_all<MODE_DW>(a, A, B, bins, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
 }
 
 }  // namespace sg

@@ -2,22 +2,27 @@
 // column set of B_k |, computed on compressed column sets: every set is a
 // list of (block = col/32, 32-bit mask) pairs, a union is a hash map from
 // block to the OR of its masks, and the count is the sum of popcounts
-// (Section 2.1, compression makes union a bitwise operation).  Rows are
-// binned by the number of keys their map can hold (Section 3.3): bins 1-3
-// give a group of 8, 16 or 32 lanes to a row, bins 4-5 a whole block with a
-// shared-memory map, bin 6 a block with a dense bitmap over all blocks of
-// columns (shared memory when it fits, otherwise global memory).
+// (Section 2.1: compression turns union into bitwise operations).
+//
+// Rows are sized by an upper bound on their distinct blocks.  A first pass
+// takes every row with bound <= 4096 in row order with a 32-slot map per
+// row and G lanes walking the pairs of each B_k; rows that do not fit are
+// marked and, with the rows whose bound exceeds 4096, handled by a second
+// pass from row lists: a warp with a 128- or 512-slot map (bins 2, 3), a
+// block with a 2048- or 8192-slot map (bins 4, 5), or a block with a dense
+// bitmap over all column blocks (bin 6; shared memory when it fits, global
+// memory otherwise).  Maps live in shared memory (Section 3.3).
 #include <climits>
 #include "internal.cuh"
 
 namespace sg {
 
-template <int S>
-__device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int blk, unsigned m) {
-    constexpr int L = __builtin_ctz(S);
+// Insert block `blk` with mask m into a map of 2^L slots; false if full.
+__device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int L, int blk, unsigned m) {
+    const unsigned msk = (1u << L) - 1;
     unsigned h = hash_slot(blk, L);
 #pragma unroll 1
-    for (int probe = 0; probe < S; probe++) {
+    for (int probe = 0; probe <= (int)msk; probe++) {
         int k = ((volatile int *)keys)[h];
         if (k == blk) {
             atomicOr(&masks[h], m);
@@ -30,50 +35,133 @@ __device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int blk, 
                 return true;
             }
         }
-        h = (h + 1) & (S - 1);
+        h = (h + 1) & msk;
     }
     return false;
 }
 
-// G lanes per row, S slots per row; each lane walks its share of the row's
-// stored a_ik (stride G) and inserts every compressed pair of B_k.
-template <int G, int S>
-__global__ void __launch_bounds__(256) k_sym_group(
+// First pass: a warp takes 32/G consecutive rows, G lanes per row, 32-slot
+// map per row.  The lanes of a warp stay converged (loops run to the
+// warp-wide maximum, idle lanes predicated off); the stored a_ik of a row are
+// loaded a batch at a time into registers and broadcast with shuffles.  A row
+// whose map fills up is marked crp[i+1] = -1 and counted in its second-pass
+// bin.
+template <int G>
+__global__ void __launch_bounds__(256) k_sym_first(
+    int64_t n, const uint8_t *__restrict__ bins, const int64_t *__restrict__ arp,
+    const int32_t *__restrict__ acol, const int64_t *__restrict__ brp,
+    const int32_t *__restrict__ ccnt, const int2 *__restrict__ pairs, int64_t *__restrict__ crp,
+    DevState *st) {
+    constexpr int S = SYM_FIRST_SLOTS, L = 5, RPW = 32 / G, WPB = 8, PER = S / G;
+    constexpr int R = (G >= 16 ? 2 : 32 / G);
+    __shared__ int keys_all[WPB * RPW * S];
+    __shared__ unsigned masks_all[WPB * RPW * S];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / G, gl = lane % G, gbase = g * G;
+    int *keys = keys_all + (w * RPW + g) * S;
+    unsigned *masks = masks_all + (w * RPW + g) * S;
+    const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
+    const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
+    for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
+        const int64_t i = base + g;
+        const int b = i < n ? bins[i] : 0;
+        const bool active = b != BIN_EMPTY && b != BIN_HUGE;
+        const int64_t p0 = active ? arp[i] : 0;
+        const int plen = active ? (int)(arp[i + 1] - p0) : 0;
+#pragma unroll
+        for (int t = 0; t < PER; t++) {
+            keys[gl + t * G] = -1;
+            masks[gl + t * G] = 0;
+        }
+        const int maxlen = __reduce_max_sync(0xffffffffu, plen);
+        __syncwarp();
+        bool fail = false;
+        for (int pb = 0; pb < maxlen; pb += G * R) {
+            int64_t q0[R];
+            int cn[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int p = pb + gl + G * r;
+                const int k = p < plen ? acol[p0 + p] : -1;
+                q0[r] = k >= 0 ? brp[k] : 0;
+                cn[r] = k >= 0 ? ccnt[k] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+#pragma unroll 1
+                for (int src = 0; src < G; src++) {
+                    if (pb + G * r + src >= maxlen) break;
+                    const int sl = gbase + src;
+                    const int64_t qb = __shfl_sync(0xffffffffu, q0[r], sl);
+                    const int c = __shfl_sync(0xffffffffu, cn[r], sl);
+                    const int nch = __reduce_max_sync(0xffffffffu, (c + G - 1) / G);
+                    for (int ch = 0; ch < nch; ch++) {
+                        const int off = ch * G + gl;
+                        if (off < c && !fail) {
+                            const int2 pr = pairs[qb + off];
+                            fail = !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
+                        }
+                    }
+                }
+            }
+            // a row whose map is full stops early (its group's lanes agree)
+            const unsigned fl = __ballot_sync(0xffffffffu, fail);
+            fail = ((fl >> gbase) & lmask) != 0;
+            if (__all_sync(0xffffffffu, fail || plen <= pb + G * R)) break;
+        }
+        __syncwarp();
+        int c = 0;
+#pragma unroll
+        for (int t = 0; t < PER; t++) c += __popc(masks[gl + t * G]);
+        for (int d = G / 2; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (active && gl == 0) {
+            if (fail) {
+                crp[i + 1] = -1;
+                atomicAdd((unsigned long long *)&st->bin_count[0][max(b, 2)], 1ull);
+            } else {
+                crp[i + 1] = c;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// A warp per row from a row list, S-slot map, lanes walk the pairs of B_k.
+template <int S>
+__global__ void __launch_bounds__(256) k_sym_warp(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
     int64_t *__restrict__ crp, int *err) {
-    constexpr int GPB = 256 / G;
+    constexpr int L = __builtin_ctz(S), WPB = 8;
     extern __shared__ int smem[];
-    const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    int *keys = smem + g * S;
-    unsigned *masks = (unsigned *)(smem + GPB * S) + g * S;
-    const unsigned gmask = (G == 32) ? 0xffffffffu
-                                     : (((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1)));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *keys = smem + w * S;
+    unsigned *masks = (unsigned *)(smem + WPB * S) + w * S;
     bool fail = false;
-    for (int64_t t = (int64_t)blockIdx.x * GPB + g; t < count; t += (int64_t)gridDim.x * GPB) {
+    for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
-        for (int s = lane; s < S; s += G) {
+        for (int s = lane; s < S; s += 32) {
             keys[s] = -1;
             masks[s] = 0;
         }
-        __syncwarp(gmask);
+        __syncwarp();
         const int64_t pe = arp[i + 1];
-        for (int64_t p = arp[i] + lane; p < pe; p += G) {
+        for (int64_t p = arp[i]; p < pe; p++) {
             const int k = acol[p];
             const int64_t q0 = brp[k];
-            const int n = ccnt[k];
-            for (int q = 0; q < n; q++) {
-                int2 pr = pairs[q0 + q];
-                fail |= !sym_insert<S>(keys, masks, pr.x, (unsigned)pr.y);
+            const int cnt = ccnt[k];
+            for (int u = lane; u < cnt; u += 32) {
+                const int2 pr = pairs[q0 + u];
+                fail |= !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
             }
         }
-        __syncwarp(gmask);
+        __syncwarp();
         int c = 0;
-        for (int s = lane; s < S; s += G) c += __popc(masks[s]);
-        for (int d = G / 2; d > 0; d >>= 1) c += __shfl_xor_sync(gmask, c, d, G);
+        for (int s = lane; s < S; s += 32) c += __popc(masks[s]);
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
         if (lane == 0) crp[i + 1] = c;
-        __syncwarp(gmask);
+        __syncwarp();
     }
     if (fail) atomicOr(err, DERR_PROBE);
 }
@@ -86,6 +174,7 @@ __global__ void __launch_bounds__(BS) k_sym_block(
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
     int64_t *__restrict__ crp, int *err) {
+    constexpr int L = __builtin_ctz(S);
     extern __shared__ int smem[];
     __shared__ int red[BS / 32];
     int *keys = smem;
@@ -106,7 +195,7 @@ __global__ void __launch_bounds__(BS) k_sym_block(
             const int n = ccnt[k];
             for (int q = lane; q < n; q += 32) {
                 int2 pr = pairs[q0 + q];
-                fail |= !sym_insert<S>(keys, masks, pr.x, (unsigned)pr.y);
+                fail |= !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
             }
         }
         __syncthreads();
@@ -183,20 +272,46 @@ static int prep(K kern, size_t smem) {
     return SPGEMM_OK;
 }
 
-static const char *SYM_LABEL[NBINS] = {"", "symbolic.bin1", "symbolic.bin2", "symbolic.bin3",
+template <int G>
+static int run_first(const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
+                     const int32_t *ccnt, const int2 *pairs, int64_t *crp, DevState *st, Ctx &c) {
+    constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
+    int64_t blocks = (A.nrows + GPB - 1) / GPB;
+    const int64_t cap = (int64_t)c.nsm * 8 * 4;
+    blocks = blocks < cap ? blocks : cap;
+    c.begin("symbolic.first", A.nrows);
+    k_sym_first<G><<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, bins, A.row_ptr, A.col_idx,
+                                                       B.row_ptr, ccnt, pairs, crp, st);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+int launch_symbolic_first(const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
+                          const int32_t *ccnt, const int2 *pairs, int64_t *crp, DevState *st,
+                          int G, Ctx &c) {
+    if (A.nrows == 0) return SPGEMM_OK;
+    switch (G) {
+        case 4: return run_first<4>(A, B, bins, ccnt, pairs, crp, st, c);
+        case 8: return run_first<8>(A, B, bins, ccnt, pairs, crp, st, c);
+        case 16: return run_first<16>(A, B, bins, ccnt, pairs, crp, st, c);
+        default: return run_first<32>(A, B, bins, ccnt, pairs, crp, st, c);
+    }
+}
+
+static const char *SYM_LABEL[NBINS] = {"", "", "symbolic.bin2", "symbolic.bin3",
                                        "symbolic.bin4", "symbolic.bin5", "symbolic.bin6", ""};
 
-template <int G, int S>
-static int run_group(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt, const int2 *pairs,
-                     const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c) {
-    constexpr int GPB = 256 / G;
-    size_t smem = (size_t)GPB * S * 8;
-    SG_TRY(prep(k_sym_group<G, S>, smem));
-    int64_t blocks = (count + GPB - 1) / GPB;
-    blocks = blocks < (int64_t)c.nsm * 64 ? blocks : (int64_t)c.nsm * 64;
+template <int S>
+static int run_warp(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt, const int2 *pairs,
+                    const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c) {
+    size_t smem = (size_t)8 * S * 8;
+    SG_TRY(prep(k_sym_warp<S>, smem));
+    int64_t blocks = (count + 7) / 8;
+    blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
     c.begin(SYM_LABEL[b], count);
-    k_sym_group<G, S><<<(unsigned)blocks, 256, smem, c.s>>>(A.row_ptr, A.col_idx, brp, ccnt, pairs,
-                                                             rows, count, crp, err);
+    k_sym_warp<S><<<(unsigned)blocks, 256, smem, c.s>>>(A.row_ptr, A.col_idx, brp, ccnt, pairs, rows,
+                                                         count, crp, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -222,22 +337,21 @@ int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
     const int nsm = c.nsm;
     int64_t off = 0;
     const int64_t *brp = B.row_ptr;
-    for (int b = 1; b < NBINS; b++) {
+    for (int b = 2; b <= BIN_HUGE; b++) {
         int64_t cnt = counts[b];
         const int32_t *r = rows + off;
         off += cnt;
         if (cnt == 0) continue;
         switch (b) {
-            case 1: SG_TRY((run_group<8, 32>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
-            case 2: SG_TRY((run_group<16, 128>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
-            case 3: SG_TRY((run_group<32, 512>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
+            case 2: SG_TRY((run_warp<128>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
+            case 3: SG_TRY((run_warp<512>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
             case 4: SG_TRY((run_block<128, 2048>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
             case 5: SG_TRY((run_block<256, 8192>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
             default: {
                 int64_t nwords = (B.ncols + 31) / 32;
                 bool shared = nwords <= SMEM_BITMAP_WORDS;
                 size_t smem = shared ? (size_t)nwords * 4 : 0;
-                SG_TRY(prep(k_sym_bitmap<BITMAP_BS>, shared ? smem : 0));
+                SG_TRY(prep(k_sym_bitmap<BITMAP_BS>, smem));
                 int64_t blocks = cnt < (int64_t)nsm ? cnt : (int64_t)nsm;
                 if (!shared && gws_bytes < (size_t)blocks * (size_t)nwords * 4) {
                     set_error("symbolic: global bitmap workspace too small");

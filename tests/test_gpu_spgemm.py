@@ -113,7 +113,7 @@ def test_every_bin_both_phases(h, ncols):
     """Rows sized to land in every bin (1..6) of both phases: the shared-memory
     maps, the global second-level map, and the shared (300k columns) or global
     (2M columns) symbolic bitmap."""
-    widths = [3, 12, 40, 150, 600, 2500, 9000, 30000]
+    widths = [3, 12, 25, 40, 150, 600, 2500, 9000, 30000]
     a = _spread_rows(widths, ncols, 5)
     eye = _eye(ncols)
     c = run(h, a, eye)
@@ -123,6 +123,43 @@ def test_every_bin_both_phases(h, ncols):
     assert all(sym[b] > 0 for b in range(1, 7)), sym
     c = run(h, a, eye, np.float32)
     assert_matches(c, oracle_product(a, eye, np.float32), "f32")
+    h.set_option(sg.OPT_F64_NATIVE, 1)
+    c = run(h, a, eye)
+    h.set_option(sg.OPT_F64_NATIVE, 0)
+    assert_matches(c, oracle.spgemm(a, eye), "f64")
+
+
+@pytest.mark.parametrize("native", [0, 1])
+@pytest.mark.parametrize("lanes", [0, 4, 8, 16, 32])
+def test_lane_options_galerkin(h, native, lanes):
+    """Every lanes-per-row choice and both FP64 accumulation modes."""
+    a, p, r = I.galerkin_problem(12)
+    h.set_option(sg.OPT_F64_NATIVE, native)
+    h.set_option(sg.OPT_LANES_NUMERIC, lanes)
+    h.set_option(sg.OPT_LANES_SYMBOLIC, lanes)
+    try:
+        for x, y in ((a, p), (r, a)):
+            c = run(h, x, y)
+            assert_matches(c, oracle.spgemm(x, y), "f64")
+    finally:
+        h.set_option(sg.OPT_F64_NATIVE, 0)
+        h.set_option(sg.OPT_LANES_NUMERIC, 0)
+        h.set_option(sg.OPT_LANES_SYMBOLIC, 0)
+
+
+def test_double_word_range_fallback(h):
+    """Values outside the double-word range (tiny, huge) take the native
+    path and still meet the FP64 tolerance; zeros are exact."""
+    a = I.random_csr(60, 50, 0.2, 31)
+    b = I.random_csr(50, 70, 0.2, 32)
+    av = a.val.copy()
+    av[::7] *= 1e-30      # below 2^-60: those rows go native
+    bv = b.val.copy()
+    for scale_b in (1.0, 1e25):   # 1e25 > 2^60: the whole call goes native
+        a2 = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, av)
+        b2 = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, bv * scale_b)
+        c = run(h, a2, b2)
+        assert_matches(c, oracle.spgemm(a2, b2), "f64")
 
 
 def test_heavy_rows_random(h):
@@ -149,9 +186,14 @@ def test_edge_cases(h):
     b1 = I.random_csr(30, 1, 0.6, 11)
     c = run(h, a, b1)
     assert_matches(c, oracle.spgemm(a, b1), "f64")
-    # A * I = A (sorted)
+    # A * I = A (sorted): exact in native FP64, within tolerance as double-words
     eye = I.Csr(30, 30, np.arange(31, dtype=np.int64), np.arange(30, dtype=np.int32), np.ones(30))
     c = run(h, a, eye)
+    assert np.array_equal(c.col.cpu().numpy(), a.col)
+    assert np.all(np.abs(c.val.cpu().numpy() - a.val) <= 1e-12 * np.abs(a.val))
+    h.set_option(sg.OPT_F64_NATIVE, 1)
+    c = run(h, a, eye)
+    h.set_option(sg.OPT_F64_NATIVE, 0)
     assert np.array_equal(c.col.cpu().numpy(), a.col) and np.array_equal(c.val.cpu().numpy(), a.val)
     # explicit zeros stay in the pattern
     az = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.zeros(a.nnz))
