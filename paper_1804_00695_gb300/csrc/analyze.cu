@@ -10,22 +10,28 @@ namespace sg {
 // 32-column block are merged into one (block, mask) pair (Section 2.1,
 // "compression ... encode multiple columns ... with fewer integers").  Rows
 // need not be sorted; a sorted row yields one pair per block, ascending.
+// The row's descriptors are written alongside: desc = {first entry (int64),
+// entries, pairs} for the product kernels and ana = {entries, pairs, first
+// block, last block} for the analysis, so each later visit of row k costs
+// one 16-byte load.
 __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
                            const int32_t *__restrict__ col, int2 *__restrict__ pairs,
-                           int32_t *__restrict__ ccnt, int2 *__restrict__ minmax, int *err) {
+                           int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
+                           int4 *__restrict__ desc, int4 *__restrict__ ana, int *err) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
-    int64_t beg = rp[r], end = rp[r + 1];
+    const int64_t beg = rp[r], end = rp[r + 1];
     int cur = -1;
     unsigned m = 0;
     int n = 0, bmin = INT_MAX, bmax = INT_MIN;
     bool bad = false;
     for (int64_t p = beg; p < end; p++) {
-        int c = col[p];
+        const int c = col[p];
         if (c < 0 || (int64_t)c >= ncols) { bad = true; continue; }
-        int b = c >> 5;
+        const int b = c >> 5;
         if (b != cur) {
-            if (cur >= 0) pairs[beg + n++] = make_int2(cur, (int)m);
+            if (cur >= 0 && pairs) pairs[beg + n] = make_int2(cur, (int)m);
+            if (cur >= 0) n++;
             cur = b;
             m = 0;
         }
@@ -33,19 +39,25 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
         bmin = min(bmin, b);
         bmax = max(bmax, b);
     }
-    if (cur >= 0) pairs[beg + n++] = make_int2(cur, (int)m);
-    ccnt[r] = n;
-    minmax[r] = make_int2(bmin, bmax);
+    if (cur >= 0) {
+        if (pairs) pairs[beg + n] = make_int2(cur, (int)m);
+        n++;
+    }
+    if (ccnt) ccnt[r] = n;
+    if (minmax) minmax[r] = make_int2(bmin, bmax);
+    const int len = (int)(end - beg);
+    if (desc) desc[r] = make_int4((int)(unsigned)(uint64_t)beg, (int)((uint64_t)beg >> 32), len, n);
+    if (ana) ana[r] = make_int4(len, n, bmin, bmax);
     if (bad) atomicOr(err, DERR_COL_RANGE);
 }
 
-int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int *err,
-                    Ctx &c) {
+int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
+                    int4 *ana, int *err, Ctx &c) {
     if (M.nrows == 0) return SPGEMM_OK;
     int64_t blocks = (M.nrows + 255) / 256;
     c.begin("compress", M.nrows);
     k_compress<<<(unsigned)blocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
-                                                    ccnt, minmax, err);
+                                                    ccnt, minmax, desc, ana, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -72,11 +84,12 @@ __device__ __forceinline__ void warp_hist(unsigned long long *hist, bool has, in
 constexpr int AN_G = 8;
 __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
                           const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
-                          const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
-                          const int2 *__restrict__ minmax, int64_t *__restrict__ flops,
+                          const int4 *__restrict__ ana, int64_t *__restrict__ flops,
                           uint8_t *__restrict__ bins, int64_t *__restrict__ crp, DevState *st) {
     __shared__ unsigned long long hist[NBINS];
+    __shared__ unsigned long long fsum;
     if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) fsum = 0;
     __syncthreads();
     const int lane = threadIdx.x % AN_G;
     const unsigned gmask = ((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1));
@@ -89,11 +102,11 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
         for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += AN_G) {
             int k = acol[p];
             if (k < 0 || (int64_t)k >= nrows_b) { bad = true; continue; }
-            f += brp[k + 1] - brp[k];
-            cp += ccnt[k];
-            int2 mm = minmax[k];
-            bmin = min(bmin, mm.x);
-            bmax = max(bmax, mm.y);
+            const int4 d = ana[k];
+            f += d.x;
+            cp += d.y;
+            bmin = min(bmin, d.z);
+            bmax = max(bmax, d.w);
         }
     }
     for (int d = AN_G / 2; d > 0; d >>= 1) {
@@ -117,7 +130,12 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
         if (b == BIN_HUGE) crp[i + 1] = -1;
     }
     warp_hist(hist, lead, b);
+    // products of the warp's rows (lane 0 of each group holds its row's count)
+    long long wf = lead ? f : 0;
+    for (int d = 16; d > 0; d >>= 1) wf += __shfl_xor_sync(0xffffffffu, wf, d);
+    if ((threadIdx.x & 31) == 0 && wf) atomicAdd(&fsum, (unsigned long long)wf);
     __syncthreads();
+    if (threadIdx.x == 0 && fsum) atomicAdd((unsigned long long *)&st->flops_total, fsum);
     if (threadIdx.x < NBINS && hist[threadIdx.x]) {
         atomicAdd((unsigned long long *)&st->sym_hist[threadIdx.x], hist[threadIdx.x]);
         if (threadIdx.x == BIN_HUGE)
@@ -125,16 +143,15 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
     }
 }
 
-int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int32_t *ccnt,
-                   const int2 *minmax, int64_t *flops, uint8_t *bins, int64_t *crp, DevState *st,
-                   Ctx &c) {
+int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int4 *ana, int64_t *flops,
+                   uint8_t *bins, int64_t *crp, DevState *st, Ctx &c) {
     if (A.nrows == 0) return SPGEMM_OK;
     int64_t threads = A.nrows * AN_G;
     int64_t blocks = (threads + 255) / 256;
     int64_t nwords = (B.ncols + 31) / 32;
     c.begin("analyze", A.nrows);
     k_analyze<<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, B.nrows, nwords, A.row_ptr, A.col_idx,
-                                                   B.row_ptr, ccnt, minmax, flops, bins, crp, st);
+                                                   ana, flops, bins, crp, st);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;

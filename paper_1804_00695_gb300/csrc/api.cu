@@ -71,7 +71,8 @@ struct spgemm_handle_s {
     bool num_lists = false;   // numeric row lists built for this symbolic result
     // options
     bool f64_native = false;
-    int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from B's row length)
+    int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from the mean products per row)
+    double mean_flops = 0;
     // launch counting and CUDA-event timing
     long long launches = 0;
     bool timing = false;
@@ -201,16 +202,19 @@ int spgemm_check(spgemm_handle h, void *stream) {
     return device_errors(err);
 }
 
-// Largest power of two <= x, clamped to [4, 32].
-static int lanes_for(double x) {
-    int g = 4;
+// Largest power of two <= x, clamped to [lo, 32].
+static int lanes_for(double x, int lo = 8) {
+    int g = lo;
     while (g < 32 && 2 * g <= x) g *= 2;
     return g;
 }
 
-// Workspace: [bins | rows] persist from symbolic to numeric; after them the
-// symbolic scratch, or (later) the numeric scratch, which may overlap it.
-static size_t ws_persist(int64_t n) { return align_up((size_t)n) + align_up((size_t)n * 4); }
+// Workspace: [bins | rows | B descriptors] persist from symbolic to numeric;
+// after them the symbolic scratch, or (later) the numeric scratch, which may
+// overlap it.
+static size_t ws_persist(int64_t n, int64_t nb) {
+    return align_up((size_t)n) + align_up((size_t)n * 4) + align_up((size_t)nb * 16);
+}
 
 int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *C_row_ptr,
                     int64_t *nnz_C, void *stream) {
@@ -235,7 +239,9 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
     } else {
         const size_t o_bins = 0;
         const size_t o_rows = align_up((size_t)n);
-        const size_t o_flops = ws_persist(n);
+        const size_t o_desc = o_rows + align_up((size_t)n * 4);
+        const size_t o_ana = ws_persist(n, B->nrows);
+        const size_t o_flops = o_ana + align_up((size_t)B->nrows * 16);
         const size_t o_pairs = o_flops + align_up((size_t)n * 8);
         const size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
         const size_t o_mm = o_ccnt + align_up((size_t)B->nrows * 4);
@@ -250,12 +256,16 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         int2 *pairs = (int2 *)(w + o_pairs);
         int32_t *ccnt = (int32_t *)(w + o_ccnt);
         int2 *minmax = (int2 *)(w + o_mm);
+        int4 *desc = (int4 *)(w + o_desc);
+        int4 *ana = (int4 *)(w + o_ana);
         Ctx c = h->ctx(s);
-        const int gs = h->g_symbolic ? h->g_symbolic
-                                     : lanes_for((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1) / 2.0);
-        SG_TRY(launch_compress(*B, pairs, ccnt, minmax, &h->dstate->err, c));
-        SG_TRY(launch_analyze(*A, *B, ccnt, minmax, flops, bins, C_row_ptr, h->dstate, c));
-        SG_TRY(launch_symbolic_first(*A, *B, bins, ccnt, pairs, C_row_ptr, h->dstate, gs, c));
+        // lanes per row from the mean number of compressed pairs a row visits
+        const double mean_pairs = (double)A->nnz / (double)n *
+                                  ((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1)) * 0.6;
+        const int gs = h->g_symbolic ? h->g_symbolic : lanes_for(mean_pairs / 8.0);
+        SG_TRY(launch_compress(*B, pairs, ccnt, minmax, desc, ana, &h->dstate->err, c));
+        SG_TRY(launch_analyze(*A, *B, ana, flops, bins, C_row_ptr, h->dstate, c));
+        SG_TRY(launch_symbolic_first(*A, bins, desc, pairs, C_row_ptr, h->dstate, gs, c));
         SG_TRY(fetch_state(h, s));
         SG_TRY(device_errors(h->hstate->err));
         long long second = 0;
@@ -275,6 +285,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         SG_TRY(fetch_state(h, s));
         SG_TRY(device_errors(h->hstate->err));
         *nnz_C = h->hstate->nnz;
+        h->mean_flops = (double)h->hstate->flops_total / (double)n;
         memcpy(h->num_counts, h->hstate->bin_count[1], sizeof(h->num_counts));
         h->max_row_nnz = h->hstate->max_row_nnz;
         h->num_gws = h->num_counts[BIN_HUGE]
@@ -282,8 +293,8 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
                          : 0;
         h->num_lists = false;
         // numeric scratch: B split into double-words, then the second-level maps
-        SG_TRY(ws_reserve(h, ws_persist(n) + align_up((size_t)B->nnz * 8) + h->num_gws, s,
-                          ws_persist(n)));
+        SG_TRY(ws_reserve(h, ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8) + h->num_gws, s,
+                          ws_persist(n, B->nrows)));
     }
     h->a_rp = A->row_ptr; h->a_col = A->col_idx; h->a_n = A->nrows; h->a_m = A->ncols;
     h->a_nnz = A->nnz;
@@ -315,8 +326,9 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     const int64_t n = A->nrows;
     uint8_t *bins = (uint8_t *)h->ws;
     int32_t *rows = (int32_t *)(h->ws + align_up((size_t)n));
-    float2 *bsplit = (float2 *)(h->ws + ws_persist(n));
-    char *gws = h->ws + ws_persist(n) + align_up((size_t)B->nnz * 8);
+    const int4 *bdesc = (const int4 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4));
+    float2 *bsplit = (float2 *)(h->ws + ws_persist(n, B->nrows));
+    char *gws = h->ws + ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
     long long listed = 0;
     for (int b = 3; b <= BIN_HUGE; b++) listed += h->num_counts[b];
@@ -324,10 +336,9 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
         SG_TRY(launch_scatter_bins(n, bins, C->row_ptr, rows, h->dstate, 1, c));
         h->num_lists = true;
     }
-    const int gn = h->g_numeric ? h->g_numeric
-                                : lanes_for((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1));
-    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, rows, h->num_counts, h->dstate,
-                          bsplit, gws, h->num_gws, h->max_row_nnz, gn, c);
+    const int gn = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 12.0);
+    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, rows, h->num_counts,
+                          h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, gn, c);
 }
 
 int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
@@ -369,7 +380,8 @@ int spgemm_compress(spgemm_handle h, const spgemm_csr *M, int32_t *count, uint32
     SG_TRY(ws_reserve(h, need, s));
     h->sym_valid = false;
     Ctx c = h->ctx(s);
-    SG_TRY(launch_compress(*M, (int2 *)pairs, count, (int2 *)h->ws, &h->dstate->err, c));
+    SG_TRY(launch_compress(*M, (int2 *)pairs, count, (int2 *)h->ws, nullptr, nullptr,
+                           &h->dstate->err, c));
     return SPGEMM_OK;
 }
 

@@ -11,8 +11,9 @@
 namespace sg {
 
 // Bounds for the emulated path: every non-zero input magnitude must lie in
-// [2^-60, 2^60] so that products, their low parts and sums stay normal floats.
-constexpr unsigned DW_EMIN = 1023 - 60, DW_EMAX = 1023 + 60;
+// [2^-32, 2^32) so that products, their low parts, the captured rounding
+// errors and sums of up to 2^20 terms stay normal floats.
+constexpr unsigned DW_EMIN = 1023 - 32, DW_EMAX = 1023 + 31;
 
 // Split a double into hi (its leading 24 significand bits, exact) and lo (the
 // remaining 29 bits rounded to a float), so x = hi + lo + e, |e| <= 2^-48 |x|.

@@ -39,6 +39,7 @@ struct DevState {          // lives in device memory, one per handle
     long long bin_count[2][SPGEMM_NBINS];   // [0] symbolic, [1] numeric
     long long bin_cursor[SPGEMM_NBINS];
     long long max_row_nnz;   // largest row of C (numeric binning)
+    long long flops_total;   // products of the whole product (analysis)
 };
 
 // ---------------------------------------------------------------- bins
@@ -114,17 +115,21 @@ struct Ctx {
 // analyze.cu
 // Compressed column sets (Section 2.1): pairs of row k sit at
 // pairs[M.row_ptr[k] .. M.row_ptr[k] + ccnt[k]), each {block, mask};
-// minmax[k] = {first block, last block} ({INT_MAX, INT_MIN} for empty rows).
-int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax,
-                    int *err, Ctx &c);
+// minmax[k] = {first block, last block} ({INT_MAX, INT_MIN} for empty rows);
+// desc[k] = {row_ptr[k] low, high 32 bits, entries, pairs};
+// ana[k] = {entries, pairs, first block, last block}.  Any output may be NULL.
+int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
+                    int4 *ana, int *err, Ctx &c);
+__device__ __forceinline__ int64_t desc_start(int4 d) {
+    return (int64_t)(((uint64_t)(unsigned)d.y << 32) | (uint64_t)(unsigned)d.x);
+}
 size_t scan_tmp_bytes(int64_t n);
 // x[0..n] holds counts in x[1..n]; on return x is the exclusive prefix
 // (x[0] = 0); *total (device) = x[n].
 int launch_scan_counts(int64_t *x, int64_t n, long long *total, void *tmp, Ctx &c);
 // Per row i of A: flops, symbolic bin; empty rows get crp[i+1] = 0.
-int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int32_t *ccnt,
-                   const int2 *minmax, int64_t *flops, uint8_t *bins, int64_t *crp,
-                   DevState *st, Ctx &c);
+int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int4 *ana, int64_t *flops,
+                   uint8_t *bins, int64_t *crp, DevState *st, Ctx &c);
 // Numeric bin of every row from its output count crp[i+1]-crp[i] and flops.
 int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, uint8_t *bins,
                            DevState *st, Ctx &c);
@@ -136,9 +141,8 @@ int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, i
 
 // symbolic.cu
 // First pass over all rows with a 32-slot map and G lanes per row.
-int launch_symbolic_first(const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
-                          const int32_t *ccnt, const int2 *pairs, int64_t *crp, DevState *st,
-                          int G, Ctx &c);
+int launch_symbolic_first(const spgemm_csr &A, const uint8_t *bins, const int4 *desc,
+                          const int2 *pairs, int64_t *crp, DevState *st, int G, Ctx &c);
 // Second pass: kernels of bins 2..6; counts[b] = rows in bin b (host),
 // rows = concatenated bin lists.  Writes nnz(C_i) to crp[i+1].
 int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
@@ -151,9 +155,9 @@ size_t symbolic_global_ws(int64_t ncols_b, int nsm);
 // 3..6 from the row lists (counts[b] rows in bin b, host).  FP64 uses
 // double-word accumulation unless f64_native; bsplit: room for nnz(B) float2.
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B,
-                   spgemm_csr &C, const uint8_t *bins, const int32_t *rows, const long long *counts,
-                   DevState *st, float2 *bsplit, void *gws, size_t gws_bytes, int64_t max_row_nnz,
-                   int G, Ctx &c);
+                   spgemm_csr &C, const uint8_t *bins, const int4 *bdesc, const int32_t *rows,
+                   const long long *counts, DevState *st, float2 *bsplit, void *gws,
+                   size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c);
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype);
 
 }  // namespace sg

@@ -101,136 +101,259 @@ __device__ __forceinline__ ValT<MODE> load_a(const void *aval, int64_t p) {
     return ((const ValT<MODE> *)aval)[p];
 }
 
+// Three-level accumulation of a double-word product p into a slot held by
+// one thread: the high float takes p.x and its exact rounding error (TwoSum)
+// joins p.y; that sum goes to the second float the same way; the last, tiny
+// residue is added to a third float.  Every rounding of the first two levels
+// is recovered exactly, so an entry with n terms ends within
+// (6 + n^3 2^-24) 2^-48 sum|a_ik||b_kj| of the exact sum, product errors
+// included, in any order of the updates.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void acc3_add(float &hi, float &lo, float &lo2, float2 p) {
+    float s1, e1, t, f, s2, e2;
+    two_sum(hi, p.x, s1, e1);
+    two_sum(e1, p.y, t, f);
+    two_sum(lo, t, s2, e2);
+    hi = s1;
+    lo = s2;
+    lo2 = __fadd_rn(lo2, __fadd_rn(e2, f));
+}
+
+// Final value of a three-level slot as a double.
+__device__ __forceinline__ double dw3_to_double(float hi, float lo, float lo2) {
+    float s, e;
+    two_sum(hi, __fadd_rn(lo, lo2), s, e);
+    return dw_to_double(s, e);
+}
+
+// Adds one product to a slot held by this thread.  FP32: px.  Double-word:
+// (px, py); rows with at most DW2_MAX_TERMS stored a_ik (so at most that many
+// terms per entry) use the two-float accumulate dw_add, whose error stays
+// within (7 + 5n) 2^-48 sum|a||b| <= 1e-12 sum|a||b|; longer rows use the
+// three-level acc3_add.  Native FP64: (px, py) are the low and high words of
+// the product, and the slot keeps a double's words in hi and lo.
+constexpr int DW2_MAX_TERMS = 48;
+
+template <int MODE>
+__device__ __forceinline__ void acc_slot(float *hi, float *lo, float *lo2, int slot, bool nat,
+                                         bool three, float px, float py) {
+    if (MODE == MODE_F32) {
+        hi[slot] += px;
+    } else if (MODE == MODE_DW && !nat) {
+        if (three) {
+            acc3_add(hi[slot], lo[slot], lo2[slot], make_float2(px, py));
+        } else {
+            const float2 r = dw_add(make_float2(hi[slot], lo[slot]), make_float2(px, py));
+            hi[slot] = r.x;
+            lo[slot] = r.y;
+        }
+    } else {
+        const double v = __hiloint2double(__float_as_int(lo[slot]), __float_as_int(hi[slot])) +
+                         __hiloint2double(__float_as_int(py), __float_as_int(px));
+        hi[slot] = __int_as_float(__double2loint(v));
+        lo[slot] = __int_as_float(__double2hiint(v));
+    }
+}
+
 // Bins 1-2: a warp takes 32/G consecutive rows, G lanes per row, map of up
-// to 64 slots per row.  All lanes of the warp stay converged: the loops run
-// to the warp-wide maximum (row length, chunks of the current B row) and
-// idle lanes are predicated off, so the rows of a warp advance in lockstep.
-// The stored a_ik of a row are loaded a batch at a time into registers
-// (entry p held by lane p % G, slot p / G) and broadcast with shuffles, so
-// only the loads of B_k sit on the path of each step.
+// to 64 slots per row.  The products of a row are dealt out evenly: the
+// stored a_ik are staged E at a time in shared memory with the prefix sums
+// of nnz(B_k), and in each step the G lanes take G consecutive products
+// (lane l the t-th, t = step*G + l), finding their a_ik with a cursor that
+// only moves forward.  Loads of B stay coalesced within each B_k.  Lanes of
+// a row that hold the same column in a step are merged with
+// __match_any_sync and only the lowest of them updates the slot, adding
+// the others' products one by one, so every slot has a single writer per
+// step and no atomics are needed; all lanes of the warp stay converged.
 template <int G, int MODE>
-__global__ void __launch_bounds__(256) k_num_small(NumP a, int64_t n, const uint8_t *__restrict__ bins,
+__global__ void __launch_bounds__(256) k_num_small(NumP a, const int4 *__restrict__ bdesc, int64_t n,
+                                                   const uint8_t *__restrict__ bins,
                                                    const DevState *st, int *err) {
-    constexpr int SMAX = 64, RPW = 32 / G, WPB = 8, PER = SMAX / G, R = (G >= 16 ? 2 : 32 / G);
-    using Slot = SlotT<MODE>;
+    constexpr int SMAX = 64, RPW = 32 / G, WPB = 8, PER = SMAX / G;
+    constexpr int E = 32, EL = E / G;   // entries staged per batch, per lane
     using V = ValT<MODE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / G, gl = lane % G, gbase = g * G;
-    Slot *acc = (Slot *)smem_raw + (w * RPW + g) * SMAX;
-    int *keys = (int *)((Slot *)smem_raw + WPB * RPW * SMAX) + (w * RPW + g) * SMAX;
+    const int rs = w * RPW + g;   // row slot in the block
+    constexpr int NR = WPB * RPW;
+    // layout (per row slot): hi[SMAX] lo[SMAX] lo2[SMAX] keys[SMAX] | eq0[E] ea[E] | pre[E+1]
+    float *hi = (float *)smem_raw + rs * SMAX;
+    float *lo = (float *)smem_raw + NR * SMAX + rs * SMAX;
+    float *lo2 = (float *)smem_raw + 2 * NR * SMAX + rs * SMAX;
+    int *keys = (int *)smem_raw + 3 * NR * SMAX + rs * SMAX;
+    long long *eq0 = (long long *)((int *)smem_raw + 4 * NR * SMAX) + rs * E;
+    double *ea = (double *)((long long *)((int *)smem_raw + 4 * NR * SMAX) + NR * E) + rs * E;
+    int *pre = (int *)((double *)((long long *)((int *)smem_raw + 4 * NR * SMAX) + NR * E) + NR * E) +
+               rs * (E + 1);
+    // native FP64 rows keep a double's low word in hi[] and its high word in lo[]
+    const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
     const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
     int flag = 0;
     const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
         const int64_t i = base + g;
-        int bi = i < n ? bins[i] : 0;
+        const int bi = i < n ? bins[i] : 0;
         const bool active = bi == 1 || bi == 2;
         const int64_t p0 = active ? a.arp[i] : 0;
         const int plen = active ? (int)(a.arp[i + 1] - p0) : 0;
         const int64_t out = active ? a.crp[i] : 0;
         const int nn = active ? (int)(a.crp[i + 1] - out) : 0;
         int S = next_pow2(2 * nn);
-        S = S < G ? G : (S > SMAX ? SMAX : S);
+        S = S < 8 ? 8 : (S > SMAX ? SMAX : S);
         const int L = __ffs(S) - 1;
 #pragma unroll
         for (int t = 0; t < PER; t++) {
             const int sidx = gl + t * G;
-            if (sidx < S) {
-                keys[sidx] = -1;
-                acc[sidx] = Slot(0);
-            }
+            keys[sidx] = -1;
+            hi[sidx] = 0.f;
+            lo[sidx] = 0.f;
+            lo2[sidx] = 0.f;
         }
-        const int maxlen = __reduce_max_sync(0xffffffffu, plen);
+        // rows with an A value outside the double-word range accumulate natively
         bool nat = MODE == MODE_F64 || b_bad;
         if (MODE == MODE_DW && !nat) {
             bool ok = true;
-            for (int p = gl; p < maxlen; p += G)
-                if (p < plen) dw_split(((const double *)a.aval)[p0 + p], ok);
+            for (int pp = gl; pp < plen; pp += G) dw_split(((const double *)a.aval)[p0 + pp], ok);
             const unsigned bad = __ballot_sync(0xffffffffu, !ok);
-            nat = ((bad >> gbase) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1))) != 0;
+            nat = ((bad >> gbase) & lmask) != 0;
         }
-        __syncwarp();
-        for (int pb = 0; pb < maxlen; pb += G * R) {
-            int kk[R];
-            V av[R];
-            int64_t q0[R];
-            int blen[R];
+        const int maxlen = __reduce_max_sync(0xffffffffu, plen);
+        const bool three = plen > DW2_MAX_TERMS;
+        for (int pb = 0; pb < maxlen; pb += E) {
+            // stage entries [pb, pb+E): lane gl takes EL consecutive entries
+            int cnt[EL];
+            int lsum = 0;
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                const int p = pb + gl + G * r;
-                const bool has = p < plen;
-                kk[r] = has ? a.acol[p0 + p] : 0;
-                av[r] = has ? ((const V *)a.aval)[p0 + p] : V(0);
-            }
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                const int p = pb + gl + G * r;
-                const bool has = p < plen;
-                q0[r] = has ? a.brp[kk[r]] : 0;
-                blen[r] = has ? (int)(a.brp[kk[r] + 1] - q0[r]) : 0;
-            }
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-#pragma unroll 1
-                for (int src = 0; src < G; src++) {
-                    if (pb + G * r + src >= maxlen) break;
-                    const int sl = gbase + src;
-                    const int64_t qb = __shfl_sync(0xffffffffu, q0[r], sl);
-                    const int bl = __shfl_sync(0xffffffffu, blen[r], sl);
-                    const V avv = __shfl_sync(0xffffffffu, av[r], sl);
-                    bool dummy = true;
-                    const float2 a2 = MODE == MODE_DW ? dw_split((double)avv, dummy) : make_float2(0.f, 0.f);
-                    const int nch = __reduce_max_sync(0xffffffffu, (bl + G - 1) / G);
-                    for (int ch = 0; ch < nch; ch++) {
-                        const int off = ch * G + gl;
-                        if (off < bl) {
-                            const int64_t q = qb + off;
-                            const int slot = map_slot(keys, L, a.bcol[q]);
-                            if (slot >= 0) acc_update<MODE>(acc, slot, nat, a.bval, a.bsplit, q, avv, a2);
-                            else flag |= DERR_PROBE;
-                        }
+            for (int u = 0; u < EL; u++) {
+                const int e = gl * EL + u;
+                const int pidx = pb + e;
+                int len = 0;
+                if (pidx < plen) {
+                    const int k = a.acol[p0 + pidx];
+                    const int4 d = bdesc[k];
+                    len = d.z;
+                    eq0[e] = desc_start(d);
+                    const V av = ((const V *)a.aval)[p0 + pidx];
+                    if (MODE == MODE_DW && !nat) {
+                        bool dummy = true;
+                        const float2 s2 = dw_split((double)av, dummy);
+                        ea[e] = __longlong_as_double(((long long)__float_as_uint(s2.y) << 32) |
+                                                     (long long)__float_as_uint(s2.x));
+                    } else {
+                        ea[e] = (double)av;
                     }
+                }
+                cnt[u] = len;
+                lsum += len;
+            }
+            // exclusive scan of the lanes' sums within the row's group
+            int incl = lsum;
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d, G);
+                if (gl >= d) incl += y;
+            }
+            int run = incl - lsum;
+#pragma unroll
+            for (int u = 0; u < EL; u++) {
+                pre[gl * EL + u] = run;
+                run += cnt[u];
+            }
+            if (gl == G - 1) pre[E] = incl;
+            const int total = __shfl_sync(0xffffffffu, incl, gbase + G - 1);
+            const int maxtot = __reduce_max_sync(0xffffffffu, total);
+            __syncwarp();
+            int e = 0;
+            for (int t0 = 0; t0 < maxtot; t0 += G) {
+                const int t = t0 + gl;
+                const bool valid = t < total;
+                int slot = -1;
+                float px = 0.f, py = 0.f;   // product payload (see acc below)
+                if (valid) {
+                    while (pre[e + 1] <= t) e++;
+                    const int64_t q = eq0[e] + (t - pre[e]);
+                    slot = map_slot(keys, L, a.bcol[q]);
+                    if (slot < 0) flag |= DERR_PROBE;
+                    if (MODE == MODE_F32) {
+                        px = (float)ea[e] * ((const float *)a.bval)[q];
+                    } else if (MODE == MODE_DW && !nat) {
+                        const unsigned long long bits = (unsigned long long)__double_as_longlong(ea[e]);
+                        const float2 a2 = make_float2(__uint_as_float((unsigned)bits),
+                                                      __uint_as_float((unsigned)(bits >> 32)));
+                        const float2 pr = dw_mul(a2, a.bsplit[q]);
+                        px = pr.x;
+                        py = pr.y;
+                    } else {
+                        const double pd = ea[e] * ((const double *)a.bval)[q];
+                        px = __int_as_float(__double2loint(pd));
+                        py = __int_as_float(__double2hiint(pd));
+                    }
+                }
+                // lanes of this row holding the same slot update it in turns,
+                // ordered by their rank among those lanes
+                const unsigned key = slot >= 0 ? (unsigned)(rs * SMAX + slot) : 0x80000000u | lane;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const int rank = __popc(peers & ((1u << lane) - 1));
+                const int maxr = __reduce_max_sync(0xffffffffu, slot >= 0 ? rank : 0);
+                for (int j = 0; j <= maxr; j++) {
+                    if (slot >= 0 && rank == j) acc_slot<MODE>(hi, lo, lo2, slot, nat, three, px, py);
                     __syncwarp();
                 }
+                __syncwarp();
             }
+            __syncwarp();
         }
         // compact the occupied slots of each row to the front (read all, then write)
         int kq[PER];
-        Slot vq[PER];
+        float hq[PER], lq[PER], l2q[PER];
 #pragma unroll
         for (int t = 0; t < PER; t++) {
             const int sidx = gl + t * G;
             kq[t] = sidx < S ? keys[sidx] : -1;
-            vq[t] = sidx < S ? acc[sidx] : Slot(0);
+            hq[t] = hi[sidx];
+            lq[t] = lo[sidx];
+            l2q[t] = lo2[sidx];
         }
         __syncwarp();
-        int cnt = 0;
-        const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
+        int cntr = 0;
 #pragma unroll
         for (int t = 0; t < PER; t++) {
             const bool occ = kq[t] != -1;
             const unsigned m = (__ballot_sync(0xffffffffu, occ) >> gbase) & lmask;
             if (occ) {
-                const int pos = cnt + __popc(m & ((1u << gl) - 1));
+                const int pos = cntr + __popc(m & ((1u << gl) - 1));
                 keys[pos] = kq[t];
-                acc[pos] = vq[t];
+                hi[pos] = hq[t];
+                lo[pos] = lq[t];
+                lo2[pos] = l2q[t];
             }
-            cnt += __popc(m);
+            cntr += __popc(m);
         }
         __syncwarp();
-        if (active && cnt != nn) {
+        if (active && cntr != nn) {
             flag |= DERR_COUNT;
-            cnt = min(cnt, nn);
+            cntr = min(cntr, nn);
         }
-        if (!active) cnt = 0;
+        if (!active) cntr = 0;
         // rank by counting smaller keys; write each row in ascending order
-        for (int e = gl; e < cnt; e += G) {
+        for (int e = gl; e < cntr; e += G) {
             const int key = keys[e];
             int r = 0;
-            for (int u = 0; u < cnt; u++) r += keys[u] < key;
+            for (int u = 0; u < cntr; u++) r += keys[u] < key;
             a.ccol[out + r] = key;
-            store_out<MODE>(a.cval, out + r, acc[e], nat);
+            if (MODE == MODE_F32)
+                ((float *)a.cval)[out + r] = hi[e];
+            else if (MODE == MODE_DW && !nat)
+                ((double *)a.cval)[out + r] = three ? dw3_to_double(hi[e], lo[e], lo2[e])
+                                                    : dw_to_double(hi[e], lo[e]);
+            else
+                ((double *)a.cval)[out + r] = __hiloint2double(__float_as_int(lo[e]), __float_as_int(hi[e]));
         }
         __syncwarp();
     }
@@ -582,28 +705,29 @@ static const char *NUM_LABEL[NBINS] = {"", "numeric.small", "numeric.small", "nu
                                        "numeric.bin4", "numeric.bin5", "numeric.bin6", ""};
 
 template <int G, int MODE>
-static int run_small(const NumP &a, int64_t n, const uint8_t *bins, DevState *st, int *err, Ctx &c) {
+static int run_small(const NumP &a, const int4 *bdesc, int64_t n, const uint8_t *bins, DevState *st,
+                     int *err, Ctx &c) {
     constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
-    const size_t smem = (size_t)GPB * 64 * (sizeof(SlotT<MODE>) + 4);
+    const size_t smem = (size_t)GPB * (64 * 16 + 32 * 16 + 33 * 4);
     SG_TRY(prep(k_num_small<G, MODE>, smem));
     int64_t blocks = (n + GPB - 1) / GPB;
     const int64_t cap = (int64_t)c.nsm * 32;
     blocks = blocks < cap ? blocks : cap;
     c.begin("numeric.small", n);
-    k_num_small<G, MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, n, bins, st, err);
+    k_num_small<G, MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, bdesc, n, bins, st, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
 }
 
 template <int MODE>
-static int run_small_g(int G, const NumP &a, int64_t n, const uint8_t *bins, DevState *st, int *err,
-                       Ctx &c) {
+static int run_small_g(int G, const NumP &a, const int4 *bdesc, int64_t n, const uint8_t *bins,
+                       DevState *st, int *err, Ctx &c) {
     switch (G) {
-        case 4: return run_small<4, MODE>(a, n, bins, st, err, c);
-        case 8: return run_small<8, MODE>(a, n, bins, st, err, c);
-        case 16: return run_small<16, MODE>(a, n, bins, st, err, c);
-        default: return run_small<32, MODE>(a, n, bins, st, err, c);
+        case 4: return run_small<4, MODE>(a, bdesc, n, bins, st, err, c);
+        case 8: return run_small<8, MODE>(a, bdesc, n, bins, st, err, c);
+        case 16: return run_small<16, MODE>(a, bdesc, n, bins, st, err, c);
+        default: return run_small<32, MODE>(a, bdesc, n, bins, st, err, c);
     }
 }
 
@@ -671,11 +795,11 @@ static int run_huge(const NumP &a, const spgemm_csr &B, const int32_t *rows, int
 
 template <int MODE>
 static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
-                   const int32_t *rows, const long long *counts, DevState *st, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
+                   const int4 *bdesc, const int32_t *rows, const long long *counts, DevState *st,
+                   void *gws, size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
     using V = typename std::conditional<MODE == MODE_F32, float, double>::type;
     int *err = &st->err;
-    if (counts[1] + counts[2] > 0) SG_TRY(run_small_g<MODE>(G, a, A.nrows, bins, st, err, c));
+    if (counts[1] + counts[2] > 0) SG_TRY(run_small_g<MODE>(G, a, bdesc, A.nrows, bins, st, err, c));
     int64_t off = 0;
     for (int b = 3; b <= BIN_HUGE; b++) {
         const int64_t cnt = counts[b];
@@ -693,14 +817,15 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
 }
 
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
-                   const uint8_t *bins, const int32_t *rows, const long long *counts, DevState *st,
-                   float2 *bsplit, void *gws, size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
+                   const uint8_t *bins, const int4 *bdesc, const int32_t *rows,
+                   const long long *counts, DevState *st, float2 *bsplit, void *gws,
+                   size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
     NumP a{A.row_ptr, A.col_idx, A.values, B.row_ptr, B.col_idx, B.values, bsplit,
            C.row_ptr, C.col_idx, C.values};
     if (dtype == SPGEMM_F32)
-        return run_all<MODE_F32>(a, A, B, bins, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+        return run_all<MODE_F32>(a, A, B, bins, bdesc, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
     if (f64_native)
-        return run_all<MODE_F64>(a, A, B, bins, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+        return run_all<MODE_F64>(a, A, B, bins, bdesc, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
     SG_CUDA(cudaMemsetAsync(&st->b_out_of_range, 0, sizeof(int), c.s));
     if (B.nnz > 0) {
         int64_t blocks = (B.nnz + 255) / 256;
@@ -710,7 +835,7 @@ int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm
         c.end();
         SG_CUDA(cudaGetLastError());
     }
-    return run_all<MODE_DW>(a, A, B, bins, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+    return run_all<MODE_DW>(a, A, B, bins, bdesc, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
 }
 
 }  // namespace sg

@@ -6,7 +6,7 @@
 //
 // Rows are sized by an upper bound on their distinct blocks.  A first pass
 // takes every row with bound <= 4096 in row order with a 32-slot map per
-// row and G lanes walking the pairs of each B_k; rows that do not fit are
+// row, G lanes sharing the row's stored a_ik; rows that do not fit are
 // marked and, with the rows whose bound exceeds 4096, handled by a second
 // pass from row lists: a warp with a 128- or 512-slot map (bins 2, 3), a
 // block with a 2048- or 8192-slot map (bins 4, 5), or a block with a dense
@@ -41,25 +41,32 @@ __device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int L, in
 }
 
 // First pass: a warp takes 32/G consecutive rows, G lanes per row, 32-slot
-// map per row.  The lanes of a warp stay converged (loops run to the
-// warp-wide maximum, idle lanes predicated off); the stored a_ik of a row are
-// loaded a batch at a time into registers and broadcast with shuffles.  A row
+// map per row.  The compressed pairs a row visits are dealt out evenly: the
+// stored a_ik are staged E at a time in shared memory with the prefix sums
+// of pairs(B_k), and in each step the G lanes take G consecutive pairs,
+// finding their a_ik with a forward-only cursor; loads of pairs stay
+// coalesced within each B_k.  Insertions are atomic (CAS on the key, OR on
+// the mask), so lanes meeting the same block need no coordination.  A row
 // whose map fills up is marked crp[i+1] = -1 and counted in its second-pass
 // bin.
 template <int G>
 __global__ void __launch_bounds__(256) k_sym_first(
     int64_t n, const uint8_t *__restrict__ bins, const int64_t *__restrict__ arp,
-    const int32_t *__restrict__ acol, const int64_t *__restrict__ brp,
-    const int32_t *__restrict__ ccnt, const int2 *__restrict__ pairs, int64_t *__restrict__ crp,
-    DevState *st) {
+    const int32_t *__restrict__ acol, const int4 *__restrict__ desc,
+    const int2 *__restrict__ pairs, int64_t *__restrict__ crp, DevState *st) {
     constexpr int S = SYM_FIRST_SLOTS, L = 5, RPW = 32 / G, WPB = 8, PER = S / G;
-    constexpr int R = (G >= 16 ? 2 : 32 / G);
-    __shared__ int keys_all[WPB * RPW * S];
-    __shared__ unsigned masks_all[WPB * RPW * S];
+    constexpr int E = 32, EL = E / G, NR = WPB * RPW;
+    __shared__ int keys_all[NR * S];
+    __shared__ unsigned masks_all[NR * S];
+    __shared__ long long eq0_all[NR * E];
+    __shared__ int pre_all[NR * (E + 1)];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / G, gl = lane % G, gbase = g * G;
-    int *keys = keys_all + (w * RPW + g) * S;
-    unsigned *masks = masks_all + (w * RPW + g) * S;
+    const int rs = w * RPW + g;
+    int *keys = keys_all + rs * S;
+    unsigned *masks = masks_all + rs * S;
+    long long *eq0 = eq0_all + rs * E;
+    int *pre = pre_all + rs * (E + 1);
     const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
     const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
@@ -74,42 +81,52 @@ __global__ void __launch_bounds__(256) k_sym_first(
             masks[gl + t * G] = 0;
         }
         const int maxlen = __reduce_max_sync(0xffffffffu, plen);
-        __syncwarp();
         bool fail = false;
-        for (int pb = 0; pb < maxlen; pb += G * R) {
-            int64_t q0[R];
-            int cn[R];
+        for (int pb = 0; pb < maxlen; pb += E) {
+            int cnt[EL];
+            int lsum = 0;
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                const int p = pb + gl + G * r;
-                const int k = p < plen ? acol[p0 + p] : -1;
-                q0[r] = k >= 0 ? brp[k] : 0;
-                cn[r] = k >= 0 ? ccnt[k] : 0;
+            for (int u = 0; u < EL; u++) {
+                const int e = gl * EL + u;
+                int c = 0;
+                if (pb + e < plen) {
+                    const int4 d = desc[acol[p0 + pb + e]];
+                    c = d.w;
+                    eq0[e] = desc_start(d);
+                }
+                cnt[u] = c;
+                lsum += c;
             }
+            int incl = lsum;
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-#pragma unroll 1
-                for (int src = 0; src < G; src++) {
-                    if (pb + G * r + src >= maxlen) break;
-                    const int sl = gbase + src;
-                    const int64_t qb = __shfl_sync(0xffffffffu, q0[r], sl);
-                    const int c = __shfl_sync(0xffffffffu, cn[r], sl);
-                    const int nch = __reduce_max_sync(0xffffffffu, (c + G - 1) / G);
-                    for (int ch = 0; ch < nch; ch++) {
-                        const int off = ch * G + gl;
-                        if (off < c && !fail) {
-                            const int2 pr = pairs[qb + off];
-                            fail = !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
-                        }
-                    }
+            for (int d = 1; d < G; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d, G);
+                if (gl >= d) incl += y;
+            }
+            int run = incl - lsum;
+#pragma unroll
+            for (int u = 0; u < EL; u++) {
+                pre[gl * EL + u] = run;
+                run += cnt[u];
+            }
+            if (gl == G - 1) pre[E] = incl;
+            int total = __shfl_sync(0xffffffffu, incl, gbase + G - 1);
+            if (fail) total = 0;
+            const int maxtot = __reduce_max_sync(0xffffffffu, total);
+            __syncwarp();
+            int e = 0;
+            for (int t0 = 0; t0 < maxtot; t0 += G) {
+                const int t = t0 + gl;
+                if (t < total) {
+                    while (pre[e + 1] <= t) e++;
+                    const int2 pr = pairs[eq0[e] + (t - pre[e])];
+                    fail |= !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
                 }
             }
-            // a row whose map is full stops early (its group's lanes agree)
             const unsigned fl = __ballot_sync(0xffffffffu, fail);
             fail = ((fl >> gbase) & lmask) != 0;
-            if (__all_sync(0xffffffffu, fail || plen <= pb + G * R)) break;
+            __syncwarp();
         }
-        __syncwarp();
         int c = 0;
 #pragma unroll
         for (int t = 0; t < PER; t++) c += __popc(masks[gl + t * G]);
@@ -273,29 +290,28 @@ static int prep(K kern, size_t smem) {
 }
 
 template <int G>
-static int run_first(const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
-                     const int32_t *ccnt, const int2 *pairs, int64_t *crp, DevState *st, Ctx &c) {
+static int run_first(const spgemm_csr &A, const uint8_t *bins, const int4 *desc, const int2 *pairs,
+                     int64_t *crp, DevState *st, Ctx &c) {
     constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
     int64_t blocks = (A.nrows + GPB - 1) / GPB;
     const int64_t cap = (int64_t)c.nsm * 8 * 4;
     blocks = blocks < cap ? blocks : cap;
     c.begin("symbolic.first", A.nrows);
-    k_sym_first<G><<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, bins, A.row_ptr, A.col_idx,
-                                                       B.row_ptr, ccnt, pairs, crp, st);
+    k_sym_first<G><<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, bins, A.row_ptr, A.col_idx, desc,
+                                                       pairs, crp, st);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
 }
 
-int launch_symbolic_first(const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
-                          const int32_t *ccnt, const int2 *pairs, int64_t *crp, DevState *st,
-                          int G, Ctx &c) {
+int launch_symbolic_first(const spgemm_csr &A, const uint8_t *bins, const int4 *desc,
+                          const int2 *pairs, int64_t *crp, DevState *st, int G, Ctx &c) {
     if (A.nrows == 0) return SPGEMM_OK;
     switch (G) {
-        case 4: return run_first<4>(A, B, bins, ccnt, pairs, crp, st, c);
-        case 8: return run_first<8>(A, B, bins, ccnt, pairs, crp, st, c);
-        case 16: return run_first<16>(A, B, bins, ccnt, pairs, crp, st, c);
-        default: return run_first<32>(A, B, bins, ccnt, pairs, crp, st, c);
+        case 4: return run_first<4>(A, bins, desc, pairs, crp, st, c);
+        case 8: return run_first<8>(A, bins, desc, pairs, crp, st, c);
+        case 16: return run_first<16>(A, bins, desc, pairs, crp, st, c);
+        default: return run_first<32>(A, bins, desc, pairs, crp, st, c);
     }
 }
 
