@@ -129,6 +129,31 @@ typedef enum spgemm_option {
 } spgemm_option;
 SPGEMM_API int spgemm_set_option(spgemm_handle handle, int option, int64_t value);
 
+/* Chunking plan (Section 3.3.1, Algorithm 4), host only.  A_row_ptr and
+ * C_row_ptr (host, nrows_A+1 each) and B_row_ptr (host, nrows_B+1) give the
+ * sizes; value_bytes is 4 or 8 (0 to size the pattern only); fast_size is
+ * the fast-memory budget in bytes.  Fills `plan`: the algorithm (2 = A and
+ * C kept in fast memory while B is streamed, Algorithm 2; 3 = B kept while
+ * A and C are streamed, Algorithm 3), the Algorithm 4 branch (1..4), the
+ * numbers of row parts, the sizes and both copy costs (Algorithm 2:
+ * size(A) + size(C) + size(B)|P_AC|; Algorithm 3: size(B) + size(A)|P_B| +
+ * size(C)(|P_B|-1)); and, when ac_cuts / b_cuts have room (cap_ac >= n_ac+1,
+ * cap_b >= n_b+1, caller-owned host arrays), the part boundaries.  Sizes of a
+ * row range are its CSR bytes: 8 per offset, 4 + value_bytes per entry.
+ * SPGEMM_ERR_BUDGET if one row exceeds its portion of the budget. */
+typedef struct spgemm_chunk_plan {
+    int algorithm;
+    int branch;
+    int64_t n_ac, n_b;
+    int64_t size_a, size_b, size_c;
+    int64_t cost_chunk1, cost_chunk2;
+    int64_t *ac_cuts, *b_cuts;   /* in: caller arrays (may be NULL); out: boundaries */
+    int64_t cap_ac, cap_b;       /* in: capacities of those arrays */
+} spgemm_chunk_plan;
+SPGEMM_API int spgemm_plan_chunks(const int64_t *A_row_ptr, int64_t nrows_A, const int64_t *C_row_ptr,
+                                  const int64_t *B_row_ptr, int64_t nrows_B, int value_bytes,
+                                  int64_t fast_size, spgemm_chunk_plan *plan);
+
 /* Synchronises `stream` and reports device-side errors raised by earlier
  * asynchronous calls on this handle (SPGEMM_ERR_INTERNAL if a hash probe
  * bound was exceeded or a row's column count disagreed with the symbolic

@@ -39,6 +39,14 @@ class TimingRec(C.Structure):
                 ("ms", C.c_double)]
 
 
+class ChunkPlanRec(C.Structure):
+    _fields_ = [("algorithm", C.c_int), ("branch", C.c_int), ("n_ac", C.c_int64), ("n_b", C.c_int64),
+                ("size_a", C.c_int64), ("size_b", C.c_int64), ("size_c", C.c_int64),
+                ("cost_chunk1", C.c_int64), ("cost_chunk2", C.c_int64),
+                ("ac_cuts", C.c_void_p), ("b_cuts", C.c_void_p), ("cap_ac", C.c_int64),
+                ("cap_b", C.c_int64)]
+
+
 class CsrDesc(C.Structure):
     _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
                 ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("values", C.c_void_p)]
@@ -74,6 +82,7 @@ def load(path: str = LIB_PATH):
         "spgemm_timings": ([p, p, i32, C.POINTER(i32)], i32),
         "spgemm_reset_timings": ([p], i32),
         "spgemm_set_option": ([p, i32, i64], i32),
+        "spgemm_plan_chunks": ([p, i64, p, p, i64, i32, i64, p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +262,31 @@ def default_handle() -> Handle:
     if d not in _default:
         _default[d] = Handle(d)
     return _default[d]
+
+
+def plan_chunks(a_row_ptr, c_row_ptr, b_row_ptr, value_bytes: int, fast_size: int) -> dict:
+    """Algorithm 4 on host row offsets (numpy int64): algorithm, branch,
+    part boundaries, sizes and the copy costs of Algorithms 2 and 3."""
+    import numpy as np
+    lib = load()
+    a = np.ascontiguousarray(a_row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(c_row_ptr, dtype=np.int64)
+    b = np.ascontiguousarray(b_row_ptr, dtype=np.int64)
+    cap_ac, cap_b = len(a) + 1, len(b) + 1
+    ac_cuts = np.zeros(cap_ac, dtype=np.int64)
+    b_cuts = np.zeros(cap_b, dtype=np.int64)
+    rec = ChunkPlanRec()
+    rec.ac_cuts, rec.b_cuts = ac_cuts.ctypes.data, b_cuts.ctypes.data
+    rec.cap_ac, rec.cap_b = cap_ac, cap_b
+    _check(lib.spgemm_plan_chunks(a.ctypes.data, len(a) - 1, c.ctypes.data, b.ctypes.data, len(b) - 1,
+                                  value_bytes, fast_size, C.byref(rec)))
+    ac = ac_cuts[:rec.n_ac + 1]
+    bb = b_cuts[:rec.n_b + 1]
+    return {"algorithm": rec.algorithm, "branch": rec.branch,
+            "p_ac": list(zip(ac[:-1].tolist(), ac[1:].tolist())),
+            "p_b": list(zip(bb[:-1].tolist(), bb[1:].tolist())),
+            "size_a": rec.size_a, "size_b": rec.size_b, "size_c": rec.size_c,
+            "cost_chunk1": rec.cost_chunk1, "cost_chunk2": rec.cost_chunk2}
 
 
 def bin_of(keys: int, flops: int) -> int:

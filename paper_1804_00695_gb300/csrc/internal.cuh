@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 #include "../../include/spgemm.h"
 
 namespace sg {
@@ -159,5 +160,14 @@ int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
                    size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c);
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype);
+
+// plan.cu: Algorithm 4.  Cuts are part boundaries (first 0, last nrows).
+struct ChunkPlan {
+    int algorithm = 0, branch = 0;
+    std::vector<int64_t> ac_cuts, b_cuts;
+    int64_t size_a = 0, size_b = 0, size_c = 0, cost1 = 0, cost2 = 0;
+};
+int plan_chunks(const int64_t *a_rp, int64_t n_ac, const int64_t *c_rp, const int64_t *b_rp,
+                int64_t n_b, int vb_ac, int vb_b, int64_t fast, ChunkPlan &p);
 
 }  // namespace sg
