@@ -154,6 +154,49 @@ SPGEMM_API int spgemm_plan_chunks(const int64_t *A_row_ptr, int64_t nrows_A, con
                                   const int64_t *B_row_ptr, int64_t nrows_B, int value_bytes,
                                   int64_t fast_size, spgemm_chunk_plan *plan);
 
+/* Chunked product for operands in host memory (Section 3.3.1).  A, B and C
+ * are host CSR arrays (page-locked memory gives full copy bandwidth); every
+ * device byte the call uses comes out of one allocation of exactly
+ * fast_mem_budget bytes, kept by the handle between calls of equal budget.
+ *
+ * spgemm_chunked_symbolic fills C_row_ptr (host, nrows(A)+1) and *nnz_C.
+ * The pattern of B stays resident while the rows of A stream through, so
+ * Algorithm 4 must be able to place the pattern of B (offsets and columns)
+ * in the large (75%) portion; otherwise SPGEMM_ERR_BUDGET.  Synchronises.
+ *
+ * spgemm_chunked_numeric fills C->col_idx and C->values (host, C->nnz each,
+ * C->row_ptr from spgemm_chunked_symbolic).  Algorithm 4 chooses the row
+ * parts and between Algorithm 2 (parts of A and C stay while the parts of B
+ * stream; parts of B that the part of A does not reach are skipped) and
+ * Algorithm 3 (parts of B stay while A and C stream, partial C going out
+ * and in).  Each step is the row-range fused multiply-add of Section 3.2.2.
+ * The streamed operand is double buffered on side streams.  Values of C are
+ * accumulated natively (FP64 or FP32).  The call returns once all copies and
+ * kernels are enqueued (it waits once per part of A for its column range);
+ * synchronise `stream` before reading C.
+ * Errors: SPGEMM_ERR_BUDGET (a row or the double-buffered parts do not fit),
+ * SPGEMM_ERR_NOMEM (the budget cannot be allocated), SPGEMM_ERR_DIM,
+ * SPGEMM_ERR_INDEX (symbolic: a column out of range), SPGEMM_ERR_ARG.
+ *
+ * spgemm_chunked_stats reports the last chunked call: algorithm (2 or 3),
+ * Algorithm 4 branch, parts, both copy-cost formulas, bytes actually copied
+ * each way, B parts skipped, and device bytes in use. */
+typedef struct spgemm_chunk_stats {
+    int algorithm, branch;
+    int64_t n_ac, n_b;
+    int64_t cost_chunk1, cost_chunk2;
+    int64_t h2d_bytes, d2h_bytes;
+    int64_t skipped_b_parts;
+    int64_t device_bytes;
+} spgemm_chunk_stats;
+SPGEMM_API int spgemm_chunked_symbolic(spgemm_handle handle, const spgemm_csr *A, const spgemm_csr *B,
+                                       int64_t *C_row_ptr, int64_t *nnz_C, size_t fast_mem_budget,
+                                       void *stream);
+SPGEMM_API int spgemm_chunked_numeric(spgemm_handle handle, int dtype, const spgemm_csr *A,
+                                      const spgemm_csr *B, spgemm_csr *C, size_t fast_mem_budget,
+                                      void *stream);
+SPGEMM_API int spgemm_chunked_stats(spgemm_handle handle, spgemm_chunk_stats *out);
+
 /* Synchronises `stream` and reports device-side errors raised by earlier
  * asynchronous calls on this handle (SPGEMM_ERR_INTERNAL if a hash probe
  * bound was exceeded or a row's column count disagreed with the symbolic

@@ -47,6 +47,12 @@ class ChunkPlanRec(C.Structure):
                 ("cap_b", C.c_int64)]
 
 
+class ChunkStatsRec(C.Structure):
+    _fields_ = [("algorithm", C.c_int), ("branch", C.c_int), ("n_ac", C.c_int64), ("n_b", C.c_int64),
+                ("cost_chunk1", C.c_int64), ("cost_chunk2", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64), ("skipped_b_parts", C.c_int64), ("device_bytes", C.c_int64)]
+
+
 class CsrDesc(C.Structure):
     _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
                 ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("values", C.c_void_p)]
@@ -83,6 +89,9 @@ def load(path: str = LIB_PATH):
         "spgemm_reset_timings": ([p], i32),
         "spgemm_set_option": ([p, i32, i64], i32),
         "spgemm_plan_chunks": ([p, i64, p, p, i64, i32, i64, p], i32),
+        "spgemm_chunked_symbolic": ([p, p, p, p, C.POINTER(i64), C.c_size_t, p], i32),
+        "spgemm_chunked_numeric": ([p, i32, p, p, p, C.c_size_t, p], i32),
+        "spgemm_chunked_stats": ([p, p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -139,6 +148,20 @@ class Csr:
         if self.val.dtype == torch.float32:
             return F32
         raise TypeError(f"unsupported value dtype {self.val.dtype}")
+
+
+@dataclass
+class HostCsr(Csr):
+    """CSR matrix in (pinned) host memory as torch CPU tensors."""
+
+    @staticmethod
+    def from_numpy(m, dtype=None, pin: bool = True) -> "HostCsr":
+        torch = _torch()
+        val = m.val if dtype is None else m.val.astype(dtype)
+        t = [torch.from_numpy(x) for x in (m.row_ptr, m.col, val)]
+        if pin:
+            t = [x.pin_memory() for x in t]
+        return HostCsr(m.nrows, m.ncols, *t)
 
 
 def _stream(stream=None) -> int:
@@ -223,6 +246,39 @@ class Handle:
         _check(_lib.spgemm_compress(self._h, C.byref(dm), cnt.data_ptr(), pairs.data_ptr(),
                                     _stream(stream)))
         return cnt, pairs
+
+    # -- chunked product, operands in (pinned) host memory ----------------------
+    def chunked_symbolic(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None):
+        """Row offsets of C (host int64 tensor, pinned) and nnz(C)."""
+        torch = _torch()
+        rp = torch.empty(A.nrows + 1, dtype=torch.int64).pin_memory()
+        nnz = C.c_int64()
+        da, db = A.desc(), B.desc()
+        _check(_lib.spgemm_chunked_symbolic(self._h, C.byref(da), C.byref(db), rp.data_ptr(),
+                                            C.byref(nnz), budget, _stream(stream)))
+        return rp, int(nnz.value)
+
+    def chunked_numeric(self, A: "HostCsr", B: "HostCsr", row_ptr, nnz: int, budget: int,
+                        stream=None) -> "HostCsr":
+        """Columns and values of C into pinned host tensors (synchronised)."""
+        torch = _torch()
+        col = torch.empty(nnz, dtype=torch.int32).pin_memory()
+        val = torch.empty(nnz, dtype=A.val.dtype).pin_memory()
+        Cm = HostCsr(A.nrows, B.ncols, row_ptr, col, val)
+        da, db, dc = A.desc(), B.desc(), Cm.desc()
+        _check(_lib.spgemm_chunked_numeric(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc),
+                                           budget, _stream(stream)))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return Cm
+
+    def chunked(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None) -> "HostCsr":
+        rp, nnz = self.chunked_symbolic(A, B, budget, stream)
+        return self.chunked_numeric(A, B, rp, nnz, budget, stream)
+
+    def chunked_stats(self) -> dict:
+        r = ChunkStatsRec()
+        _check(_lib.spgemm_chunked_stats(self._h, C.byref(r)))
+        return {f: getattr(r, f) for f, _ in ChunkStatsRec._fields_}
 
     def set_option(self, option: int, value: int):
         _check(_lib.spgemm_set_option(self._h, option, value))

@@ -73,6 +73,13 @@ struct spgemm_handle_s {
     bool f64_native = false;
     int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from the mean products per row)
     double mean_flops = 0;
+    // chunked calls: budget arena, side streams, events, last statistics
+    void *arena = nullptr;
+    size_t arena_cap = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev[8] = {};
+    ChunkStats cstats;
+    float chunk_ms = 0;
     // launch counting and CUDA-event timing
     long long launches = 0;
     bool timing = false;
@@ -185,6 +192,11 @@ int spgemm_destroy(spgemm_handle h) {
         if (r.e0) cudaEventDestroy(r.e0);
         if (r.e1) cudaEventDestroy(r.e1);
     }
+    if (h->arena) cudaFree(h->arena);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     if (h->dstate) cudaFree(h->dstate);
     if (h->hstate) cudaFreeHost(h->hstate);
     delete h;
@@ -339,6 +351,109 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     const int gn = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 12.0);
     return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, rows, h->num_counts,
                           h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, gn, c);
+}
+
+// Side streams, events and the budget arena of the chunked calls.
+static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &env, Ctx &c) {
+    if (!h->s_in) {
+        SG_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
+        SG_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+        for (auto &e : h->ev) SG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (h->arena_cap != budget) {
+        if (h->arena) {
+            SG_CUDA(cudaStreamSynchronize(s));
+            SG_CUDA(cudaFree(h->arena));
+            h->arena = nullptr;
+            h->arena_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->arena, budget);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("chunked: cannot allocate the %zu-byte budget: %s", budget, cudaGetErrorString(e));
+            return SPGEMM_ERR_NOMEM;
+        }
+        h->arena_cap = budget;
+    }
+    // work issued before this call on the caller's stream comes first
+    SG_CUDA(cudaEventRecord(h->ev[7], s));
+    SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[7], 0));
+    SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[7], 0));
+    env.ctx = &c;
+    env.arena = h->arena;
+    env.s_in = h->s_in;
+    env.s_out = h->s_out;
+    for (int k = 0; k < 8; k++) env.ev[k] = h->ev[k];
+    env.err = &h->dstate->err;
+    return SPGEMM_OK;
+}
+
+int spgemm_chunked_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B,
+                            int64_t *C_row_ptr, int64_t *nnz_C, size_t fast_mem_budget, void *stream) {
+    if (!h || !C_row_ptr || !nnz_C) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", false));
+    SG_TRY(check_csr(B, "B", false));
+    if (A->ncols != B->nrows) { set_error("dimension mismatch"); return SPGEMM_ERR_DIM; }
+    for (int64_t k = 0; k < A->nnz; k++)
+        if (A->col_idx[k] < 0 || A->col_idx[k] >= B->nrows) {
+            set_error("column %lld of A out of range", (long long)k);
+            return SPGEMM_ERR_INDEX;
+        }
+    for (int64_t k = 0; k < B->nnz; k++)
+        if (B->col_idx[k] < 0 || B->col_idx[k] >= B->ncols) {
+            set_error("column %lld of B out of range", (long long)k);
+            return SPGEMM_ERR_INDEX;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    Ctx c = h->ctx(s);
+    ChunkEnv env;
+    SG_TRY(chunk_env(h, fast_mem_budget, s, env, c));
+    h->cstats = ChunkStats();
+    SG_TRY(chunked_symbolic(env, *A, *B, C_row_ptr, nnz_C, fast_mem_budget, h->cstats));
+    SG_CUDA(cudaStreamSynchronize(s));
+    SG_TRY(fetch_state(h, s));
+    return device_errors(h->hstate->err);
+}
+
+int spgemm_chunked_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_csr *B,
+                           spgemm_csr *C, size_t fast_mem_budget, void *stream) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) { set_error("bad dtype %d", dtype); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", true));
+    SG_TRY(check_csr(B, "B", true));
+    SG_TRY(check_csr(C, "C", true));
+    if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) {
+        set_error("dimension mismatch");
+        return SPGEMM_ERR_DIM;
+    }
+    if (C->row_ptr[C->nrows] != C->nnz) {
+        set_error("C.row_ptr does not end at C.nnz");
+        return SPGEMM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    Ctx c = h->ctx(s);
+    ChunkEnv env;
+    SG_TRY(chunk_env(h, fast_mem_budget, s, env, c));
+    h->cstats = ChunkStats();
+    return chunked_numeric(env, dtype, *A, *B, *C, fast_mem_budget, h->cstats);
+}
+
+int spgemm_chunked_stats(spgemm_handle h, spgemm_chunk_stats *out) {
+    if (!h || !out) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    const ChunkStats &x = h->cstats;
+    out->algorithm = x.algorithm;
+    out->branch = x.branch;
+    out->n_ac = x.n_ac;
+    out->n_b = x.n_b;
+    out->cost_chunk1 = x.cost1;
+    out->cost_chunk2 = x.cost2;
+    out->h2d_bytes = x.h2d;
+    out->d2h_bytes = x.d2h;
+    out->skipped_b_parts = x.skipped_b;
+    out->device_bytes = x.device_bytes;
+    return SPGEMM_OK;
 }
 
 int spgemm_set_option(spgemm_handle h, int option, int64_t value) {

@@ -1,0 +1,771 @@
+// Multi-memory chunking of Section 3.3.1: operands in host memory are moved
+// through a fixed device budget ("fast memory") in row parts chosen by
+// Algorithm 4, and multiplied part by part with the row-range fused
+// multiply-add of Section 3.2.2: C2_i = sum over stored a_ik with k in the B
+// part's row range of a_ik * B_k, plus the partial row C1_i already held.
+//
+//  * Algorithm 2 (A and C in place): for each A/C part, its rows of A and the
+//    offsets of C come in, C starts empty (only offsets are copied, as the
+//    paper notes), the B parts stream through, and the finished C part goes
+//    back to host memory.  B parts that no column of the A part reaches are
+//    skipped (same result, fewer bytes).
+//  * Algorithm 3 (B in place): for each B part, every A/C part streams in
+//    with its partial C (none before the first B part) and back out.
+//
+// Partial rows live in the final layout of C (offsets from the symbolic
+// phase): the first m slots of a row hold its partial entries in ascending
+// column order, the rest hold column -1.  Copies run on two side streams
+// (host to device, device to host) and the streamed operand is double
+// buffered: while part t is multiplied, part t+1 is copied in.  Every
+// device byte of a call comes out of one arena of exactly the budget.
+//
+// The symbolic phase is chunked the same way with the pattern only; it keeps
+// the pattern of B resident (its Algorithm 4 plan must put all of B in one
+// part) and streams the rows of A, counting distinct columns per row.
+#include <climits>
+#include <cstring>
+#include <algorithm>
+#include "internal.cuh"
+
+namespace sg {
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_rebase(int64_t *rp, int64_t n1, int64_t base) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) rp[i] -= base;
+}
+
+__global__ void k_col_range(const int32_t *__restrict__ col, int64_t nnz, int *mm) {
+    int lo = INT_MAX, hi = -1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        lo = min(lo, col[i]);
+        hi = max(hi, col[i]);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ bool fma_insert(int *keys, V *vals, int L, int col, V v) {
+    const unsigned msk = (1u << L) - 1;
+    unsigned h = hash_slot(col, L);
+#pragma unroll 1
+    for (int probe = 0; probe <= (int)msk; probe++) {
+        int k = ((volatile int *)keys)[h];
+        if (k == -1) {
+            k = atomicCAS(&keys[h], -1, col);
+            if (k == -1) k = col;
+        }
+        if (k == col) {
+            if (vals) atomicAdd(&vals[h], v);
+            return true;
+        }
+        h = (h + 1) & msk;
+    }
+    return false;
+}
+
+template <typename V, typename Sync>
+__device__ __forceinline__ void bitonic_kv(int *k, V *v, int P, int tid, int NT, Sync sync) {
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < P / 2; t += NT) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const int x = k[lo], y = k[hi];
+                if ((x > y) == asc) {
+                    k[lo] = y;
+                    k[hi] = x;
+                    if (v) {
+                        const V tv = v[lo];
+                        v[lo] = v[hi];
+                        v[hi] = tv;
+                    }
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// Fused multiply-add on a row range of B (Section 3.2.2), a warp per row of
+// the A/C part with at most FMA_WARP_CAP entries in C: the partial row and
+// the products of the stored a_ik with lo <= k < hi (other columns of A are
+// skipped; they need not be sorted) are merged in a shared-memory map, then
+// written back sorted, padded with -1.
+constexpr int FMA_WARP_CAP = 256, FMA_S = 512, FMA_WPB = 8;
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_fma_warp(
+    int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const V *__restrict__ aval, int64_t lo, int64_t hi, const int64_t *__restrict__ brp,
+    const int32_t *__restrict__ bcol, const V *__restrict__ bval, const int64_t *__restrict__ crp,
+    int32_t *__restrict__ ccol, V *__restrict__ cval, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    V *vals = (V *)smem_raw + w * FMA_S;
+    int *keys = (int *)((V *)smem_raw + FMA_WPB * FMA_S) + w * FMA_S;
+    int flag = 0;
+    for (int64_t i = (int64_t)blockIdx.x * FMA_WPB + w; i < nrows; i += (int64_t)gridDim.x * FMA_WPB) {
+        const int64_t c0 = crp[i];
+        const int cap = (int)(crp[i + 1] - c0);
+        if (cap == 0 || cap > FMA_WARP_CAP) continue;
+        int S = 32;
+        while (S < 2 * cap) S <<= 1;
+        const int L = __ffs(S) - 1;
+        for (int s = lane; s < S; s += 32) {
+            keys[s] = -1;
+            if (cval) vals[s] = V(0);
+        }
+        __syncwarp();
+        for (int t = lane; t < cap; t += 32) {
+            const int c = ccol[c0 + t];
+            if (c >= 0 && !fma_insert<V>(keys, cval ? vals : nullptr, L, c, cval ? cval[c0 + t] : V(0)))
+                flag |= DERR_PROBE;
+        }
+        const int64_t pe = arp[i + 1];
+        for (int64_t p = arp[i]; p < pe; p++) {
+            const int64_t k = acol[p];
+            if (k < lo || k >= hi) continue;
+            const V av = aval ? aval[p] : V(0);
+            const int64_t q1 = brp[k - lo + 1];
+            for (int64_t q = brp[k - lo] + lane; q < q1; q += 32)
+                if (!fma_insert<V>(keys, cval ? vals : nullptr, L, bcol[q], cval ? av * bval[q] : V(0)))
+                    flag |= DERR_PROBE;
+        }
+        __syncwarp();
+        // compact in place (read everything first), sort, write back
+        constexpr int PER = FMA_S / 32;
+        int kq[PER];
+        V vq[PER];
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int s = lane + 32 * u;
+            kq[u] = s < S ? keys[s] : -1;
+            vq[u] = (s < S && cval) ? vals[s] : V(0);
+        }
+        __syncwarp();
+        int n = 0;
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const bool occ = kq[u] != -1;
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
+            if (occ) {
+                const int pos = n + __popc(m & ((1u << lane) - 1));
+                keys[pos] = kq[u];
+                vals[pos] = vq[u];
+            }
+            n += __popc(m);
+        }
+        if (n > cap) {
+            flag |= DERR_COUNT;
+            n = cap;
+        }
+        int P = 1;
+        while (P < n) P <<= 1;
+        for (int e = n + lane; e < P; e += 32) keys[e] = INT_MAX;
+        __syncwarp();
+        bitonic_kv<V>(keys, cval ? vals : nullptr, P, lane, 32, [] { __syncwarp(); });
+        for (int e = lane; e < cap; e += 32) {
+            ccol[c0 + e] = e < n ? keys[e] : -1;
+            if (cval) cval[c0 + e] = e < n ? vals[e] : V(0);
+        }
+        __syncwarp();
+    }
+    if (flag) atomicOr(err, flag);
+}
+
+// Same for rows with more than FMA_WARP_CAP entries: a block per row, map
+// and sort buffer in global memory (per block: 2^L slots, L from cap_max).
+template <typename V>
+__global__ void __launch_bounds__(256) k_fma_block(
+    int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const V *__restrict__ aval, int64_t lo, int64_t hi, const int64_t *__restrict__ brp,
+    const int32_t *__restrict__ bcol, const V *__restrict__ bval, const int64_t *__restrict__ crp,
+    int32_t *__restrict__ ccol, V *__restrict__ cval, int *err, int64_t slots, unsigned char *gws) {
+    __shared__ int nsh;
+    int *keys = (int *)(gws + (size_t)blockIdx.x * (size_t)slots * (8 + 2 * sizeof(V)));
+    V *vals = (V *)(keys + slots);
+    int *ck = (int *)(vals + slots);
+    V *cv = (V *)(ck + slots);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int flag = 0;
+    for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+        const int64_t c0 = crp[i];
+        const int64_t cap = crp[i + 1] - c0;
+        if (cap <= FMA_WARP_CAP) continue;
+        int L = 1;
+        while ((1LL << L) < 2 * cap) L++;
+        const int64_t S = 1LL << L;
+        for (int64_t s = threadIdx.x; s < S; s += 256) {
+            keys[s] = -1;
+            vals[s] = V(0);
+        }
+        if (threadIdx.x == 0) nsh = 0;
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < cap; t += 256) {
+            const int c = ccol[c0 + t];
+            if (c >= 0 && !fma_insert<V>(keys, cval ? vals : nullptr, L, c, cval ? cval[c0 + t] : V(0)))
+                flag |= DERR_PROBE;
+        }
+        const int64_t pe = arp[i + 1];
+        for (int64_t p = arp[i] + w; p < pe; p += 8) {
+            const int64_t k = acol[p];
+            if (k < lo || k >= hi) continue;
+            const V av = aval ? aval[p] : V(0);
+            const int64_t q1 = brp[k - lo + 1];
+            for (int64_t q = brp[k - lo] + lane; q < q1; q += 32)
+                if (!fma_insert<V>(keys, cval ? vals : nullptr, L, bcol[q], cval ? av * bval[q] : V(0)))
+                    flag |= DERR_PROBE;
+        }
+        __syncthreads();
+        for (int64_t s = threadIdx.x; s < S; s += 256) {
+            const int key = keys[s];
+            const bool occ = key != -1;
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&nsh, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (occ) {
+                const int pos = base + __popc(m & ((1u << lane) - 1));
+                if (pos < cap) {
+                    ck[pos] = key;
+                    cv[pos] = vals[s];
+                }
+            }
+        }
+        __syncthreads();
+        int n = nsh;
+        if (n > cap) {
+            flag |= DERR_COUNT;
+            n = (int)cap;
+        }
+        int P = 1;
+        while (P < n) P <<= 1;
+        for (int e = n + threadIdx.x; e < P; e += 256) ck[e] = INT_MAX;
+        __syncthreads();
+        bitonic_kv<V>(ck, cval ? cv : nullptr, P, threadIdx.x, 256, [] { __syncthreads(); });
+        for (int64_t e = threadIdx.x; e < cap; e += 256) {
+            ccol[c0 + e] = e < n ? ck[e] : -1;
+            if (cval) cval[c0 + e] = e < n ? cv[e] : V(0);
+        }
+        __syncthreads();
+    }
+    if (flag) atomicOr(err, flag);
+}
+
+// Symbolic count for a part of A against the resident pattern of B: a warp
+// per row, distinct columns counted in a shared-memory set; rows with more
+// than CNT_S/2 distinct columns are counted again by a block with a bitmap
+// of all columns in global memory.
+constexpr int CNT_S = 2048, CNT_WPB = 8;
+
+__global__ void __launch_bounds__(256) k_count_warp(
+    int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, int64_t *__restrict__ cnt,
+    int *overflow) {
+    extern __shared__ int skeys[];
+    __shared__ int scount[CNT_WPB];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *keys = skeys + w * CNT_S;
+    constexpr int L = __builtin_ctz(CNT_S);
+    for (int64_t i = (int64_t)blockIdx.x * CNT_WPB + w; i < nrows; i += (int64_t)gridDim.x * CNT_WPB) {
+        for (int s = lane; s < CNT_S; s += 32) keys[s] = -1;
+        if (lane == 0) scount[w] = 0;
+        __syncwarp();
+        bool full = false;
+        int mine = 0;
+        const int64_t pe = arp[i + 1];
+        for (int64_t p = arp[i]; p < pe && !full; p++) {
+            const int k = acol[p];
+            const int64_t q1 = brp[k + 1];
+            for (int64_t q = brp[k] + lane; q < q1; q += 32) {
+                const int col = bcol[q];
+                unsigned h = hash_slot(col, L);
+                bool done = false;
+                for (int probe = 0; probe < CNT_S / 2 && !done; probe++) {
+                    const int kk = ((volatile int *)keys)[h];
+                    if (kk == col) done = true;
+                    else if (kk == -1) {
+                        const int old = atomicCAS(&keys[h], -1, col);
+                        if (old == -1) { mine++; done = true; }
+                        else if (old == col) done = true;
+                    }
+                    h = (h + 1) & (CNT_S - 1);
+                }
+                if (!done) full = true;
+            }
+            full = __any_sync(0xffffffffu, full);
+        }
+        for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
+        if (lane == 0) {
+            if (full || mine > CNT_S / 2) {
+                cnt[i] = -1;
+                atomicAdd(overflow, 1);
+            } else {
+                cnt[i] = mine;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_count_bitmap(
+    int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, int64_t *__restrict__ cnt,
+    int64_t nwords, unsigned *gbits) {
+    __shared__ long long red[8];
+    unsigned *bits = gbits + (size_t)blockIdx.x * (size_t)nwords;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+        if (cnt[i] >= 0) continue;
+        for (int64_t s = threadIdx.x; s < nwords; s += 256) bits[s] = 0;
+        __syncthreads();
+        const int64_t pe = arp[i + 1];
+        for (int64_t p = arp[i] + w; p < pe; p += 8) {
+            const int k = acol[p];
+            for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+                const int col = bcol[q];
+                atomicOr(&bits[col >> 5], 1u << (col & 31));
+            }
+        }
+        __syncthreads();
+        long long c = 0;
+        for (int64_t s = threadIdx.x; s < nwords; s += 256) c += __popc(bits[s]);
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (lane == 0) red[w] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int j = 0; j < 8; j++) t += red[j];
+            cnt[i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host side
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    void *take(size_t bytes) {
+        size_t a = (used + 255) & ~(size_t)255;
+        if (a + bytes > cap) return nullptr;
+        used = a + bytes;
+        return base + a;
+    }
+};
+
+static size_t r256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int64_t part_bytes(const int64_t *rp, int64_t r0, int64_t r1, int vb) {
+    return (r1 - r0 + 1) * 8 + (rp[r1] - rp[r0]) * (int64_t)(4 + vb);
+}
+
+// Device copy of rows [r0, r1) of a host CSR matrix into (rp, col, val),
+// offsets rebased to 0; returns the bytes moved.
+static int64_t copy_rows_in(const spgemm_csr &M, int64_t r0, int64_t r1, int vb, int64_t *rp,
+                            int32_t *col, void *val, cudaStream_t s, int *status) {
+    const int64_t p0 = M.row_ptr[r0], p1 = M.row_ptr[r1];
+    int64_t bytes = (r1 - r0 + 1) * 8;
+    cudaError_t e = cudaMemcpyAsync(rp, M.row_ptr + r0, (size_t)(r1 - r0 + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && p1 > p0) {
+        e = cudaMemcpyAsync(col, M.col_idx + p0, (size_t)(p1 - p0) * 4, cudaMemcpyHostToDevice, s);
+        bytes += (p1 - p0) * 4;
+        if (e == cudaSuccess && vb && val) {
+            e = cudaMemcpyAsync(val, (const char *)M.values + (size_t)p0 * vb, (size_t)(p1 - p0) * vb,
+                                cudaMemcpyHostToDevice, s);
+            bytes += (p1 - p0) * vb;
+        }
+    }
+    if (e == cudaSuccess && r1 > r0) {
+        k_rebase<<<(unsigned)((r1 - r0 + 1 + 255) / 256), 256, 0, s>>>(rp, r1 - r0 + 1, p0);
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
+        e = cudaMemsetAsync(rp, 0, 8, s);
+    }
+    if (e != cudaSuccess) {
+        set_error("chunked copy: %s", cudaGetErrorString(e));
+        *status = SPGEMM_ERR_CUDA;
+    }
+    return bytes;
+}
+
+struct PartBuf {
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    void *val = nullptr;
+};
+
+static bool take_part(Arena &ar, PartBuf &b, int64_t rows, int64_t nnz, int vb) {
+    b.rp = (int64_t *)ar.take((size_t)(rows + 1) * 8);
+    b.col = (int32_t *)ar.take((size_t)std::max<int64_t>(nnz, 1) * 4);
+    b.val = vb ? ar.take((size_t)std::max<int64_t>(nnz, 1) * vb) : nullptr;
+    return b.rp && b.col && (vb == 0 || b.val);
+}
+
+template <typename V>
+static int launch_fma(const PartBuf &A, int64_t nrows, int64_t lo, int64_t hi, const PartBuf &B,
+                      const PartBuf &Cp, bool values, int64_t fma_blocks, int64_t slots, void *gws,
+                      int *err, Ctx &c) {
+    const size_t smem = (size_t)FMA_WPB * FMA_S * (sizeof(V) + 4);
+    SG_CUDA(cudaFuncSetAttribute(k_fma_warp<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (nrows + FMA_WPB - 1) / FMA_WPB;
+    blocks = std::min<int64_t>(blocks, (int64_t)c.nsm * 16);
+    if (blocks > 0) {
+        c.begin("chunked.fma", nrows);
+        k_fma_warp<V><<<(unsigned)blocks, 256, smem, c.s>>>(
+            nrows, A.rp, A.col, values ? (const V *)A.val : nullptr, lo, hi, B.rp, B.col,
+            values ? (const V *)B.val : nullptr, Cp.rp, Cp.col, values ? (V *)Cp.val : nullptr, err);
+        c.end();
+        SG_CUDA(cudaGetLastError());
+    }
+    if (fma_blocks > 0 && nrows > 0) {
+        int64_t bb = std::min<int64_t>(nrows, fma_blocks);
+        c.begin("chunked.fma_block", nrows);
+        k_fma_block<V><<<(unsigned)bb, 256, 0, c.s>>>(
+            nrows, A.rp, A.col, values ? (const V *)A.val : nullptr, lo, hi, B.rp, B.col,
+            values ? (const V *)B.val : nullptr, Cp.rp, Cp.col, values ? (V *)Cp.val : nullptr, err,
+            slots, (unsigned char *)gws);
+        c.end();
+        SG_CUDA(cudaGetLastError());
+    }
+    return SPGEMM_OK;
+}
+
+int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_csr &B,
+                    spgemm_csr &C, size_t budget, ChunkStats &stats) {
+    const int vb = dtype == SPGEMM_F64 ? 8 : 4;
+    Ctx &c = *env.ctx;
+    const cudaStream_t s = c.s;
+    // the largest row of C decides whether the block kernel and its maps are needed
+    int64_t cap_max = 0;
+    for (int64_t i = 0; i < C.nrows; i++) cap_max = std::max(cap_max, C.row_ptr[i + 1] - C.row_ptr[i]);
+    const bool big_rows = cap_max > FMA_WARP_CAP;
+    int64_t slots = 2;
+    while (slots < 2 * cap_max) slots <<= 1;
+    // blocks of the wide-row kernel: as many as an eighth of the budget holds
+    const size_t per_block = (size_t)slots * (8 + 2 * vb);
+    const int64_t fma_blocks = big_rows ? std::max<int64_t>(1, std::min<int64_t>(c.nsm, (int64_t)(budget / 8 / per_block))) : 0;
+    const size_t gws_bytes = (size_t)fma_blocks * per_block;
+    const size_t reserve = r256(gws_bytes) + 4096;
+    if (budget <= reserve) {
+        set_error("chunked: budget %zu below the fixed working set %zu", budget, reserve);
+        return SPGEMM_ERR_BUDGET;
+    }
+    // Algorithm 4 on the budget left after the fixed reserve.  The streamed
+    // (inner) operand is double buffered, so if the outer part plus two inner
+    // parts exceed the budget, the inner operand is cut again, finer, with
+    // BinarySearch: the algorithm and the outer parts stay as Algorithm 4
+    // chose them.
+    ChunkPlan p;
+    const int64_t avail = (int64_t)(budget - reserve) - 16 * 256;
+    SG_TRY(plan_chunks(A.row_ptr, A.nrows, C.row_ptr, B.row_ptr, B.nrows, vb, vb, (int64_t)(budget - reserve), p));
+    auto buf_ac = [&](const std::vector<int64_t> &cuts) {
+        int64_t mr = 0, ma = 0, mc = 0;
+        for (size_t j = 0; j + 1 < cuts.size(); j++) {
+            mr = std::max(mr, cuts[j + 1] - cuts[j]);
+            ma = std::max(ma, A.row_ptr[cuts[j + 1]] - A.row_ptr[cuts[j]]);
+            mc = std::max(mc, C.row_ptr[cuts[j + 1]] - C.row_ptr[cuts[j]]);
+        }
+        return 2 * (mr + 1) * 8 + (ma + mc) * (int64_t)(4 + vb);
+    };
+    auto buf_b = [&](const std::vector<int64_t> &cuts) {
+        int64_t mr = 0, mb = 0;
+        for (size_t t = 0; t + 1 < cuts.size(); t++) {
+            mr = std::max(mr, cuts[t + 1] - cuts[t]);
+            mb = std::max(mb, B.row_ptr[cuts[t + 1]] - B.row_ptr[cuts[t]]);
+        }
+        return (mr + 1) * 8 + mb * (int64_t)(4 + vb);
+    };
+    {
+        const bool alg2 = p.algorithm == 2;
+        const int64_t outer = alg2 ? buf_ac(p.ac_cuts) : buf_b(p.b_cuts);
+        std::vector<int64_t> &inner_cuts = alg2 ? p.b_cuts : p.ac_cuts;
+        double limit = (double)(avail - outer) / 2.0;
+        for (int iter = 0; (alg2 ? buf_b(inner_cuts) : buf_ac(inner_cuts)) * 2 + outer > avail; iter++) {
+            bool cut_ok = limit > 0 && iter < 40 &&
+                          (alg2 ? cut_rows(B.row_ptr, nullptr, B.nrows, vb, limit, inner_cuts)
+                                : cut_rows(A.row_ptr, C.row_ptr, A.nrows, vb, limit, inner_cuts));
+            if (!cut_ok) {
+                set_error("chunked: budget %zu too small for a part and two double-buffered parts", budget);
+                return SPGEMM_ERR_BUDGET;
+            }
+            limit *= 0.85;
+        }
+    }
+    stats.algorithm = p.algorithm;
+    stats.branch = p.branch;
+    stats.n_ac = (int64_t)p.ac_cuts.size() - 1;
+    stats.n_b = (int64_t)p.b_cuts.size() - 1;
+    stats.cost1 = p.cost1;
+    stats.cost2 = p.cost2;
+    // carve the arena
+    Arena ar{(char *)env.arena, budget, 0};
+    void *gws = gws_bytes ? ar.take(gws_bytes) : nullptr;
+    int *mm = (int *)ar.take(16);
+    int64_t max_ac_rows = 0, max_ac_a = 0, max_ac_c = 0, max_b_rows = 0, max_b_nnz = 0;
+    for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+        const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1];
+        max_ac_rows = std::max(max_ac_rows, r1 - r0);
+        max_ac_a = std::max(max_ac_a, A.row_ptr[r1] - A.row_ptr[r0]);
+        max_ac_c = std::max(max_ac_c, C.row_ptr[r1] - C.row_ptr[r0]);
+    }
+    for (size_t t = 0; t + 1 < p.b_cuts.size(); t++) {
+        max_b_rows = std::max(max_b_rows, p.b_cuts[t + 1] - p.b_cuts[t]);
+        max_b_nnz = std::max(max_b_nnz, B.row_ptr[p.b_cuts[t + 1]] - B.row_ptr[p.b_cuts[t]]);
+    }
+    const int nbuf_ac = p.algorithm == 2 ? 1 : 2, nbuf_b = p.algorithm == 2 ? 2 : 1;
+    PartBuf Ab[2], Cb[2], Bb[2];
+    bool ok = mm != nullptr;
+    for (int u = 0; u < nbuf_ac && ok; u++)
+        ok = take_part(ar, Ab[u], max_ac_rows, max_ac_a, vb) && take_part(ar, Cb[u], max_ac_rows, max_ac_c, vb);
+    for (int u = 0; u < nbuf_b && ok; u++) ok = take_part(ar, Bb[u], max_b_rows, max_b_nnz, vb);
+    if (!ok) {
+        set_error("chunked: parts do not fit the %zu-byte budget", budget);
+        return SPGEMM_ERR_BUDGET;
+    }
+    stats.device_bytes = (int64_t)ar.used;
+    int st = SPGEMM_OK;
+    const cudaStream_t si = env.s_in, so = env.s_out;
+    cudaEvent_t *ev = env.ev;   // [0..1] copied-in, [2..3] compute done, [4..5] copied-out
+    int *err = env.err;
+    auto fma = [&](const PartBuf &Ap, int64_t rows, int64_t lo, int64_t hi, const PartBuf &Bp,
+                   const PartBuf &Cp) -> int {
+        return dtype == SPGEMM_F64
+                   ? launch_fma<double>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c)
+                   : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c);
+    };
+    if (p.algorithm == 2) {
+        for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+            const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
+            const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
+            // the previous part's products must be done and its C part must have
+            // left the device before the buffers are reused
+            if (j > 0) {
+                SG_CUDA(cudaStreamWaitEvent(si, ev[6], 0));
+                SG_CUDA(cudaStreamWaitEvent(si, ev[4], 0));
+            }
+            stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[0].rp, Ab[0].col, Ab[0].val, si, &st);
+            SG_TRY(st);
+            // C starts empty: only its offsets come in
+            SG_CUDA(cudaMemcpyAsync(Cb[0].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
+            stats.h2d += (rows + 1) * 8;
+            if (rows > 0)
+                k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, si>>>(Cb[0].rp, rows + 1, C.row_ptr[r0]);
+            if (cn > 0) {
+                SG_CUDA(cudaMemsetAsync(Cb[0].col, 0xff, (size_t)cn * 4, si));
+                SG_CUDA(cudaMemsetAsync(Cb[0].val, 0, (size_t)cn * vb, si));
+            }
+            // column range of the A part decides which B parts it needs
+            const int init[2] = {INT_MAX, -1};
+            SG_CUDA(cudaMemcpyAsync(mm, init, 8, cudaMemcpyHostToDevice, si));
+            const int64_t an = A.row_ptr[r1] - A.row_ptr[r0];
+            if (an > 0)
+                k_col_range<<<(unsigned)std::min<int64_t>((an + 255) / 256, (int64_t)c.nsm * 8), 256, 0, si>>>(Ab[0].col, an, mm);
+            int hmm[2];
+            SG_CUDA(cudaMemcpyAsync(hmm, mm, 8, cudaMemcpyDeviceToHost, si));
+            SG_CUDA(cudaStreamSynchronize(si));
+            std::vector<size_t> need;
+            for (size_t t = 0; t + 1 < p.b_cuts.size(); t++)
+                if (hmm[1] >= 0 && p.b_cuts[t] <= hmm[1] && p.b_cuts[t + 1] > hmm[0]) need.push_back(t);
+            stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
+            // stream the needed B parts, double buffered
+            for (size_t u = 0; u < need.size(); u++) {
+                const int slot = (int)(u & 1);
+                const size_t t = need[u];
+                if (u >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[2 + slot], 0));
+                stats.h2d += copy_rows_in(B, p.b_cuts[t], p.b_cuts[t + 1], vb, Bb[slot].rp, Bb[slot].col,
+                                          Bb[slot].val, si, &st);
+                SG_TRY(st);
+                SG_CUDA(cudaEventRecord(ev[slot], si));
+                SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
+                SG_TRY(fma(Ab[0], rows, p.b_cuts[t], p.b_cuts[t + 1], Bb[slot], Cb[0]));
+                SG_CUDA(cudaEventRecord(ev[2 + slot], s));
+            }
+            // finished part of C back to host memory (after its offsets and
+            // initial state, copied on si, and every product, on s)
+            SG_CUDA(cudaEventRecord(ev[7], si));
+            SG_CUDA(cudaEventRecord(ev[6], s));
+            SG_CUDA(cudaStreamWaitEvent(so, ev[6], 0));
+            SG_CUDA(cudaStreamWaitEvent(so, ev[7], 0));
+            if (cn > 0) {
+                const int64_t p0 = C.row_ptr[r0];
+                SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[0].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
+                SG_CUDA(cudaMemcpyAsync((char *)C.values + (size_t)p0 * vb, Cb[0].val, (size_t)cn * vb,
+                                        cudaMemcpyDeviceToHost, so));
+                stats.d2h += cn * (4 + vb);
+            }
+            SG_CUDA(cudaEventRecord(ev[4], so));
+            SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
+        }
+    } else {
+        for (size_t t = 0; t + 1 < p.b_cuts.size(); t++) {
+            const int64_t b0 = p.b_cuts[t], b1 = p.b_cuts[t + 1];
+            SG_CUDA(cudaStreamWaitEvent(si, ev[6], 0));
+            stats.h2d += copy_rows_in(B, b0, b1, vb, Bb[0].rp, Bb[0].col, Bb[0].val, si, &st);
+            SG_TRY(st);
+            for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+                const int slot = (int)(j & 1);
+                const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
+                const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0], p0 = C.row_ptr[r0];
+                // this buffer's previous C part must have gone out first
+                SG_CUDA(cudaStreamWaitEvent(si, ev[4 + slot], 0));
+                stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st);
+                SG_TRY(st);
+                SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
+                stats.h2d += (rows + 1) * 8;
+                if (rows > 0)
+                    k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, si>>>(Cb[slot].rp, rows + 1, p0);
+                if (cn > 0) {
+                    if (t == 0) {
+                        SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, si));
+                        SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, si));
+                    } else {   // partial C from the previous B parts
+                        SG_CUDA(cudaMemcpyAsync(Cb[slot].col, C.col_idx + p0, (size_t)cn * 4, cudaMemcpyHostToDevice, si));
+                        SG_CUDA(cudaMemcpyAsync(Cb[slot].val, (const char *)C.values + (size_t)p0 * vb,
+                                                (size_t)cn * vb, cudaMemcpyHostToDevice, si));
+                        stats.h2d += cn * (4 + vb);
+                    }
+                }
+                SG_CUDA(cudaEventRecord(ev[slot], si));
+                SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
+                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[0], Cb[slot]));
+                SG_CUDA(cudaEventRecord(ev[2 + slot], s));
+                SG_CUDA(cudaStreamWaitEvent(so, ev[2 + slot], 0));
+                if (cn > 0) {
+                    SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[slot].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
+                    SG_CUDA(cudaMemcpyAsync((char *)C.values + (size_t)p0 * vb, Cb[slot].val, (size_t)cn * vb,
+                                            cudaMemcpyDeviceToHost, so));
+                    stats.d2h += cn * (4 + vb);
+                }
+                SG_CUDA(cudaEventRecord(ev[4 + slot], so));
+            }
+            // the next B part may only overwrite the buffer once every use of it is done
+            SG_CUDA(cudaEventRecord(ev[6], s));
+        }
+        SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
+        SG_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
+    }
+    SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
+    return SPGEMM_OK;
+}
+
+int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, int64_t *C_row_ptr,
+                     int64_t *nnz_C, size_t budget, ChunkStats &stats) {
+    Ctx &c = *env.ctx;
+    const cudaStream_t s = c.s, si = env.s_in;
+    const int64_t nwords = (B.ncols + 31) / 32;
+    // pattern-only sizes; C contributes its offsets only
+    std::vector<int64_t> zeros((size_t)A.nrows + 1, 0);
+    ChunkPlan p;
+    const size_t bitmap = r256((size_t)c.nsm * (size_t)nwords * 4);
+    const size_t reserve = bitmap + 4096;
+    if (budget <= reserve) {
+        set_error("chunked symbolic: budget %zu below the fixed working set %zu", budget, reserve);
+        return SPGEMM_ERR_BUDGET;
+    }
+    int64_t fast = (int64_t)(budget - reserve);
+    SG_TRY(plan_chunks(A.row_ptr, A.nrows, zeros.data(), B.row_ptr, B.nrows, 0, 0, fast, p));
+    if (p.b_cuts.size() != 2) {
+        set_error("chunked symbolic: the pattern of B (%lld bytes) must fit the budget's large portion",
+                  (long long)p.size_b);
+        return SPGEMM_ERR_BUDGET;
+    }
+    // A parts are double buffered: shrink them until B + 2 parts fit
+    int64_t max_rows = 0, max_nnz = 0;
+    for (int iter = 0; iter < 16; iter++) {
+        max_rows = max_nnz = 0;
+        for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+            max_rows = std::max(max_rows, p.ac_cuts[j + 1] - p.ac_cuts[j]);
+            max_nnz = std::max(max_nnz, A.row_ptr[p.ac_cuts[j + 1]] - A.row_ptr[p.ac_cuts[j]]);
+        }
+        const size_t need = r256((size_t)(B.nrows + 1) * 8) + r256((size_t)std::max<int64_t>(B.nnz, 1) * 4) +
+                            2 * (r256((size_t)(max_rows + 1) * 8) + r256((size_t)std::max<int64_t>(max_nnz, 1) * 4) +
+                                 r256((size_t)max_rows * 8)) + reserve + 1024;
+        if (need <= budget) break;
+        fast = fast * 3 / 4;
+        SG_TRY(plan_chunks(A.row_ptr, A.nrows, zeros.data(), B.row_ptr, B.nrows, 0, 0, fast, p));
+        if (p.b_cuts.size() != 2 || iter == 15) {
+            set_error("chunked symbolic: budget %zu too small", budget);
+            return SPGEMM_ERR_BUDGET;
+        }
+    }
+    stats.algorithm = p.algorithm;
+    stats.branch = p.branch;
+    stats.n_ac = (int64_t)p.ac_cuts.size() - 1;
+    stats.n_b = 1;
+    Arena ar{(char *)env.arena, budget, 0};
+    unsigned *bits = (unsigned *)ar.take(bitmap);
+    int *ovf = (int *)ar.take(16);
+    PartBuf Bp, Ap[2];
+    int64_t *cnt[2];
+    bool ok = bits && ovf && take_part(ar, Bp, B.nrows, B.nnz, 0);
+    for (int u = 0; u < 2 && ok; u++) {
+        ok = take_part(ar, Ap[u], max_rows, max_nnz, 0);
+        cnt[u] = (int64_t *)ar.take((size_t)std::max<int64_t>(max_rows, 1) * 8);
+        ok = ok && cnt[u];
+    }
+    if (!ok) {
+        set_error("chunked symbolic: parts do not fit the %zu-byte budget", budget);
+        return SPGEMM_ERR_BUDGET;
+    }
+    stats.device_bytes = (int64_t)ar.used;
+    int st = SPGEMM_OK;
+    stats.h2d += copy_rows_in(B, 0, B.nrows, 0, Bp.rp, Bp.col, nullptr, si, &st);
+    SG_TRY(st);
+    SG_CUDA(cudaEventRecord(env.ev[6], si));
+    SG_CUDA(cudaStreamWaitEvent(s, env.ev[6], 0));
+    std::vector<int64_t> hcnt((size_t)std::max<int64_t>(max_rows, 1));
+    int64_t carry = 0;
+    C_row_ptr[0] = 0;
+    const size_t smem = (size_t)CNT_WPB * CNT_S * 4;
+    SG_CUDA(cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+        const int slot = (int)(j & 1);
+        const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
+        if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, env.ev[2 + slot], 0));
+        stats.h2d += copy_rows_in(A, r0, r1, 0, Ap[slot].rp, Ap[slot].col, nullptr, si, &st);
+        SG_TRY(st);
+        SG_CUDA(cudaEventRecord(env.ev[slot], si));
+        SG_CUDA(cudaStreamWaitEvent(s, env.ev[slot], 0));
+        if (rows == 0) continue;
+        SG_CUDA(cudaMemsetAsync(ovf, 0, 4, s));
+        const int64_t blocks = std::min<int64_t>((rows + CNT_WPB - 1) / CNT_WPB, (int64_t)c.nsm * 16);
+        c.begin("chunked.count", rows);
+        k_count_warp<<<(unsigned)blocks, 256, smem, s>>>(rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col,
+                                                         cnt[slot], ovf);
+        c.end();
+        SG_CUDA(cudaGetLastError());
+        int hovf = 0;
+        SG_CUDA(cudaMemcpyAsync(&hovf, ovf, 4, cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaStreamSynchronize(s));
+        if (hovf > 0) {
+            c.begin("chunked.count_bitmap", rows);
+            k_count_bitmap<<<(unsigned)std::min<int64_t>(rows, (int64_t)c.nsm), 256, 0, s>>>(
+                rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col, cnt[slot], nwords, bits);
+            c.end();
+            SG_CUDA(cudaGetLastError());
+        }
+        SG_CUDA(cudaMemcpyAsync(hcnt.data(), cnt[slot], (size_t)rows * 8, cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaEventRecord(env.ev[2 + slot], s));
+        SG_CUDA(cudaStreamSynchronize(s));
+        stats.d2h += rows * 8;
+        for (int64_t r = 0; r < rows; r++) {
+            carry += hcnt[(size_t)r];
+            C_row_ptr[r0 + r + 1] = carry;
+        }
+    }
+    *nnz_C = carry;
+    return SPGEMM_OK;
+}
+
+}  // namespace sg

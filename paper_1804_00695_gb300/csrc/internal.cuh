@@ -169,5 +169,26 @@ struct ChunkPlan {
 };
 int plan_chunks(const int64_t *a_rp, int64_t n_ac, const int64_t *c_rp, const int64_t *b_rp,
                 int64_t n_b, int vb_ac, int vb_b, int64_t fast, ChunkPlan &p);
+// BinarySearch cuts of one matrix (rp2 null) or a row-aligned pair.
+bool cut_rows(const int64_t *rp1, const int64_t *rp2, int64_t n, int vb, double psize,
+              std::vector<int64_t> &cuts);
+
+// chunked.cu: Algorithms 2 and 3 with host operands.
+struct ChunkEnv {
+    Ctx *ctx = nullptr;
+    void *arena = nullptr;        // exactly the budget, device
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev[8] = {};
+    int *err = nullptr;
+};
+struct ChunkStats {
+    int algorithm = 0, branch = 0;
+    int64_t n_ac = 0, n_b = 0, cost1 = 0, cost2 = 0, h2d = 0, d2h = 0, skipped_b = 0,
+            device_bytes = 0;
+};
+int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_csr &B,
+                    spgemm_csr &C, size_t budget, ChunkStats &stats);
+int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, int64_t *C_row_ptr,
+                     int64_t *nnz_C, size_t budget, ChunkStats &stats);
 
 }  // namespace sg

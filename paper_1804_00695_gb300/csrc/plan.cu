@@ -62,6 +62,12 @@ static bool binary_search(const SizeFn &f, int64_t nrows, double psize,
     return true;
 }
 
+bool cut_rows(const int64_t *rp1, const int64_t *rp2, int64_t n, int vb, double psize,
+              std::vector<int64_t> &cuts) {
+    SizeFn f{rp1, rp2, vb, vb};
+    return binary_search(f, n, psize, cuts);
+}
+
 static double balanced(int64_t total, double portion) {
     double np = std::ceil((double)total / portion);
     if (np < 1) np = 1;

@@ -1,0 +1,153 @@
+"""GPU parity of the chunked product (Section 3.3.1, Algorithms 2-4) with
+operands in host memory: the result equals the oracle (pattern exact, values
+within tolerance) for budgets from "everything fits" down to many parts,
+both loop orders run, and the bytes copied follow the copy-cost formulas."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1804_00695_gb300 as sg
+from oracle import chunking as CH
+from paper_1804_00695_gb300 import inputs as I
+from gpu_helpers import TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h(cuda_lib):
+    return sg.Handle()
+
+
+def check(c, ref, tag):
+    assert np.array_equal(c.row_ptr.numpy(), ref.row_ptr)
+    assert np.array_equal(c.col.numpy(), ref.col)
+    err = np.abs(c.val.double().numpy() - ref.val)
+    assert np.all(err <= TOL[tag] * ref.bound)
+
+
+def find_budget(a, c_rp, b, vb, alg, min_ac=1, min_b=1):
+    """A budget whose Algorithm 4 plan uses `alg` with at least the given
+    numbers of parts (searched on the CPU with the native planner)."""
+    tot = sum(CH.range_bytes(x, 0, len(x) - 1, vb) for x in (a, c_rp, b))
+    for frac in np.geomspace(3.0, 0.02, 160):
+        f = int(tot * frac)
+        try:
+            p = sg.plan_chunks(a, c_rp, b, vb, f)
+        except sg.SpgemmError:
+            continue
+        if p["algorithm"] == alg and len(p["p_ac"]) >= min_ac and len(p["p_b"]) >= min_b:
+            return f, p
+    return None, None
+
+
+@pytest.mark.parametrize("dtype,tag", [(np.float64, "f64"), (np.float32, "f32")])
+def test_chunked_everything_fits(h, dtype, tag):
+    a, p, r = I.galerkin_problem(12)
+    A, P = sg.HostCsr.from_numpy(a, dtype), sg.HostCsr.from_numpy(p, dtype)
+    c = h.chunked(A, P, 1 << 28)
+    ref = oracle.spgemm(I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, a.val.astype(dtype).astype(np.float64)),
+                        I.Csr(p.nrows, p.ncols, p.row_ptr, p.col, p.val.astype(dtype).astype(np.float64)))
+    check(c, ref, tag)
+    st = h.chunked_stats()
+    assert st["n_ac"] == 1 and st["n_b"] == 1
+
+
+def expected_bytes(st, a, b, c_rp, nnz_c, vb=8):
+    """Bytes Algorithm 3 copies for the plan the driver reports: B once, A
+    and C offsets every pass, C entries in after the first pass and out every
+    pass; each extra part boundary re-sends one 8-byte offset.  (The paper
+    counts size(C)(|P_B|-1) for C; the copies out are counted here too.)"""
+    nac, nb = st["n_ac"], st["n_b"]
+    sa = CH.range_bytes(a.row_ptr, 0, a.nrows, vb)
+    sb = CH.range_bytes(b.row_ptr, 0, b.nrows, vb)
+    ent = nnz_c * (4 + vb)
+    assert st["algorithm"] == 3   # Algorithm 2 bytes depend on skipped parts: formula test below
+    h2d = (sb + 8 * (nb - 1)) + nb * (sa + 8 * (nac - 1)) + nb * (a.nrows + nac) * 8 + (nb - 1) * ent
+    return h2d, nb * ent
+
+
+def run_chunked(h, a, b, budget):
+    ref = oracle.spgemm(a, b)
+    A, B = sg.HostCsr.from_numpy(a), sg.HostCsr.from_numpy(b)
+    rp, nnz = h.chunked_symbolic(A, B, max(budget, 1 << 22))
+    assert np.array_equal(rp.numpy(), ref.row_ptr) and nnz == ref.nnz
+    c = h.chunked_numeric(A, B, rp, nnz, budget)
+    check(c, ref, "f64")
+    return ref, h.chunked_stats()
+
+
+def test_chunked_many_parts(h):
+    """Random unsorted matrices, many parts on both sides."""
+    a = I.random_csr(900, 700, 0.02, 71, shuffle_cols=True)
+    b = I.random_csr(700, 800, 0.03, 72, shuffle_cols=True)
+    ref = oracle.spgemm(a, b)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, b.row_ptr, 8, 2, 2, 2)
+    assert budget is not None
+    ref, st = run_chunked(h, a, b, budget)
+    assert st["n_ac"] >= 2 and st["n_b"] >= 2
+
+
+def test_chunked_alg3_b_larger(h):
+    """B much larger than A and C: Algorithm 3 with several parts of B, so
+    partial rows of C go out and come back in."""
+    a = I.random_csr(200, 20000, 0.0005, 83, shuffle_cols=True)
+    b = I.random_csr(20000, 300, 0.033, 84, shuffle_cols=True)
+    ref = oracle.spgemm(a, b)
+    # the driver re-plans on a smaller budget to double buffer, so try the
+    # budgets for which the plain plan is Algorithm 3 until the driver's is
+    tot = sum(CH.range_bytes(x, 0, len(x) - 1, 8) for x in (a.row_ptr, ref.row_ptr, b.row_ptr))
+    hit = False
+    for frac in np.geomspace(0.2, 0.04, 30):
+        f = int(tot * frac)
+        try:
+            p = sg.plan_chunks(a.row_ptr, ref.row_ptr, b.row_ptr, 8, f)
+        except sg.SpgemmError:
+            continue
+        if p["algorithm"] != 3 or len(p["p_b"]) < 2:
+            continue
+        try:
+            ref, st = run_chunked(h, a, b, f)
+        except sg.SpgemmError as e:
+            assert e.status == 5
+            continue
+        if st["algorithm"] == 3 and st["n_b"] >= 2:
+            h2d, d2h = expected_bytes(st, a, b, ref.row_ptr, ref.nnz)
+            assert st["h2d_bytes"] == h2d and st["d2h_bytes"] == d2h
+            hit = True
+            break
+    assert hit
+
+
+def test_chunked_alg2_bytes_match_formula(h):
+    """Algorithm 2 with every B part needed: bytes = size(A) + size(C) +
+    size(B)|P_AC| (the paper's copy cost) plus 8 bytes per extra boundary."""
+    a = I.random_csr(1500, 400, 0.05, 91)
+    b = I.random_csr(400, 600, 0.04, 92)
+    ref = oracle.spgemm(a, b)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, b.row_ptr, 8, 2, 2, 2)
+    assert budget is not None
+    ref, st = run_chunked(h, a, b, budget)
+    assert st["algorithm"] == 2 and st["skipped_b_parts"] == 0
+    nac, nb = st["n_ac"], st["n_b"]
+    extra = 2 * 8 * (nac - 1) + 8 * (nb - 1) * nac
+    assert st["h2d_bytes"] + st["d2h_bytes"] == st["cost_chunk1"] + extra
+
+
+def test_chunked_banded_skips_b_parts(h):
+    """A banded operand (3D 27-point Laplacian): parts of B outside the A
+    part's column range are skipped; the product is unchanged."""
+    a = I.laplace3d_27pt(14)
+    ref = oracle.spgemm(a, a)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, a.row_ptr, 8, 2, 3, 4)
+    assert budget is not None
+    ref, st = run_chunked(h, a, a, budget)
+    assert st["algorithm"] == 2 and st["skipped_b_parts"] > 0
+
+
+def test_chunked_budget_errors(h):
+    a = I.random_csr(50, 40, 0.2, 95)
+    A = sg.HostCsr.from_numpy(a)
+    with pytest.raises(sg.SpgemmError) as ei:
+        h.chunked(A, sg.HostCsr.from_numpy(I.random_csr(40, 30, 0.2, 96)), 512)
+    assert ei.value.status == 5
