@@ -197,6 +197,28 @@ SPGEMM_API int spgemm_chunked_numeric(spgemm_handle handle, int dtype, const spg
                                       void *stream);
 SPGEMM_API int spgemm_chunked_stats(spgemm_handle handle, spgemm_chunk_stats *out);
 
+/* Row offsets from per-row counts, allocating nothing (this entry point
+ * has no counterpart in the paper; it exposes the symbolic phase's scan step
+ * for callers that may not allocate device memory: code inside CUDA stream
+ * capture, callers whose device memory belongs to another allocator, and
+ * paths that cannot afford cudaMalloc's implicit synchronisation).
+ * row_ptr: device, nrows+1 int64, the count of row i in row_ptr[i+1]
+ * (row_ptr[0] is ignored); on completion row_ptr holds the exclusive prefix
+ * (row_ptr[0] = 0, row_ptr[nrows] = total).  No handle is needed.  The
+ * scratch is a fixed device array of 512 KiB that every device loading the
+ * library holds until exit; it serves up to
+ * spgemm_row_offsets_noalloc_max_rows() rows (about 134 million); a larger
+ * nrows is rejected with SPGEMM_ERR_ARG before anything runs.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * The stream must belong to the current device.  Asynchronous; calls share
+ * the scratch, so calls that overlap on the GPU (different streams, not
+ * ordered) race and must be avoided; each call overwrites all the scratch it
+ * reads, so nothing needs clearing between calls.  Calls no cudaMalloc,
+ * cudaFree or allocating routine. */
+SPGEMM_API int spgemm_row_offsets_noalloc(int64_t *row_ptr, int64_t nrows, void *stream);
+SPGEMM_API int64_t spgemm_row_offsets_noalloc_max_rows(void);
+
 /* Synchronises `stream` and reports device-side errors raised by earlier
  * asynchronous calls on this handle (SPGEMM_ERR_INTERNAL if a hash probe
  * bound was exceeded or a row's column count disagreed with the symbolic

@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked_symbolic": ([p, p, p, p, C.POINTER(i64), C.c_size_t, p], i32),
         "spgemm_chunked_numeric": ([p, i32, p, p, p, C.c_size_t, p], i32),
         "spgemm_chunked_stats": ([p, p], i32),
+        "spgemm_row_offsets_noalloc": ([p, i64, p], i32),
+        "spgemm_row_offsets_noalloc_max_rows": ([], i64),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
