@@ -197,6 +197,20 @@ SPGEMM_API int spgemm_chunked_numeric(spgemm_handle handle, int dtype, const spg
                                       void *stream);
 SPGEMM_API int spgemm_chunked_stats(spgemm_handle handle, spgemm_chunk_stats *out);
 
+/* Backward of C = A*B for a scalar loss L with dC = dL/dC given on the
+ * pattern of C: the product is bilinear, so
+ *   dA_ik = sum over stored b_kj of dC_ij b_kj   (dC B^T restricted to the pattern of A)
+ *   dB_kj = sum over stored a_ik of a_ik dC_ij   (A^T dC restricted to the pattern of B)
+ * A, B: device CSR (values of B needed for dA, values of A for dB); C: the
+ * pattern of A*B as produced by spgemm_numeric (ascending columns) with
+ * C->values = dC.  dA_values (A->nnz) and dB_values (B->nnz) are device
+ * outputs, either may be NULL; both are overwritten.  One pass over the
+ * forward products, each dC_ij found by binary search in row i of C; dB is
+ * accumulated with atomic adds.  Asynchronous; a product missing from the
+ * pattern of C is reported by spgemm_check (SPGEMM_ERR_INTERNAL). */
+SPGEMM_API int spgemm_backward(spgemm_handle handle, int dtype, const spgemm_csr *A, const spgemm_csr *B,
+                               const spgemm_csr *C, void *dA_values, void *dB_values, void *stream);
+
 /* Row offsets from per-row counts, allocating nothing (this entry point
  * has no counterpart in the paper; it exposes the symbolic phase's scan step
  * for callers that may not allocate device memory: code inside CUDA stream

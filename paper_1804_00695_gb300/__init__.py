@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked_symbolic": ([p, p, p, p, C.POINTER(i64), C.c_size_t, p], i32),
         "spgemm_chunked_numeric": ([p, i32, p, p, p, C.c_size_t, p], i32),
         "spgemm_chunked_stats": ([p, p], i32),
+        "spgemm_backward": ([p, i32, p, p, p, p, p, p], i32),
         "spgemm_row_offsets_noalloc": ([p, i64, p], i32),
         "spgemm_row_offsets_noalloc_max_rows": ([], i64),
     }
@@ -227,6 +228,20 @@ class Handle:
         rp, nnz = self.symbolic(A, B, stream)
         return self.numeric(A, B, rp, nnz, stream)
 
+    def backward(self, A: Csr, B: Csr, Cm: Csr, dC, need_a: bool = True, need_b: bool = True,
+                 stream=None):
+        """(dA values on pattern(A), dB values on pattern(B)) for dC given on
+        the pattern of C = A*B."""
+        torch = _torch()
+        da = torch.empty_like(A.val) if need_a else None
+        db = torch.empty_like(B.val) if need_b else None
+        dcm = Csr(Cm.nrows, Cm.ncols, Cm.row_ptr, Cm.col, dC.contiguous())
+        d1, d2, d3 = A.desc(), B.desc(), dcm.desc()
+        _check(_lib.spgemm_backward(self._h, A.dtype_code(), C.byref(d1), C.byref(d2), C.byref(d3),
+                                    da.data_ptr() if da is not None else None,
+                                    db.data_ptr() if db is not None else None, _stream(stream)))
+        return da, db
+
     def check(self, stream=None):
         _check(_lib.spgemm_check(self._h, _stream(stream)))
 
@@ -354,3 +369,51 @@ def bin_of(keys: int, flops: int) -> int:
 def spgemm(A: Csr, B: Csr, stream=None) -> Csr:
     """C = A*B with both phases on the current device's default handle."""
     return default_handle().spgemm(A, B, stream)
+
+
+def _autograd_class():
+    torch = _torch()
+
+    class SpGEMMFunction(torch.autograd.Function):
+        """C = A*B with a hand-written backward: dA = (dC B^T) on the pattern
+        of A and dB = (A^T dC) on the pattern of B, computed by the
+        library's backward kernel (no dense intermediates)."""
+
+        @staticmethod
+        def forward(ctx, a_val, b_val, a_rp, a_col, b_rp, b_col, shape, handle):
+            m, k, n = shape
+            A = Csr(m, k, a_rp, a_col, a_val.detach())
+            B = Csr(k, n, b_rp, b_col, b_val.detach())
+            Cm = handle.spgemm(A, B)
+            ctx.save_for_backward(a_val, b_val, a_rp, a_col, b_rp, b_col, Cm.row_ptr, Cm.col)
+            ctx.shape, ctx.handle = shape, handle
+            ctx.mark_non_differentiable(Cm.row_ptr, Cm.col)
+            return Cm.row_ptr, Cm.col, Cm.val
+
+        @staticmethod
+        def backward(ctx, g_rp, g_col, g_val):
+            a_val, b_val, a_rp, a_col, b_rp, b_col, c_rp, c_col = ctx.saved_tensors
+            m, k, n = ctx.shape
+            A = Csr(m, k, a_rp, a_col, a_val.detach())
+            B = Csr(k, n, b_rp, b_col, b_val.detach())
+            Cm = Csr(m, n, c_rp, c_col, None)
+            if g_val is None:
+                return (None,) * 8
+            da, db = ctx.handle.backward(A, B, Cm, g_val, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+            return da, db, None, None, None, None, None, None
+
+    return SpGEMMFunction
+
+
+_fn = None
+
+
+def spgemm_autograd(A: Csr, B: Csr, handle: "Handle" = None) -> Csr:
+    """Differentiable C = A*B: gradients flow to A.val and B.val."""
+    global _fn
+    if _fn is None:
+        _fn = _autograd_class()
+    h = handle or default_handle()
+    rp, col, val = _fn.apply(A.val, B.val, A.row_ptr, A.col, B.row_ptr, B.col,
+                             (A.nrows, A.ncols, B.ncols), h)
+    return Csr(A.nrows, B.ncols, rp, col, val)

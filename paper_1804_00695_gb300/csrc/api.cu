@@ -456,6 +456,24 @@ int spgemm_chunked_stats(spgemm_handle h, spgemm_chunk_stats *out) {
     return SPGEMM_OK;
 }
 
+int spgemm_backward(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_csr *B,
+                    const spgemm_csr *C, void *dA_values, void *dB_values, void *stream) {
+    if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) { set_error("bad dtype %d", dtype); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", dB_values != nullptr));
+    SG_TRY(check_csr(B, "B", dA_values != nullptr));
+    SG_TRY(check_csr(C, "C (values = dC)", true));
+    if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) {
+        set_error("dimension mismatch");
+        return SPGEMM_ERR_DIM;
+    }
+    if (!dA_values && !dB_values) return SPGEMM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    Ctx c = h->ctx(s);
+    return launch_backward(dtype, *A, *B, *C, dA_values, dB_values, &h->dstate->err, c);
+}
+
 int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
     if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
     switch (option) {

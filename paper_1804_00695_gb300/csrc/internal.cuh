@@ -161,6 +161,10 @@ int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm
                    size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c);
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype);
 
+// backward.cu: dA on pattern(A), dB on pattern(B) from dC on pattern(C).
+int launch_backward(int dtype, const spgemm_csr &A, const spgemm_csr &B, const spgemm_csr &C, void *da,
+                    void *db, int *err, Ctx &c);
+
 // plan.cu: Algorithm 4.  Cuts are part boundaries (first 0, last nrows).
 struct ChunkPlan {
     int algorithm = 0, branch = 0;

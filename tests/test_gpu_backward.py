@@ -1,0 +1,83 @@
+"""GPU parity of the backward kernel and the autograd Function: dA and dB
+against the oracle gradient, the bilinear identity <dA,A> = <dC,C> = <dB,B>,
+and torch.autograd through the library."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1804_00695_gb300 as sg
+from paper_1804_00695_gb300 import inputs as I
+from gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h(cuda_lib):
+    return sg.Handle()
+
+
+def grads(h, a, b, dtype, seed):
+    import torch
+    A, B = to_dev(a, dtype), to_dev(b, dtype)
+    C = h.spgemm(A, B)
+    dc = (I.uniform01(np.arange(C.nnz, dtype=np.uint64), seed) * 2 - 1).astype(dtype)
+    da, db = h.backward(A, B, C, torch.from_numpy(dc).cuda())
+    h.check()
+    ref = oracle.spgemm(I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, a.val.astype(dtype).astype(np.float64)),
+                        I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, b.val.astype(dtype).astype(np.float64)))
+    ra, rb = oracle.backward(I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, a.val.astype(dtype).astype(np.float64)),
+                             I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, b.val.astype(dtype).astype(np.float64)),
+                             ref.row_ptr, ref.col, dc.astype(np.float64))
+    return da.double().cpu().numpy(), db.double().cpu().numpy(), ra, rb, dc, ref
+
+
+def bound_a(a, b, ref, dc):
+    """sum over terms of |dC_ij||b_kj| per entry of A (tolerance scale)."""
+    absd = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, np.abs(b.val.astype(np.float64)))
+    dct = I.Csr(ref.nrows, ref.ncols, ref.row_ptr, ref.col, np.abs(dc.astype(np.float64)))
+    ba, _ = oracle.backward(I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.ones(a.nnz)), absd,
+                            ref.row_ptr, ref.col, dct.val)
+    return ba
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 1e-5)])
+@pytest.mark.parametrize("case", ["random", "batch_like", "galerkin"])
+def test_backward_matches_oracle(h, dtype, tol, case):
+    if case == "random":
+        a = I.random_csr(300, 200, 0.04, 11, shuffle_cols=True)
+        b = I.random_csr(200, 250, 0.05, 12, shuffle_cols=True)
+    elif case == "batch_like":
+        a = I.random_square(3000, 21, dtype=np.float64)
+        b = I.random_square(3000, 22, dtype=np.float64)
+    else:
+        a, b, _ = I.galerkin_problem(10)
+    da, db, ra, rb, dc, ref = grads(h, a, b, dtype, 13)
+    ba = bound_a(a, b, ref, dc)
+    assert np.all(np.abs(da - ra) <= tol * ba + 1e-300)
+    # dB: each entry sums |a_ik||dC_ij| terms; scale by the same kind of bound
+    absa = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.abs(a.val.astype(dtype).astype(np.float64)))
+    _, bb = oracle.backward(absa, I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, np.ones(b.nnz)),
+                            ref.row_ptr, ref.col, np.abs(dc.astype(np.float64)))
+    assert np.all(np.abs(db - rb) <= tol * bb + 1e-300)
+    # Euler identity of the bilinear form on the device results
+    lc = float(dc.astype(np.float64) @ ref.val)
+    scale = float(np.abs(dc.astype(np.float64)) @ ref.bound)
+    assert abs(da @ a.val.astype(dtype).astype(np.float64) - lc) <= 10 * tol * scale
+    assert abs(db @ b.val.astype(dtype).astype(np.float64) - lc) <= 10 * tol * scale
+
+
+def test_autograd_function(h):
+    import torch
+    a = I.random_csr(120, 90, 0.05, 21)
+    b = I.random_csr(90, 80, 0.06, 22)
+    A, B = to_dev(a), to_dev(b)
+    A.val.requires_grad_(True)
+    B.val.requires_grad_(True)
+    C = sg.spgemm_autograd(A, B, h)
+    w = torch.linspace(-1, 1, C.nnz, dtype=torch.float64, device="cuda")
+    loss = (C.val * w).sum()
+    loss.backward()
+    ra, rb = oracle.backward(a, b, C.row_ptr.cpu().numpy(), C.col.cpu().numpy(), w.cpu().numpy())
+    assert np.allclose(A.val.grad.cpu().numpy(), ra, rtol=1e-10, atol=1e-12)
+    assert np.allclose(B.val.grad.cpu().numpy(), rb, rtol=1e-10, atol=1e-12)
