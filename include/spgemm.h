@@ -120,12 +120,19 @@ SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr 
  *    (zeros excepted) and rows wider than 128 entries accumulate in native
  *    FP64.  1 = native FP64 everywhere.
  *  SPGEMM_OPT_LANES_NUMERIC / SPGEMM_OPT_LANES_SYMBOLIC (0, 4, 8, 16, 32;
- *    default 0 = from the mean row length of B): lanes that share a row in
- *    the kernels for rows with few outputs. */
+ *    default 0 = from the mean products per row): lanes that share a row in
+ *    the kernels for rows with few outputs (a warp holds 32/lanes rows).
+ *  SPGEMM_OPT_SMALL_CAP (16 or 32, default 32): the largest output row the
+ *    small-row numeric kernel takes; larger rows go to a warp each.
+ *  SPGEMM_OPT_SLOT_FACTOR (2 or 4, default 2): hash-map slots per output
+ *    entry in the small-row numeric kernel.
+ * spgemm_autotune picks the last three by timing. */
 typedef enum spgemm_option {
     SPGEMM_OPT_F64_NATIVE = 1,
     SPGEMM_OPT_LANES_NUMERIC = 2,
-    SPGEMM_OPT_LANES_SYMBOLIC = 3
+    SPGEMM_OPT_LANES_SYMBOLIC = 3,
+    SPGEMM_OPT_SMALL_CAP = 4,
+    SPGEMM_OPT_SLOT_FACTOR = 5
 } spgemm_option;
 SPGEMM_API int spgemm_set_option(spgemm_handle handle, int option, int64_t value);
 
@@ -210,6 +217,36 @@ SPGEMM_API int spgemm_chunked_stats(spgemm_handle handle, spgemm_chunk_stats *ou
  * pattern of C is reported by spgemm_check (SPGEMM_ERR_INTERNAL). */
 SPGEMM_API int spgemm_backward(spgemm_handle handle, int dtype, const spgemm_csr *A, const spgemm_csr *B,
                                const spgemm_csr *C, void *dA_values, void *dB_values, void *stream);
+
+/* Batched products C_i = A_i * B_i, i < nbatch (<= 65535), run as one
+ * product of block-diagonal operands so that every kernel takes all
+ * instances in one launch.  A and B are host arrays of nbatch descriptors of
+ * device matrices (row_ptr[0] == 0).  The output is the stacked C: rows of
+ * instance i follow those of instance i-1, columns are local to the
+ * instance; C_row_ptr: device, sum of nrows(A_i) + 1 int64.
+ * spgemm_batched_symbolic also returns nnz(C) in *nnz_total and, if inst_nnz
+ * (host, nbatch) is not NULL, nnz(C_i) per instance; synchronises.
+ * spgemm_batched_numeric needs the same instance patterns as the symbolic
+ * call on this handle; values may live in other arrays between calls (the
+ * instance table is re-sent then).  With unchanged arrays it issues only
+ * kernel launches on `stream` (no synchronisation, no allocation), so it can
+ * be captured in a CUDA graph and replayed.
+ * spgemm_batched_backward: dA and dB (stacked over instances, device) for
+ * dC given as C->values on the stacked pattern of the last batched product. */
+SPGEMM_API int spgemm_batched_symbolic(spgemm_handle handle, int nbatch, const spgemm_csr *A,
+                                       const spgemm_csr *B, int64_t *C_row_ptr, int64_t *nnz_total,
+                                       int64_t *inst_nnz, void *stream);
+SPGEMM_API int spgemm_batched_numeric(spgemm_handle handle, int dtype, int nbatch, const spgemm_csr *A,
+                                      const spgemm_csr *B, spgemm_csr *C, void *stream);
+SPGEMM_API int spgemm_batched_backward(spgemm_handle handle, int dtype, const spgemm_csr *C,
+                                       void *dA_values, void *dB_values, void *stream);
+
+/* Autotuner: times `reps` runs of the last spgemm_numeric call on this handle
+ * (same arguments; C is overwritten) under every combination of lanes per row
+ * (8, 16, 32), small-row cap (16, 32) and map slots per entry (2, 4), keeps
+ * the fastest as the handle's options and leaves C computed with it.
+ * choice (host, 3): lanes, cap, slots; *best_ms: its time.  Synchronises. */
+SPGEMM_API int spgemm_autotune(spgemm_handle handle, int reps, int64_t *choice, float *best_ms, void *stream);
 
 /* Row offsets from per-row counts, allocating nothing (this entry point
  * has no counterpart in the paper; it exposes the symbolic phase's scan step

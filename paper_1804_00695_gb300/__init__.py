@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libspgemm_gb300.so")
 
 F32, F64 = 0, 1
 NBINS = 8
-OPT_F64_NATIVE, OPT_LANES_NUMERIC, OPT_LANES_SYMBOLIC = 1, 2, 3
+OPT_F64_NATIVE, OPT_LANES_NUMERIC, OPT_LANES_SYMBOLIC, OPT_SMALL_CAP, OPT_SLOT_FACTOR = 1, 2, 3, 4, 5
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_DIM", 3: "ERR_INDEX", 4: "ERR_NOMEM", 5: "ERR_BUDGET",
           6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_NOT_SYMBOLIC", 9: "ERR_INTERNAL"}
 
@@ -93,6 +93,10 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked_numeric": ([p, i32, p, p, p, C.c_size_t, p], i32),
         "spgemm_chunked_stats": ([p, p], i32),
         "spgemm_backward": ([p, i32, p, p, p, p, p, p], i32),
+        "spgemm_batched_symbolic": ([p, i32, p, p, p, C.POINTER(i64), p, p], i32),
+        "spgemm_batched_numeric": ([p, i32, i32, p, p, p, p], i32),
+        "spgemm_batched_backward": ([p, i32, p, p, p, p], i32),
+        "spgemm_autotune": ([p, i32, p, C.POINTER(C.c_float), p], i32),
         "spgemm_row_offsets_noalloc": ([p, i64, p], i32),
         "spgemm_row_offsets_noalloc_max_rows": ([], i64),
     }
@@ -241,6 +245,15 @@ class Handle:
                                     da.data_ptr() if da is not None else None,
                                     db.data_ptr() if db is not None else None, _stream(stream)))
         return da, db
+
+    # -- tuning -------------------------------------------------------------------
+    def autotune(self, reps: int = 3, stream=None):
+        """Time the last numeric call under every tunable setting; keep the
+        fastest.  Returns ((lanes, small_cap, slot_factor), ms)."""
+        ch = (C.c_int64 * 3)()
+        ms = C.c_float()
+        _check(_lib.spgemm_autotune(self._h, reps, ch, C.byref(ms), _stream(stream)))
+        return (int(ch[0]), int(ch[1]), int(ch[2])), float(ms.value)
 
     def check(self, stream=None):
         _check(_lib.spgemm_check(self._h, _stream(stream)))
@@ -417,3 +430,88 @@ def spgemm_autograd(A: Csr, B: Csr, handle: "Handle" = None) -> Csr:
     rp, col, val = _fn.apply(A.val, B.val, A.row_ptr, A.col, B.row_ptr, B.col,
                              (A.nrows, A.ncols, B.ncols), h)
     return Csr(A.nrows, B.ncols, rp, col, val)
+
+
+class Batch:
+    """nbatch independent products A_i * B_i run as one product of
+    block-diagonal operands (one launch per kernel for all instances).
+    The result is stacked: rows of instance i after those of i-1, columns
+    local to the instance."""
+
+    def __init__(self, handle: "Handle", As, Bs):
+        self.h = handle
+        self.As, self.Bs = list(As), list(Bs)
+        self.n = len(self.As)
+        self._arrays()
+
+    def _arrays(self):
+        self.da = (CsrDesc * max(self.n, 1))(*[a.desc() for a in self.As])
+        self.db = (CsrDesc * max(self.n, 1))(*[b.desc() for b in self.Bs])
+
+    @property
+    def rows(self):
+        return sum(a.nrows for a in self.As)
+
+    def symbolic(self, stream=None):
+        torch = _torch()
+        dev = self.As[0].row_ptr.device
+        rp = torch.empty(self.rows + 1, dtype=torch.int64, device=dev)
+        nnz = C.c_int64()
+        per = (C.c_int64 * max(self.n, 1))()
+        _check(_lib.spgemm_batched_symbolic(self.h.ptr, self.n, self.da, self.db, rp.data_ptr(), C.byref(nnz),
+                                            per, _stream(stream)))
+        self.row_ptr, self.nnz, self.inst_nnz = rp, int(nnz.value), [int(per[i]) for i in range(self.n)]
+        return rp, self.nnz
+
+    def alloc(self):
+        torch = _torch()
+        dev = self.As[0].row_ptr.device
+        return Csr(self.rows, max(b.ncols for b in self.Bs), self.row_ptr,
+                   torch.empty(self.nnz, dtype=torch.int32, device=dev),
+                   torch.empty(self.nnz, dtype=self.As[0].val.dtype, device=dev))
+
+    def numeric_into(self, Cm: Csr, stream=None):
+        self._arrays()
+        dc = Cm.desc()
+        _check(_lib.spgemm_batched_numeric(self.h.ptr, self.As[0].dtype_code(), self.n, self.da, self.db,
+                                           C.byref(dc), _stream(stream)))
+
+    def run(self, stream=None) -> Csr:
+        self.symbolic(stream)
+        Cm = self.alloc()
+        self.numeric_into(Cm, stream)
+        return Cm
+
+    def split(self, Cm: Csr):
+        """Per-instance views of the stacked result."""
+        out, r0, p0 = [], 0, 0
+        for a, b, nz in zip(self.As, self.Bs, self.inst_nnz):
+            rp = Cm.row_ptr[r0:r0 + a.nrows + 1] - p0
+            out.append(Csr(a.nrows, b.ncols, rp, Cm.col[p0:p0 + nz], Cm.val[p0:p0 + nz]))
+            r0 += a.nrows
+            p0 += nz
+        return out
+
+    def backward(self, Cm: Csr, dC, need_a: bool = True, need_b: bool = True, stream=None):
+        """Stacked dA, dB for dC on the stacked pattern; split with split_grads."""
+        torch = _torch()
+        dev = dC.device
+        na = sum(a.nnz for a in self.As)
+        nb = sum(b.nnz for b in self.Bs)
+        da = torch.empty(na, dtype=dC.dtype, device=dev) if need_a else None
+        db = torch.empty(nb, dtype=dC.dtype, device=dev) if need_b else None
+        dcm = Csr(Cm.nrows, Cm.ncols, Cm.row_ptr, Cm.col, dC.contiguous())
+        d = dcm.desc()
+        _check(_lib.spgemm_batched_backward(self.h.ptr, self.As[0].dtype_code(), C.byref(d),
+                                            da.data_ptr() if da is not None else None,
+                                            db.data_ptr() if db is not None else None, _stream(stream)))
+        return da, db
+
+    def split_grads(self, da, db):
+        ga, gb, pa, pb = [], [], 0, 0
+        for a, b in zip(self.As, self.Bs):
+            ga.append(da[pa:pa + a.nnz] if da is not None else None)
+            gb.append(db[pb:pb + b.nnz] if db is not None else None)
+            pa += a.nnz
+            pb += b.nnz
+        return ga, gb

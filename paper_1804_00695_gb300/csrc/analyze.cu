@@ -223,18 +223,18 @@ int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, 
 
 // Row lists for the list-driven kernels.  phase 0 (symbolic second pass):
 // rows marked -1 in crp[i+1] (overflowed the first pass, or bin 6), listed by
-// max(bins[i], 2).  phase 1 (numeric): rows of bins 3..6.  Within a warp the
+// max(bins[i], 2).  phase 1 (numeric): rows of bins first_bin..6.  Within a warp the
 // lanes with the same bin reserve their slots with one atomic
 // (__match_any_sync), so rows stay in ascending order inside each warp.
 __global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
                                const int64_t *__restrict__ crp, int32_t *__restrict__ rows,
-                               DevState *st, int phase) {
+                               DevState *st, int phase, int first_bin) {
     __shared__ long long off[NBINS];
     if (threadIdx.x == 0) {
         long long o = 0;
         for (int b = 0; b < NBINS; b++) {
             off[b] = o;
-            if (b >= (phase == 0 ? 2 : 3) && b <= BIN_HUGE) o += st->bin_count[phase][b];
+            if (b >= (phase == 0 ? 2 : first_bin) && b <= BIN_HUGE) o += st->bin_count[phase][b];
         }
     }
     __syncthreads();
@@ -245,7 +245,7 @@ __global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
             if (crp[i + 1] < 0) b = max((int)bins[i], 2);
         } else {
             int x = bins[i];
-            if (x >= 3) b = x;
+            if (x >= first_bin) b = x;
         }
     }
     unsigned act = __ballot_sync(0xffffffffu, b != BIN_EMPTY);
@@ -262,11 +262,12 @@ __global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
 }
 
 int launch_scatter_bins(int64_t n, const uint8_t *bins, const int64_t *crp, int32_t *rows,
-                        DevState *st, int phase, Ctx &c) {
+                        DevState *st, int phase, Ctx &c, int first_bin) {
     if (n == 0) return SPGEMM_OK;
     SG_CUDA(cudaMemsetAsync(st->bin_cursor, 0, sizeof(st->bin_cursor), c.s));
     c.begin("scatter_bins", n);
-    k_scatter_bins<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, bins, crp, rows, st, phase);
+    k_scatter_bins<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, bins, crp, rows, st, phase,
+                                                                   first_bin);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;

@@ -68,7 +68,8 @@ struct spgemm_handle_s {
     long long num_counts[NBINS] = {0};
     int64_t max_row_nnz = 0;
     size_t num_gws = 0;   // bytes of the second-level maps numeric needs
-    bool num_lists = false;   // numeric row lists built for this symbolic result
+    int num_lists = 0;        // first bin of the numeric row lists built (0 = none)
+    int small_cap = 32, slot_factor = 2;
     // options
     bool f64_native = false;
     int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from the mean products per row)
@@ -80,6 +81,18 @@ struct spgemm_handle_s {
     cudaEvent_t ev[8] = {};
     ChunkStats cstats;
     float chunk_ms = 0;
+    // batched calls: stacked operands and the instance table
+    char *bws = nullptr;
+    size_t bws_cap = 0;
+    std::vector<BatchInst> inst;
+    BatchInst *dinst = nullptr;
+    spgemm_csr As{}, Bs{};
+    int64_t *inst_out = nullptr;   // device, nbatch+1 offsets gathered from C
+    int64_t max_ar = 0, max_an = 0, max_br = 0, max_bn = 0;
+    // last numeric call (for the autotuner)
+    bool have_last = false;
+    int last_dtype = 0;
+    spgemm_csr lastA{}, lastB{}, lastC{};
     // launch counting and CUDA-event timing
     long long launches = 0;
     bool timing = false;
@@ -193,6 +206,7 @@ int spgemm_destroy(spgemm_handle h) {
         if (r.e1) cudaEventDestroy(r.e1);
     }
     if (h->arena) cudaFree(h->arena);
+    if (h->bws) cudaFree(h->bws);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->s_in) cudaStreamDestroy(h->s_in);
@@ -303,7 +317,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         h->num_gws = h->num_counts[BIN_HUGE]
                          ? numeric_global_ws(h->max_row_nnz, B->ncols, h->nsm, SPGEMM_F64)
                          : 0;
-        h->num_lists = false;
+        h->num_lists = 0;
         // numeric scratch: B split into double-words, then the second-level maps
         SG_TRY(ws_reserve(h, ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8) + h->num_gws, s,
                           ws_persist(n, B->nrows)));
@@ -342,15 +356,24 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     float2 *bsplit = (float2 *)(h->ws + ws_persist(n, B->nrows));
     char *gws = h->ws + ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
+    h->have_last = true;
+    h->last_dtype = dtype;
+    h->lastA = *A;
+    h->lastB = *B;
+    h->lastC = *C;
+    NumTune tune;
+    tune.G = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 12.0);
+    tune.small_cap = h->small_cap;
+    tune.slot_factor = h->slot_factor;
+    const int first_list = tune.small_cap >= 32 ? 3 : 2;
     long long listed = 0;
-    for (int b = 3; b <= BIN_HUGE; b++) listed += h->num_counts[b];
-    if (listed > 0 && !h->num_lists) {
-        SG_TRY(launch_scatter_bins(n, bins, C->row_ptr, rows, h->dstate, 1, c));
-        h->num_lists = true;
+    for (int b = first_list; b <= BIN_HUGE; b++) listed += h->num_counts[b];
+    if (listed > 0 && h->num_lists != first_list) {
+        SG_TRY(launch_scatter_bins(n, bins, C->row_ptr, rows, h->dstate, 1, c, first_list));
+        h->num_lists = first_list;
     }
-    const int gn = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 12.0);
     return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, rows, h->num_counts,
-                          h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, gn, c);
+                          h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, tune, c);
 }
 
 // Side streams, events and the budget arena of the chunked calls.
@@ -474,6 +497,205 @@ int spgemm_backward(spgemm_handle h, int dtype, const spgemm_csr *A, const spgem
     return launch_backward(dtype, *A, *B, *C, dA_values, dB_values, &h->dstate->err, c);
 }
 
+__global__ void k_gather_offsets(const BatchInst *__restrict__ inst, int nb, const int64_t *__restrict__ crp,
+                                 int64_t total_rows, int64_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb) out[i] = crp[inst[i].a_row_off];
+    if (i == nb) out[nb] = crp[total_rows];
+}
+
+// Instance table of a batch; returns totals.  Fills h->inst (host).
+static int batch_table(spgemm_handle h, int nbatch, const spgemm_csr *A, const spgemm_csr *B, bool need_vals) {
+    if (nbatch < 0 || (nbatch > 0 && (!A || !B))) { set_error("bad batch"); return SPGEMM_ERR_ARG; }
+    if (nbatch > 65535) { set_error("at most 65535 instances per batch"); return SPGEMM_ERR_ARG; }
+    h->inst.assign((size_t)nbatch, BatchInst{});
+    int64_t ar = 0, an = 0, br = 0, bn = 0;
+    h->max_ar = h->max_an = h->max_br = h->max_bn = 0;
+    for (int i = 0; i < nbatch; i++) {
+        SG_TRY(check_csr(&A[i], "A[i]", need_vals));
+        SG_TRY(check_csr(&B[i], "B[i]", need_vals));
+        if (A[i].ncols != B[i].nrows) {
+            set_error("instance %d: dimension mismatch", i);
+            return SPGEMM_ERR_DIM;
+        }
+        BatchInst &d = h->inst[(size_t)i];
+        d.arp = A[i].row_ptr; d.acol = A[i].col_idx; d.aval = A[i].values;
+        d.brp = B[i].row_ptr; d.bcol = B[i].col_idx; d.bval = B[i].values;
+        d.a_rows = A[i].nrows; d.a_nnz = A[i].nnz; d.b_rows = B[i].nrows; d.b_nnz = B[i].nnz;
+        d.a_p0 = d.b_p0 = 0;
+        d.a_row_off = ar; d.a_nnz_off = an; d.b_row_off = br; d.b_nnz_off = bn;
+        ar += A[i].nrows; an += A[i].nnz; br += B[i].nrows; bn += B[i].nnz;
+        h->max_ar = std::max(h->max_ar, A[i].nrows); h->max_an = std::max(h->max_an, A[i].nnz);
+        h->max_br = std::max(h->max_br, B[i].nrows); h->max_bn = std::max(h->max_bn, B[i].nnz);
+    }
+    if (br >= (1LL << 31)) { set_error("batch: stacked rows of B exceed int32 columns"); return SPGEMM_ERR_INDEX; }
+    int64_t maxcol = 0;
+    for (int i = 0; i < nbatch; i++) maxcol = std::max(maxcol, B[i].ncols);
+    h->As = spgemm_csr{ar, br, an, nullptr, nullptr, nullptr};
+    h->Bs = spgemm_csr{br, maxcol, bn, nullptr, nullptr, nullptr};
+    return SPGEMM_OK;
+}
+
+int spgemm_batched_symbolic(spgemm_handle h, int nbatch, const spgemm_csr *A, const spgemm_csr *B,
+                            int64_t *C_row_ptr, int64_t *nnz_total, int64_t *inst_nnz, void *stream) {
+    if (!h || !C_row_ptr || !nnz_total) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    SG_TRY(batch_table(h, nbatch, A, B, false));
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    const int64_t ar = h->As.nrows, an = h->As.nnz, br = h->Bs.nrows, bn = h->Bs.nnz;
+    // stacked arrays: table | A rp, col, val | B rp, col, val | instance offsets
+    const size_t o_tab = 0;
+    const size_t o_arp = align_up((size_t)nbatch * sizeof(BatchInst));
+    const size_t o_acol = o_arp + align_up((size_t)(ar + 1) * 8);
+    const size_t o_aval = o_acol + align_up((size_t)an * 4);
+    const size_t o_brp = o_aval + align_up((size_t)an * 8);
+    const size_t o_bcol = o_brp + align_up((size_t)(br + 1) * 8);
+    const size_t o_bval = o_bcol + align_up((size_t)bn * 4);
+    const size_t o_out = o_bval + align_up((size_t)bn * 8);
+    const size_t need = o_out + align_up((size_t)(nbatch + 1) * 8);
+    if (need > h->bws_cap) {
+        if (h->bws) SG_CUDA(cudaFreeAsync(h->bws, s));
+        h->bws = nullptr;
+        h->bws_cap = 0;
+        cudaError_t e = cudaMallocAsync((void **)&h->bws, need, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("batched: allocation of %zu bytes failed", need);
+            return SPGEMM_ERR_NOMEM;
+        }
+        h->bws_cap = need;
+    }
+    char *w = h->bws;
+    h->dinst = (BatchInst *)(w + o_tab);
+    h->As.row_ptr = (int64_t *)(w + o_arp); h->As.col_idx = (int32_t *)(w + o_acol); h->As.values = w + o_aval;
+    h->Bs.row_ptr = (int64_t *)(w + o_brp); h->Bs.col_idx = (int32_t *)(w + o_bcol); h->Bs.values = w + o_bval;
+    h->inst_out = (int64_t *)(w + o_out);
+    if (nbatch > 0)
+        SG_CUDA(cudaMemcpyAsync(h->dinst, h->inst.data(), (size_t)nbatch * sizeof(BatchInst),
+                                cudaMemcpyHostToDevice, s));
+    Ctx c = h->ctx(s);
+    if (nbatch > 0) {
+        SG_TRY(launch_stack(h->dinst, nbatch, h->max_ar, h->max_an, 0, true, 0, ar, an, h->As.row_ptr,
+                            h->As.col_idx, nullptr, c));
+        SG_TRY(launch_stack(h->dinst, nbatch, h->max_br, h->max_bn, 1, true, 0, br, bn, h->Bs.row_ptr,
+                            h->Bs.col_idx, nullptr, c));
+    } else {
+        SG_CUDA(cudaMemsetAsync(h->As.row_ptr, 0, 8, s));
+        SG_CUDA(cudaMemsetAsync(h->Bs.row_ptr, 0, 8, s));
+    }
+    SG_TRY(spgemm_symbolic(h, &h->As, &h->Bs, C_row_ptr, nnz_total, stream));
+    if (inst_nnz && nbatch > 0) {
+        k_gather_offsets<<<(nbatch + 1 + 255) / 256, 256, 0, s>>>(h->dinst, nbatch, C_row_ptr, ar, h->inst_out);
+        SG_CUDA(cudaGetLastError());
+        std::vector<int64_t> off((size_t)nbatch + 1);
+        SG_CUDA(cudaMemcpyAsync(off.data(), h->inst_out, (size_t)(nbatch + 1) * 8, cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nbatch; i++) inst_nnz[i] = off[(size_t)i + 1] - off[(size_t)i];
+    }
+    return SPGEMM_OK;
+}
+
+int spgemm_batched_numeric(spgemm_handle h, int dtype, int nbatch, const spgemm_csr *A, const spgemm_csr *B,
+                           spgemm_csr *C, void *stream) {
+    if (!h || !C) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) { set_error("bad dtype %d", dtype); return SPGEMM_ERR_ARG; }
+    if (nbatch != (int)h->inst.size()) { set_error("batched numeric: no matching batched symbolic"); return SPGEMM_ERR_NOT_SYMBOLIC; }
+    bool vals_changed = false;
+    for (int i = 0; i < nbatch; i++) {
+        BatchInst &d = h->inst[(size_t)i];
+        if (A[i].row_ptr != d.arp || A[i].col_idx != d.acol || B[i].row_ptr != d.brp || B[i].col_idx != d.bcol ||
+            A[i].nnz != d.a_nnz || B[i].nnz != d.b_nnz) {
+            set_error("batched numeric: instance %d differs from the batched symbolic", i);
+            return SPGEMM_ERR_NOT_SYMBOLIC;
+        }
+        if ((A[i].nnz && !A[i].values) || (B[i].nnz && !B[i].values)) { set_error("instance %d: NULL values", i); return SPGEMM_ERR_ARG; }
+        if (A[i].values != d.aval || B[i].values != d.bval) {
+            d.aval = A[i].values;
+            d.bval = B[i].values;
+            vals_changed = true;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    if (vals_changed && nbatch > 0)
+        SG_CUDA(cudaMemcpyAsync(h->dinst, h->inst.data(), (size_t)nbatch * sizeof(BatchInst),
+                                cudaMemcpyHostToDevice, s));
+    Ctx c = h->ctx(s);
+    const int vb = dtype == SPGEMM_F64 ? 8 : 4;
+    if (nbatch > 0) {
+        SG_TRY(launch_stack(h->dinst, nbatch, h->max_ar, h->max_an, 0, false, vb, h->As.nrows, h->As.nnz,
+                            nullptr, nullptr, (void *)h->As.values, c));
+        SG_TRY(launch_stack(h->dinst, nbatch, h->max_br, h->max_bn, 1, false, vb, h->Bs.nrows, h->Bs.nnz,
+                            nullptr, nullptr, (void *)h->Bs.values, c));
+    }
+    return spgemm_numeric(h, dtype, &h->As, &h->Bs, C, stream);
+}
+
+int spgemm_batched_backward(spgemm_handle h, int dtype, const spgemm_csr *C, void *dA_values,
+                            void *dB_values, void *stream) {
+    if (!h || !C) { set_error("NULL handle or C"); return SPGEMM_ERR_ARG; }
+    if (h->inst.empty() && h->As.nrows == 0) return SPGEMM_OK;
+    return spgemm_backward(h, dtype, &h->As, &h->Bs, C, dA_values, dB_values, stream);
+}
+
+int spgemm_autotune(spgemm_handle h, int reps, int64_t *choice, float *best_ms, void *stream) {
+    if (!h || !h->have_last) { set_error("autotune: run spgemm_numeric once first"); return SPGEMM_ERR_ARG; }
+    if (reps < 1) reps = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0));
+    SG_CUDA(cudaEventCreate(&e1));
+    const int saved[3] = {h->g_numeric, h->small_cap, h->slot_factor};
+    float best = 1e30f;
+    int bg = saved[0], bc = saved[1], bs = saved[2];
+    int status = SPGEMM_OK;
+    const int gs[3] = {8, 16, 32}, caps[2] = {32, 16}, slots[2] = {2, 4};
+    for (int gi = 0; gi < 3 && status == SPGEMM_OK; gi++)
+        for (int ci = 0; ci < 2 && status == SPGEMM_OK; ci++)
+            for (int si = 0; si < 2 && status == SPGEMM_OK; si++) {
+                h->g_numeric = gs[gi];
+                h->small_cap = caps[ci];
+                h->slot_factor = slots[si];
+                status = spgemm_numeric(h, h->last_dtype, &h->lastA, &h->lastB, &h->lastC, stream);
+                if (status != SPGEMM_OK) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && status == SPGEMM_OK; r++)
+                    status = spgemm_numeric(h, h->last_dtype, &h->lastA, &h->lastB, &h->lastC, stream);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)reps;
+                if (ms < best) {
+                    best = ms;
+                    bg = gs[gi];
+                    bc = caps[ci];
+                    bs = slots[si];
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != SPGEMM_OK) {
+        h->g_numeric = saved[0];
+        h->small_cap = saved[1];
+        h->slot_factor = saved[2];
+        return status;
+    }
+    h->g_numeric = bg;
+    h->small_cap = bc;
+    h->slot_factor = bs;
+    // leave C holding the product under the chosen settings
+    SG_TRY(spgemm_numeric(h, h->last_dtype, &h->lastA, &h->lastB, &h->lastC, stream));
+    if (choice) {
+        choice[0] = bg;
+        choice[1] = bc;
+        choice[2] = bs;
+    }
+    if (best_ms) *best_ms = best;
+    return SPGEMM_OK;
+}
+
 int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
     if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
     switch (option) {
@@ -485,6 +707,14 @@ int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
                 return SPGEMM_ERR_ARG;
             }
             (option == SPGEMM_OPT_LANES_NUMERIC ? h->g_numeric : h->g_symbolic) = (int)value;
+            return SPGEMM_OK;
+        case SPGEMM_OPT_SMALL_CAP:
+            if (value != 16 && value != 32) { set_error("small-row cap must be 16 or 32"); return SPGEMM_ERR_ARG; }
+            h->small_cap = (int)value;
+            return SPGEMM_OK;
+        case SPGEMM_OPT_SLOT_FACTOR:
+            if (value != 2 && value != 4) { set_error("slot factor must be 2 or 4"); return SPGEMM_ERR_ARG; }
+            h->slot_factor = (int)value;
             return SPGEMM_OK;
         default: set_error("unknown option %d", option); return SPGEMM_ERR_ARG;
     }

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string>
 #include <vector>
+#include <algorithm>
 #include "../../include/spgemm.h"
 
 namespace sg {
@@ -137,7 +138,7 @@ int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, 
 // Row lists per bin: rows[offset(b) + t]; offsets from st->bin_count[phase]
 // (phase 0: symbolic second pass, phase 1: numeric bins 3..6).
 int launch_scatter_bins(int64_t n, const uint8_t *bins, const int64_t *crp, int32_t *rows,
-                        DevState *st, int phase, Ctx &c);
+                        DevState *st, int phase, Ctx &c, int first_bin = 3);
 int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, int *err, Ctx &c);
 
 // symbolic.cu
@@ -155,11 +156,34 @@ size_t symbolic_global_ws(int64_t ncols_b, int nsm);
 // Runs the numeric kernels: bins 1-2 over all rows in order (bins[i]), bins
 // 3..6 from the row lists (counts[b] rows in bin b, host).  FP64 uses
 // double-word accumulation unless f64_native; bsplit: room for nnz(B) float2.
+// Tunables of the numeric phase: lanes per row of the small-row kernel,
+// largest output row it takes (16 or 32; bin 2 rows go to the warp kernel
+// when 16), and map slots per output entry (2 or 4).
+struct NumTune {
+    int G = 8;
+    int small_cap = 32;
+    int slot_factor = 2;
+};
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B,
                    spgemm_csr &C, const uint8_t *bins, const int4 *bdesc, const int32_t *rows,
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c);
+                   size_t gws_bytes, int64_t max_row_nnz, const NumTune &tune, Ctx &c);
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype);
+
+// batched.cu: one instance of a batch, with its place in the stacked arrays.
+struct BatchInst {
+    const int64_t *arp, *brp;
+    const int32_t *acol, *bcol;
+    const void *aval, *bval;
+    int64_t a_rows, a_nnz, b_rows, b_nnz;
+    int64_t a_p0, b_p0;                  // row_ptr[0] of each operand
+    int64_t a_row_off, a_nnz_off, b_row_off, b_nnz_off;
+};
+// Stack operand `which` (0 = A, 1 = B) of all instances: offsets and
+// (shifted) columns when `pattern`, values when val is not null.
+int launch_stack(const BatchInst *dinst, int nb, int64_t max_rows, int64_t max_nnz, int which, bool pattern,
+                 int vb, int64_t total_rows, int64_t total_nnz, int64_t *rp, int32_t *col, void *val,
+                 Ctx &c);
 
 // backward.cu: dA on pattern(A), dB on pattern(B) from dC on pattern(C).
 int launch_backward(int dtype, const spgemm_csr &A, const spgemm_csr &B, const spgemm_csr &C, void *da,

@@ -173,7 +173,8 @@ __device__ __forceinline__ void acc_slot(float *hi, float *lo, float *lo2, int s
 template <int G, int MODE>
 __global__ void __launch_bounds__(256) k_num_small(NumP a, const int4 *__restrict__ bdesc, int64_t n,
                                                    const uint8_t *__restrict__ bins,
-                                                   const DevState *st, int *err) {
+                                                   const DevState *st, int *err, int maxbin,
+                                                   int slot_factor) {
     constexpr int SMAX = 64, RPW = 32 / G, WPB = 8, PER = SMAX / G;
     constexpr int E = 32, EL = E / G;   // entries staged per batch, per lane
     using V = ValT<MODE>;
@@ -199,12 +200,12 @@ __global__ void __launch_bounds__(256) k_num_small(NumP a, const int4 *__restric
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
         const int64_t i = base + g;
         const int bi = i < n ? bins[i] : 0;
-        const bool active = bi == 1 || bi == 2;
+        const bool active = bi >= 1 && bi <= maxbin;
         const int64_t p0 = active ? a.arp[i] : 0;
         const int plen = active ? (int)(a.arp[i + 1] - p0) : 0;
         const int64_t out = active ? a.crp[i] : 0;
         const int nn = active ? (int)(a.crp[i + 1] - out) : 0;
-        int S = next_pow2(2 * nn);
+        int S = next_pow2(slot_factor * nn);
         S = S < 8 ? 8 : (S > SMAX ? SMAX : S);
         const int L = __ffs(S) - 1;
 #pragma unroll
@@ -706,7 +707,7 @@ static const char *NUM_LABEL[NBINS] = {"", "numeric.small", "numeric.small", "nu
 
 template <int G, int MODE>
 static int run_small(const NumP &a, const int4 *bdesc, int64_t n, const uint8_t *bins, DevState *st,
-                     int *err, Ctx &c) {
+                     int *err, int maxbin, int slot_factor, Ctx &c) {
     constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
     const size_t smem = (size_t)GPB * (64 * 16 + 32 * 16 + 33 * 4);
     SG_TRY(prep(k_num_small<G, MODE>, smem));
@@ -714,20 +715,22 @@ static int run_small(const NumP &a, const int4 *bdesc, int64_t n, const uint8_t 
     const int64_t cap = (int64_t)c.nsm * 32;
     blocks = blocks < cap ? blocks : cap;
     c.begin("numeric.small", n);
-    k_num_small<G, MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, bdesc, n, bins, st, err);
+    k_num_small<G, MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, bdesc, n, bins, st, err, maxbin,
+                                                                 slot_factor);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
 }
 
 template <int MODE>
-static int run_small_g(int G, const NumP &a, const int4 *bdesc, int64_t n, const uint8_t *bins,
+static int run_small_g(const NumTune &t, const NumP &a, const int4 *bdesc, int64_t n, const uint8_t *bins,
                        DevState *st, int *err, Ctx &c) {
-    switch (G) {
-        case 4: return run_small<4, MODE>(a, bdesc, n, bins, st, err, c);
-        case 8: return run_small<8, MODE>(a, bdesc, n, bins, st, err, c);
-        case 16: return run_small<16, MODE>(a, bdesc, n, bins, st, err, c);
-        default: return run_small<32, MODE>(a, bdesc, n, bins, st, err, c);
+    const int maxbin = t.small_cap >= 32 ? 2 : 1;
+    switch (t.G) {
+        case 4: return run_small<4, MODE>(a, bdesc, n, bins, st, err, maxbin, t.slot_factor, c);
+        case 8: return run_small<8, MODE>(a, bdesc, n, bins, st, err, maxbin, t.slot_factor, c);
+        case 16: return run_small<16, MODE>(a, bdesc, n, bins, st, err, maxbin, t.slot_factor, c);
+        default: return run_small<32, MODE>(a, bdesc, n, bins, st, err, maxbin, t.slot_factor, c);
     }
 }
 
@@ -796,17 +799,20 @@ static int run_huge(const NumP &a, const spgemm_csr &B, const int32_t *rows, int
 template <int MODE>
 static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
                    const int4 *bdesc, const int32_t *rows, const long long *counts, DevState *st,
-                   void *gws, size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
+                   void *gws, size_t gws_bytes, int64_t max_row_nnz, const NumTune &t, Ctx &c) {
     using V = typename std::conditional<MODE == MODE_F32, float, double>::type;
     int *err = &st->err;
-    if (counts[1] + counts[2] > 0) SG_TRY(run_small_g<MODE>(G, a, bdesc, A.nrows, bins, st, err, c));
+    const int first_list = t.small_cap >= 32 ? 3 : 2;
+    if (counts[1] + (first_list == 3 ? counts[2] : 0) > 0)
+        SG_TRY(run_small_g<MODE>(t, a, bdesc, A.nrows, bins, st, err, c));
     int64_t off = 0;
-    for (int b = 3; b <= BIN_HUGE; b++) {
+    for (int b = first_list; b <= BIN_HUGE; b++) {
         const int64_t cnt = counts[b];
         const int32_t *r = rows + off;
         off += cnt;
         if (cnt == 0) continue;
         switch (b) {
+            case 2:
             case 3: SG_TRY(run_warp<MODE>(a, r, cnt, st, err, c)); break;
             case 4: SG_TRY((run_block<128, 2048, V>(a, r, cnt, err, b, c))); break;
             case 5: SG_TRY((run_block<256, 8192, V>(a, r, cnt, err, b, c))); break;
@@ -819,7 +825,7 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
                    const uint8_t *bins, const int4 *bdesc, const int32_t *rows,
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, int G, Ctx &c) {
+                   size_t gws_bytes, int64_t max_row_nnz, const NumTune &G, Ctx &c) {
     NumP a{A.row_ptr, A.col_idx, A.values, B.row_ptr, B.col_idx, B.values, bsplit,
            C.row_ptr, C.col_idx, C.values};
     if (dtype == SPGEMM_F32)
