@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--workload", default="galerkin128",
+                    choices=["galerkin128", "rmat20", "chunked256", "batched256"])
     return ap.parse_args()
 
 
@@ -180,6 +182,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "galerkin128":
+        import bench_workloads
+        return bench_workloads.run(args, rank, world, local)
 
     import torch
     import paper_1804_00695_gb300 as sg

@@ -301,6 +301,14 @@ class Handle:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         return Cm
 
+    def chunked_numeric_into(self, A: "HostCsr", B: "HostCsr", Cm: "HostCsr", budget: int, stream=None):
+        """Fill the preallocated (pinned) Cm.col / Cm.val; synchronised."""
+        da, db, dc = A.desc(), B.desc(), Cm.desc()
+        _check(_lib.spgemm_chunked_numeric(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc),
+                                           budget, _stream(stream)))
+        torch = _torch()
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
     def chunked(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None) -> "HostCsr":
         rp, nnz = self.chunked_symbolic(A, B, budget, stream)
         return self.chunked_numeric(A, B, rp, nnz, budget, stream)

@@ -17,17 +17,20 @@ namespace sg {
 __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
                            const int32_t *__restrict__ col, int2 *__restrict__ pairs,
                            int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
-                           int4 *__restrict__ desc, int4 *__restrict__ ana, int *err) {
+                           int4 *__restrict__ desc, int4 *__restrict__ ana, int *err,
+                           int *unsorted_flag) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     const int64_t beg = rp[r], end = rp[r + 1];
     int cur = -1;
     unsigned m = 0;
-    int n = 0, bmin = INT_MAX, bmax = INT_MIN;
-    bool bad = false;
+    int n = 0, bmin = INT_MAX, bmax = INT_MIN, prev = -1;
+    bool bad = false, unsorted = false;
     for (int64_t p = beg; p < end; p++) {
         const int c = col[p];
         if (c < 0 || (int64_t)c >= ncols) { bad = true; continue; }
+        unsorted |= c <= prev;
+        prev = c;
         const int b = c >> 5;
         if (b != cur) {
             if (cur >= 0 && pairs) pairs[beg + n] = make_int2(cur, (int)m);
@@ -49,15 +52,16 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
     if (desc) desc[r] = make_int4((int)(unsigned)(uint64_t)beg, (int)((uint64_t)beg >> 32), len, n);
     if (ana) ana[r] = make_int4(len, n, bmin, bmax);
     if (bad) atomicOr(err, DERR_COL_RANGE);
+    if (unsorted && unsorted_flag) atomicOr(unsorted_flag, 1);
 }
 
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
-                    int4 *ana, int *err, Ctx &c) {
+                    int4 *ana, int *err, Ctx &c, int *unsorted) {
     if (M.nrows == 0) return SPGEMM_OK;
     int64_t blocks = (M.nrows + 255) / 256;
     c.begin("compress", M.nrows);
     k_compress<<<(unsigned)blocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
-                                                    ccnt, minmax, desc, ana, err);
+                                                    ccnt, minmax, desc, ana, err, unsorted);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -88,8 +92,9 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
                           uint8_t *__restrict__ bins, int64_t *__restrict__ crp, DevState *st) {
     __shared__ unsigned long long hist[NBINS];
     __shared__ unsigned long long fsum;
+    __shared__ unsigned long long alen_max;
     if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
-    if (threadIdx.x == 0) fsum = 0;
+    if (threadIdx.x == 0) { fsum = 0; alen_max = 0; }
     __syncthreads();
     const int lane = threadIdx.x % AN_G;
     const unsigned gmask = ((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1));
@@ -132,10 +137,17 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
     warp_hist(hist, lead, b);
     // products of the warp's rows (lane 0 of each group holds its row's count)
     long long wf = lead ? f : 0;
-    for (int d = 16; d > 0; d >>= 1) wf += __shfl_xor_sync(0xffffffffu, wf, d);
+    long long wl = lead ? (long long)(arp[i + 1] - arp[i]) : 0;   // longest row of A
+    for (int d = 16; d > 0; d >>= 1) {
+        wf += __shfl_xor_sync(0xffffffffu, wf, d);
+        wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, d));
+    }
     if ((threadIdx.x & 31) == 0 && wf) atomicAdd(&fsum, (unsigned long long)wf);
+    if ((threadIdx.x & 31) == 0 && wl) atomicMax(&alen_max, (unsigned long long)wl);
     __syncthreads();
     if (threadIdx.x == 0 && fsum) atomicAdd((unsigned long long *)&st->flops_total, fsum);
+    if (threadIdx.x == 0 && alen_max && alen_max > (unsigned long long)*(volatile long long *)&st->max_alen)
+        atomicMax((unsigned long long *)&st->max_alen, alen_max);
     if (threadIdx.x < NBINS && hist[threadIdx.x]) {
         atomicAdd((unsigned long long *)&st->sym_hist[threadIdx.x], hist[threadIdx.x]);
         if (threadIdx.x == BIN_HUGE)

@@ -69,6 +69,8 @@ struct spgemm_handle_s {
     int64_t max_row_nnz = 0;
     size_t num_gws = 0;   // bytes of the second-level maps numeric needs
     int num_lists = 0;        // first bin of the numeric row lists built (0 = none)
+    bool b_sorted = false;    // every row of B strictly ascending (symbolic)
+    int64_t max_alen = 0;     // longest row of A
     int small_cap = 32, slot_factor = 2;
     // options
     bool f64_native = false;
@@ -239,7 +241,7 @@ static int lanes_for(double x, int lo = 8) {
 // after them the symbolic scratch, or (later) the numeric scratch, which may
 // overlap it.
 static size_t ws_persist(int64_t n, int64_t nb) {
-    return align_up((size_t)n) + align_up((size_t)n * 4) + align_up((size_t)nb * 16);
+    return align_up((size_t)n) + align_up((size_t)n * 4) + align_up((size_t)nb * 16) + align_up((size_t)nb * 8);
 }
 
 int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *C_row_ptr,
@@ -270,8 +272,8 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         const size_t o_flops = o_ana + align_up((size_t)B->nrows * 16);
         const size_t o_pairs = o_flops + align_up((size_t)n * 8);
         const size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
-        const size_t o_mm = o_ccnt + align_up((size_t)B->nrows * 4);
-        const size_t o_tmp = o_mm + align_up((size_t)B->nrows * 8);
+        const size_t o_mm = o_desc + align_up((size_t)B->nrows * 16);   // persistent, after desc
+        const size_t o_tmp = o_ccnt + align_up((size_t)B->nrows * 4);
         const size_t o_gws = o_tmp + align_up(scan_tmp_bytes(n));
         const size_t gws_bytes = symbolic_global_ws(B->ncols, h->nsm);
         SG_TRY(ws_reserve(h, o_gws + gws_bytes, s));
@@ -289,7 +291,8 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         const double mean_pairs = (double)A->nnz / (double)n *
                                   ((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1)) * 0.6;
         const int gs = h->g_symbolic ? h->g_symbolic : lanes_for(mean_pairs / 8.0);
-        SG_TRY(launch_compress(*B, pairs, ccnt, minmax, desc, ana, &h->dstate->err, c));
+        SG_TRY(launch_compress(*B, pairs, ccnt, minmax, desc, ana, &h->dstate->err, c,
+                               &h->dstate->b_unsorted));
         SG_TRY(launch_analyze(*A, *B, ana, flops, bins, C_row_ptr, h->dstate, c));
         SG_TRY(launch_symbolic_first(*A, bins, desc, pairs, C_row_ptr, h->dstate, gs, c));
         SG_TRY(fetch_state(h, s));
@@ -314,8 +317,11 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         h->mean_flops = (double)h->hstate->flops_total / (double)n;
         memcpy(h->num_counts, h->hstate->bin_count[1], sizeof(h->num_counts));
         h->max_row_nnz = h->hstate->max_row_nnz;
+        h->b_sorted = h->hstate->b_unsorted == 0;
+        h->max_alen = h->hstate->max_alen;
         h->num_gws = h->num_counts[BIN_HUGE]
-                         ? numeric_global_ws(h->max_row_nnz, B->ncols, h->nsm, SPGEMM_F64)
+                         ? std::max(numeric_global_ws(h->max_row_nnz, B->ncols, h->nsm, SPGEMM_F64),
+                                    window_global_ws(h->max_alen, h->nsm))
                          : 0;
         h->num_lists = 0;
         // numeric scratch: B split into double-words, then the second-level maps
@@ -353,6 +359,8 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     uint8_t *bins = (uint8_t *)h->ws;
     int32_t *rows = (int32_t *)(h->ws + align_up((size_t)n));
     const int4 *bdesc = (const int4 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4));
+    const int2 *bmm = (const int2 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4) +
+                                     align_up((size_t)B->nrows * 16));
     float2 *bsplit = (float2 *)(h->ws + ws_persist(n, B->nrows));
     char *gws = h->ws + ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
@@ -372,8 +380,9 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
         SG_TRY(launch_scatter_bins(n, bins, C->row_ptr, rows, h->dstate, 1, c, first_list));
         h->num_lists = first_list;
     }
-    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, rows, h->num_counts,
-                          h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, tune, c);
+    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, bmm, rows, h->num_counts,
+                          h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, tune, h->b_sorted,
+                          h->max_alen, c);
 }
 
 // Side streams, events and the budget arena of the chunked calls.

@@ -42,6 +42,9 @@ struct DevState {          // lives in device memory, one per handle
     long long bin_cursor[SPGEMM_NBINS];
     long long max_row_nnz;   // largest row of C (numeric binning)
     long long flops_total;   // products of the whole product (analysis)
+    int b_unsorted;          // some row of B has columns out of ascending order
+    int pad2;
+    long long max_alen;      // longest row of A (analysis)
 };
 
 // ---------------------------------------------------------------- bins
@@ -120,8 +123,9 @@ struct Ctx {
 // minmax[k] = {first block, last block} ({INT_MAX, INT_MIN} for empty rows);
 // desc[k] = {row_ptr[k] low, high 32 bits, entries, pairs};
 // ana[k] = {entries, pairs, first block, last block}.  Any output may be NULL.
+// `unsorted` (may be null) is set to 1 if a row of M is not strictly ascending.
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
-                    int4 *ana, int *err, Ctx &c);
+                    int4 *ana, int *err, Ctx &c, int *unsorted = nullptr);
 __device__ __forceinline__ int64_t desc_start(int4 d) {
     return (int64_t)(((uint64_t)(unsigned)d.y << 32) | (uint64_t)(unsigned)d.x);
 }
@@ -165,10 +169,13 @@ struct NumTune {
     int slot_factor = 2;
 };
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B,
-                   spgemm_csr &C, const uint8_t *bins, const int4 *bdesc, const int32_t *rows,
+                   spgemm_csr &C, const uint8_t *bins, const int4 *bdesc, const int2 *bmm,
+                   const int32_t *rows,
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, const NumTune &tune, Ctx &c);
+                   size_t gws_bytes, int64_t max_row_nnz, const NumTune &tune, bool b_sorted,
+                   int64_t max_alen, Ctx &c);
 size_t numeric_global_ws(int64_t max_row_nnz, int64_t ncols_b, int nsm, int dtype);
+size_t window_global_ws(int64_t max_alen, int nsm);
 
 // batched.cu: one instance of a batch, with its place in the stacked arrays.
 struct BatchInst {

@@ -124,6 +124,19 @@ __device__ __forceinline__ void acc3_add(float &hi, float &lo, float &lo2, float
     lo2 = __fadd_rn(lo2, __fadd_rn(e2, f));
 }
 
+// The same three levels updated by atomic adds, for slots shared by lanes
+// that may add to them at once: the returned old values give the exact
+// rounding errors of the first two levels.
+__device__ __forceinline__ void dw_atomic_acc(float2 *v2, float *v3, int slot, float2 p) {
+    float s1, e1, t, f, s2, e2;
+    const float o1 = atomicAdd(&v2[slot].x, p.x);
+    two_sum(o1, p.x, s1, e1);
+    two_sum(e1, p.y, t, f);
+    const float o2 = atomicAdd(&v2[slot].y, t);
+    two_sum(o2, t, s2, e2);
+    atomicAdd(&v3[slot], __fadd_rn(e2, f));
+}
+
 // Final value of a three-level slot as a double.
 __device__ __forceinline__ double dw3_to_double(float hi, float lo, float lo2) {
     float s, e;
@@ -385,84 +398,408 @@ __device__ __forceinline__ void bitonic(int *k, V *v, int P, int tid, int NT, Sy
     }
 }
 
-// Bin 3: a warp per listed row, map of up to 256 slots, bitonic output sort.
+// Column span of row i in 32-column blocks, from the blocks B_k reaches
+// (bmm[k] = {first block, last block}); a warp computes it, all lanes return it.
+__device__ __forceinline__ int row_span_blocks(const NumP &a, const int2 *__restrict__ bmm, int64_t i,
+                                               int &bmin) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = a.arp[i], p1 = a.arp[i + 1];
+    int lo = INT_MAX, hi = -1;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+        const int2 m = bmm[a.acol[p]];
+        lo = min(lo, m.x);
+        hi = max(hi, m.y);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    bmin = lo;
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
+__device__ __forceinline__ int row_span_words(const NumP &a, const int2 *__restrict__ bmm, int64_t i) {
+    int bmin;
+    return row_span_blocks(a, bmm, i, bmin);
+}
+
+// Rows of bins 2-4 whose columns fall within 32*BW consecutive columns: a
+// dense accumulator over the row's column span (the dense accumulator of
+// Section 3.1, restricted to the span and held in shared memory).  Pass 1
+// marks every reachable column in a bitmap over the span; prefix counts of
+// the bitmap words turn a column into its rank in the output row; pass 2
+// adds every product into vals[rank] (atomically: FP32 and native FP64 in
+// their type, double-words through the three-level dw_atomic_acc).  The row
+// is then written in column order straight from the bitmap: no hash map,
+// no sort.  Products are dealt out over the warp's 32 lanes as in the other
+// kernels.  Per warp: bitmap, 16-bit prefix counts, NMAX values.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_num_warp(NumP a, const int32_t *__restrict__ rows,
-                                                  int64_t count, const DevState *st, int *err) {
-    constexpr int SMAX = 256, WPB = 8, PER = SMAX / 32;
-    using Slot = SlotT<MODE>;
+struct RankVal {
+    static constexpr int bytes = MODE == MODE_F32 ? 4 : (MODE == MODE_DW ? 12 : 8);
+};
+
+template <int BW, int NMAX, int WPB, int MODE>
+struct RankLayout {
+    static constexpr size_t per_warp =
+        ((size_t)BW * 6 + (size_t)NMAX * RankVal<MODE>::bytes + 32 * 16 + 33 * 4 + 64 + 15) & ~(size_t)15;
+    static constexpr size_t bytes = per_warp * WPB;
+};
+
+template <int BW, int NMAX, int WPB, int MODE>
+__global__ void __launch_bounds__(WPB * 32) k_num_rank(NumP a, const int4 *__restrict__ bdesc,
+                                                       const int2 *__restrict__ bmm,
+                                                       const int32_t *__restrict__ rows, int64_t count,
+                                                       int min_span_words, const DevState *st, int *err) {
+    using Lay = RankLayout<BW, NMAX, WPB, MODE>;
+    using V = ValT<MODE>;
+    constexpr int E = 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Slot *acc = (Slot *)smem_raw + w * SMAX;
-    int *keys = (int *)((Slot *)smem_raw + WPB * SMAX) + w * SMAX;
+    unsigned char *base = smem_raw + (size_t)w * Lay::per_warp;
+    long long *eq0 = (long long *)base;
+    double *ea = (double *)(eq0 + E);
+    unsigned *bits = (unsigned *)(ea + E);
+    unsigned short *pref = (unsigned short *)(bits + BW);
+    unsigned char *vbase = (unsigned char *)(((uintptr_t)(pref + BW) + 15) & ~(uintptr_t)15);
+    float *vf = (float *)vbase;                              // FP32
+    double *v8 = (double *)vbase;                            // native FP64
+    float2 *v2 = (float2 *)vbase;                            // double-word hi, lo
+    float *v3 = (float *)(v2 + NMAX);                        // third level
+    int *pre = (int *)(vbase + (size_t)NMAX * RankVal<MODE>::bytes);
     const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
     int flag = 0;
     for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
         const int64_t out = a.crp[i];
         const int nn = (int)(a.crp[i + 1] - out);
-        int S = next_pow2(2 * nn);
-        S = S < 32 ? 32 : (S > SMAX ? SMAX : S);
-        const int L = __ffs(S) - 1;
-        for (int s = lane; s < S; s += 32) {
-            keys[s] = -1;
-            acc[s] = Slot(0);
-        }
-        const int64_t p0 = a.arp[i], pe = a.arp[i + 1];
+        if (nn > NMAX) continue;
+        int bmin;
+        const int nw = row_span_blocks(a, bmm, i, bmin);
+        if (nw > BW || nw <= min_span_words || nw == 0) continue;
+        const int64_t p0 = a.arp[i];
+        const int plen = (int)(a.arp[i + 1] - p0);
         bool nat = MODE == MODE_F64 || b_bad;
         if (MODE == MODE_DW && !nat) {
             bool ok = true;
-            for (int64_t p = p0 + lane; p < pe; p += 32) dw_split(((const double *)a.aval)[p], ok);
+            for (int pp = lane; pp < plen; pp += 32) dw_split(((const double *)a.aval)[p0 + pp], ok);
             nat = !__all_sync(0xffffffffu, ok);
         }
+        for (int x = lane; x < nw; x += 32) bits[x] = 0;
+        for (int x = lane; x < nn; x += 32) {
+            if (MODE == MODE_F32) vf[x] = 0.f;
+            else if (MODE == MODE_DW) { v2[x] = make_float2(0.f, 0.f); v3[x] = 0.f; }
+            else v8[x] = 0.0;
+        }
         __syncwarp();
-        for (int64_t p = p0; p < pe; p++) {
-            const int k = a.acol[p];
-            const ValT<MODE> av = load_a<MODE>(a.aval, p);
-            bool dummy = true;
-            const float2 a2 = MODE == MODE_DW ? dw_split((double)av, dummy) : make_float2(0.f, 0.f);
-            const int64_t q1 = a.brp[k + 1];
-            for (int64_t q = a.brp[k] + lane; q - lane < q1; q += 32) {
-                if (q < q1) {
-                    const int slot = map_slot(keys, L, a.bcol[q]);
-                    if (slot >= 0) acc_update<MODE>(acc, slot, nat, a.bval, a.bsplit, q, av, a2);
-                    else flag |= DERR_PROBE;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int pb = 0; pb < plen; pb += E) {
+                int len = 0;
+                if (pb + lane < plen) {
+                    const int4 d = bdesc[a.acol[p0 + pb + lane]];
+                    len = d.z;
+                    eq0[lane] = desc_start(d);
+                    if (pass == 1) {
+                        const V av = ((const V *)a.aval)[p0 + pb + lane];
+                        if (MODE == MODE_DW && !nat) {
+                            bool dummy = true;
+                            const float2 s2 = dw_split((double)av, dummy);
+                            ea[lane] = __longlong_as_double(((long long)__float_as_uint(s2.y) << 32) |
+                                                            (long long)__float_as_uint(s2.x));
+                        } else {
+                            ea[lane] = (double)av;
+                        }
+                    }
+                }
+                int incl = len;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                pre[lane] = incl - len;
+                if (lane == 31) pre[E] = incl;
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
+                int e = 0;
+                for (int t0 = 0; t0 < total; t0 += 32) {
+                    const int tt = t0 + lane;
+                    if (tt < total) {
+                        while (pre[e + 1] <= tt) e++;
+                        const int64_t q = eq0[e] + (tt - pre[e]);
+                        const int col = a.bcol[q];
+                        const int wd = (col >> 5) - bmin;
+                        const unsigned bit = 1u << (col & 31);
+                        if (pass == 0) {
+                            atomicOr(&bits[wd], bit);
+                        } else {
+                            const int r = (int)pref[wd] + __popc(bits[wd] & (bit - 1));
+                            if (MODE == MODE_F32) {
+                                atomicAdd(&vf[r], (float)ea[e] * ((const float *)a.bval)[q]);
+                            } else if (MODE == MODE_DW && !nat) {
+                                const unsigned long long bb = (unsigned long long)__double_as_longlong(ea[e]);
+                                const float2 a2 = make_float2(__uint_as_float((unsigned)bb),
+                                                              __uint_as_float((unsigned)(bb >> 32)));
+                                dw_atomic_acc(v2, v3, r, dw_mul(a2, a.bsplit[q]));
+                            } else {
+                                atomicAdd(&v8[r], ea[e] * ((const double *)a.bval)[q]);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (pass == 0) {
+                // prefix counts of the words: a contiguous run per lane, warp scan
+                const int per = (nw + 31) / 32;
+                const int x0 = min(nw, lane * per), x1 = min(nw, x0 + per);
+                int sum = 0;
+                for (int x = x0; x < x1; x++) sum += __popc(bits[x]);
+                int incl = sum;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                int run = incl - sum;
+                for (int x = x0; x < x1; x++) {
+                    pref[x] = (unsigned short)run;
+                    run += __popc(bits[x]);
+                }
+                if (__shfl_sync(0xffffffffu, incl, 31) != nn) flag |= DERR_COUNT;
+                __syncwarp();
+            }
+        }
+        // write the row in column order straight from the bitmap
+        const int per = (nw + 31) / 32;
+        const int x0 = min(nw, lane * per), x1 = min(nw, x0 + per);
+        for (int x = x0; x < x1; x++) {
+            unsigned word = bits[x];
+            int r = pref[x];
+            while (word) {
+                const int b = __ffs(word) - 1;
+                word &= word - 1;
+                if (r < nn) {
+                    a.ccol[out + r] = (bmin + x) * 32 + b;
+                    if (MODE == MODE_F32) ((float *)a.cval)[out + r] = vf[r];
+                    else if (MODE == MODE_DW && !nat) ((double *)a.cval)[out + r] = dw3_to_double(v2[r].x, v2[r].y, v3[r]);
+                    else ((double *)a.cval)[out + r] = v8[r];
+                }
+                r++;
+            }
+        }
+        __syncwarp();
+    }
+    if (flag) atomicOr(err, flag);
+}
+
+// Bins 3-4 (and bin 2 when the small-row cap is 16): a warp per listed row,
+// a map of up to SMAX slots (rows with at most SMAX/2 outputs).  The row's
+// products are dealt out over the 32 lanes as in k_num_small (stored a_ik
+// staged 32 at a time with the prefix sums of nnz(B_k)); slots are updated
+// atomically (FP32 and native FP64 in their type, double-words through the
+// three-level dw_atomic_acc).  The output is written in column order
+// without a sort when the row's column span is at most 32*BW: the columns
+// are marked in a bitmap over the span, each lane walks a run of its words
+// from its prefix count and looks the values up in the map.  Wider rows
+// are compacted and sorted with a bitonic network.
+template <int MODE>
+struct WideSlot {   // bytes per map slot: key + value (+ third level)
+    static constexpr int bytes = MODE == MODE_F32 ? 8 : 16;
+};
+
+template <int SMAX, int BW, int WPB, int MODE>
+struct WideLayout {
+    static constexpr size_t table = (size_t)SMAX * WideSlot<MODE>::bytes;
+    static constexpr size_t aux = ((size_t)BW * 4 > (size_t)SMAX / 2 * 12 ? (size_t)BW * 4 : (size_t)SMAX / 2 * 12);
+    static constexpr size_t stage = 32 * 16 + 33 * 4 + 16;
+    static constexpr size_t per_warp = (table + aux + stage + 15) & ~(size_t)15;
+    static constexpr size_t bytes = per_warp * WPB;
+};
+
+template <int SMAX, int BW, int WPB, int MODE>
+__global__ void __launch_bounds__(WPB * 32) k_num_wide(NumP a, const int4 *__restrict__ bdesc,
+                                                       const int2 *__restrict__ bmm,
+                                                       const int32_t *__restrict__ rows, int64_t count,
+                                                       int min_nnz, int min_span_words, const DevState *st,
+                                                       int *err) {
+    using Lay = WideLayout<SMAX, BW, WPB, MODE>;
+    using V = ValT<MODE>;
+    constexpr int E = 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *base = smem_raw + (size_t)w * Lay::per_warp;
+    // table: FP32 {float val}[S] | keys[S];  otherwise {float2 or double}[S] | lo2[S] | keys[S]
+    float2 *v2 = (float2 *)base;
+    double *v8 = (double *)base;
+    float *vf = (float *)base;
+    float *v3 = MODE == MODE_F32 ? nullptr : (float *)(v8 + SMAX);
+    int *keys = MODE == MODE_F32 ? (int *)(vf + SMAX) : (int *)(v3 + SMAX);
+    unsigned *bits = (unsigned *)(base + Lay::table);
+    int *ck = (int *)bits;
+    double *cv = (double *)((int *)bits + SMAX / 2);
+    long long *eq0 = (long long *)(base + Lay::table + Lay::aux);
+    double *ea = (double *)(eq0 + E);
+    int *pre = (int *)(ea + E);
+    int *ncount = pre + E + 1;
+    const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
+    int flag = 0;
+    for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
+        const int i = rows[t];
+        const int64_t out = a.crp[i];
+        const int nn = (int)(a.crp[i + 1] - out);
+        if (nn < min_nnz || nn > SMAX / 2) continue;
+        if (min_span_words > 0 && row_span_words(a, bmm, i) <= min_span_words) continue;
+        int S = next_pow2(2 * nn);
+        S = S < 32 ? 32 : (S > SMAX ? SMAX : S);
+        const int L = __ffs(S) - 1;
+        for (int u = lane; u < S; u += 32) {
+            keys[u] = -1;
+            if (MODE == MODE_F32) {
+                vf[u] = 0.f;
+            } else {
+                v8[u] = 0.0;
+                v3[u] = 0.f;
+            }
+        }
+        const int64_t p0 = a.arp[i];
+        const int plen = (int)(a.arp[i + 1] - p0);
+        bool nat = MODE == MODE_F64 || b_bad;
+        if (MODE == MODE_DW && !nat) {
+            bool ok = true;
+            for (int pp = lane; pp < plen; pp += 32) dw_split(((const double *)a.aval)[p0 + pp], ok);
+            nat = !__all_sync(0xffffffffu, ok);
+        }
+        int cmin = INT_MAX, cmax = -1;
+        __syncwarp();
+        for (int pb = 0; pb < plen; pb += E) {
+            int len = 0;
+            if (pb + lane < plen) {
+                const int4 d = bdesc[a.acol[p0 + pb + lane]];
+                len = d.z;
+                eq0[lane] = desc_start(d);
+                const V av = ((const V *)a.aval)[p0 + pb + lane];
+                if (MODE == MODE_DW && !nat) {
+                    bool dummy = true;
+                    const float2 s2 = dw_split((double)av, dummy);
+                    ea[lane] = __longlong_as_double(((long long)__float_as_uint(s2.y) << 32) |
+                                                    (long long)__float_as_uint(s2.x));
+                } else {
+                    ea[lane] = (double)av;
+                }
+            }
+            int incl = len;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            pre[lane] = incl - len;
+            if (lane == 31) pre[E] = incl;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            int e = 0;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int tt = t0 + lane;
+                if (tt < total) {
+                    while (pre[e + 1] <= tt) e++;
+                    const int64_t q = eq0[e] + (tt - pre[e]);
+                    const int col = a.bcol[q];
+                    cmin = min(cmin, col);
+                    cmax = max(cmax, col);
+                    const int slot = map_slot(keys, L, col);
+                    if (slot < 0) {
+                        flag |= DERR_PROBE;
+                    } else if (MODE == MODE_F32) {
+                        atomicAdd(&vf[slot], (float)ea[e] * ((const float *)a.bval)[q]);
+                    } else if (MODE == MODE_DW && !nat) {
+                        const unsigned long long bb = (unsigned long long)__double_as_longlong(ea[e]);
+                        const float2 a2 = make_float2(__uint_as_float((unsigned)bb), __uint_as_float((unsigned)(bb >> 32)));
+                        dw_atomic_acc(v2, v3, slot, dw_mul(a2, a.bsplit[q]));
+                    } else {
+                        atomicAdd(&v8[slot], ea[e] * ((const double *)a.bval)[q]);
+                    }
                 }
             }
             __syncwarp();
         }
-        int kk[PER];
-        Slot vv[PER];
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            const int s = lane + u * 32;
-            kk[u] = s < S ? keys[s] : -1;
-            vv[u] = s < S ? acc[s] : Slot(0);
+        for (int d = 16; d > 0; d >>= 1) {
+            cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, d));
+            cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, d));
         }
-        __syncwarp();
-        int cnt = 0;
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            const bool occ = kk[u] != -1;
-            const unsigned m = __ballot_sync(0xffffffffu, occ);
-            if (occ) {
-                const int pos = cnt + __popc(m & ((1u << lane) - 1));
-                keys[pos] = kk[u];
-                acc[pos] = vv[u];
+        const int64_t span = cmax >= cmin ? (int64_t)cmax - cmin + 1 : 0;
+        auto slot_value = [&](int u) -> double {
+            if (MODE == MODE_F32) return (double)vf[u];
+            if (MODE == MODE_DW && !nat) return dw3_to_double(v2[u].x, v2[u].y, v3[u]);
+            return v8[u];
+        };
+        if (span <= 32LL * BW) {
+            const int nw = (int)((span + 31) >> 5);
+            for (int x = lane; x < nw; x += 32) bits[x] = 0;
+            __syncwarp();
+            for (int u = lane; u < S; u += 32) {
+                const int key = keys[u];
+                if (key >= 0) atomicOr(&bits[(key - cmin) >> 5], 1u << ((key - cmin) & 31));
             }
-            cnt += __popc(m);
-        }
-        if (cnt != nn) {
-            flag |= DERR_COUNT;
-            cnt = min(cnt, nn);
-        }
-        const int P = next_pow2(cnt);
-        for (int e = cnt + lane; e < P; e += 32) keys[e] = INT_MAX;
-        __syncwarp();
-        bitonic<Slot>(keys, acc, P, lane, 32, [] { __syncwarp(); });
-        for (int e = lane; e < cnt; e += 32) {
-            a.ccol[out + e] = keys[e];
-            store_out<MODE>(a.cval, out + e, acc[e], nat);
+            __syncwarp();
+            const int per = (nw + 31) / 32;
+            const int x0 = min(nw, lane * per), x1 = min(nw, x0 + per);
+            int sum = 0;
+            for (int x = x0; x < x1; x++) sum += __popc(bits[x]);
+            int incl = sum;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            if (__shfl_sync(0xffffffffu, incl, 31) != nn) flag |= DERR_COUNT;
+            int r = incl - sum;
+            for (int x = x0; x < x1; x++) {
+                unsigned word = bits[x];
+                while (word) {
+                    const int bpos = __ffs(word) - 1;
+                    word &= word - 1;
+                    const int col = cmin + x * 32 + bpos;
+                    unsigned hh = hash_slot(col, L);
+                    while (keys[hh] != col) hh = (hh + 1) & (S - 1);
+                    if (r < nn) {
+                        a.ccol[out + r] = col;
+                        if (MODE == MODE_F32) ((float *)a.cval)[out + r] = vf[hh];
+                        else ((double *)a.cval)[out + r] = slot_value((int)hh);
+                    }
+                    r++;
+                }
+            }
+        } else {
+            // compact (values as double), bitonic sort, write
+            if (lane == 0) *ncount = 0;
+            __syncwarp();
+            for (int u0 = 0; u0 < S; u0 += 32) {
+                const int u = u0 + lane;
+                const int key = keys[u];
+                const bool occ = key >= 0;
+                const unsigned m = __ballot_sync(0xffffffffu, occ);
+                const int basec = *ncount;
+                if (occ) {
+                    const int pos = basec + __popc(m & ((1u << lane) - 1));
+                    if (pos < SMAX / 2) {
+                        ck[pos] = key;
+                        cv[pos] = slot_value(u);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) *ncount = basec + __popc(m);
+                __syncwarp();
+            }
+            int n = min(*ncount, SMAX / 2);
+            if (n != nn) {
+                flag |= DERR_COUNT;
+                n = min(n, nn);
+            }
+            const int P = next_pow2(n);
+            for (int x = n + lane; x < P; x += 32) ck[x] = INT_MAX;
+            __syncwarp();
+            bitonic<double>(ck, cv, P, lane, 32, [] { __syncwarp(); });
+            for (int x = lane; x < n; x += 32) {
+                a.ccol[out + x] = ck[x];
+                if (MODE == MODE_F32) ((float *)a.cval)[out + x] = (float)cv[x];
+                else ((double *)a.cval)[out + x] = cv[x];
+            }
         }
         __syncwarp();
     }
@@ -694,6 +1031,141 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
     if (flag) atomicOr(err, flag);
 }
 
+// Bin 6 when every row of B is sorted: a dense accumulator over windows of
+// W columns (Section 3.1's dense accumulator, kept in shared memory a window
+// at a time).  Each stored a_ik keeps a cursor into B_k; for a window, the
+// lanes of a warp advance the cursor over the entries of B_k that fall in it
+// and add a_ik * b_kj into win[j - w0] (atomically) while marking j in a
+// bitmap.  The window's entries then leave in column order: prefix counts of
+// the bitmap words give each its place, and the slot is cleared as it is
+// read.  Windows between the row's first and last reachable column are
+// visited in order, so the row is written sorted without a sort.  Global
+// memory per block: one 8-byte cursor per stored entry of the longest row.
+constexpr int WIN_BS = 512;
+
+template <typename V, int W>
+__global__ void __launch_bounds__(WIN_BS) k_num_window(
+    const int64_t *__restrict__ arp, const int32_t *__restrict__ acol, const V *__restrict__ aval,
+    const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, const V *__restrict__ bval,
+    const int64_t *__restrict__ crp, int32_t *__restrict__ ccol, V *__restrict__ cval,
+    const int32_t *__restrict__ rows, int64_t count, int *err, int64_t max_alen, int64_t *gcur) {
+    constexpr int NW = W / 32, NWARP = WIN_BS / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *win = (V *)smem_raw;
+    unsigned *bits = (unsigned *)(win + W);
+    __shared__ int bmin_s, bmax_s, wtot;
+    __shared__ int red[NWARP];
+    int64_t *cur = gcur + (size_t)blockIdx.x * (size_t)max_alen;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int flag = 0;
+    for (int x = threadIdx.x; x < W; x += WIN_BS) win[x] = V(0);
+    for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+        const int i = rows[t];
+        const int64_t p0 = arp[i], plen = arp[i + 1] - p0;
+        const int64_t out = crp[i], expect = crp[i + 1] - out;
+        if (threadIdx.x == 0) {
+            bmin_s = INT_MAX;
+            bmax_s = -1;
+        }
+        __syncthreads();
+        int lmin = INT_MAX, lmax = -1;
+        for (int64_t p = threadIdx.x; p < plen; p += WIN_BS) {
+            const int k = acol[p0 + p];
+            const int64_t q0 = brp[k], q1 = brp[k + 1];
+            cur[p] = q0;
+            if (q1 > q0) {
+                lmin = min(lmin, bcol[q0]);
+                lmax = max(lmax, bcol[q1 - 1]);
+            }
+        }
+        atomicMin(&bmin_s, lmin);
+        atomicMax(&bmax_s, lmax);
+        __syncthreads();
+        const int cmin = bmin_s, cmax = bmax_s;
+        int64_t written = 0;
+        for (int64_t w0 = cmax >= 0 ? ((int64_t)cmin / W) * W : 1; w0 <= cmax; w0 += W) {
+            const int64_t w1 = w0 + W;
+            for (int x = threadIdx.x; x < NW; x += WIN_BS) bits[x] = 0;
+            __syncthreads();
+            for (int64_t p = w; p < plen; p += NWARP) {
+                const int k = acol[p0 + p];
+                const V av = aval[p0 + p];
+                int64_t c = cur[p];
+                const int64_t q1 = brp[k + 1];
+                while (c < q1) {
+                    const int64_t q = c + lane;
+                    const int col = q < q1 ? bcol[q] : INT_MAX;
+                    const bool in = col < w1;
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    if (in) {
+                        const int rel = (int)(col - w0);
+                        atomicAdd(&win[rel], av * bval[q]);
+                        atomicOr(&bits[rel >> 5], 1u << (rel & 31));
+                    }
+                    c += __popc(m);
+                    if (m != 0xffffffffu) break;
+                }
+                if (lane == 0) cur[p] = c;
+            }
+            __syncthreads();
+            // prefix counts of the words, two per thread
+            constexpr int PERT = (NW + WIN_BS - 1) / WIN_BS;
+            int sum = 0;
+#pragma unroll
+            for (int u = 0; u < PERT; u++) {
+                const int x = threadIdx.x * PERT + u;
+                if (x < NW) sum += __popc(bits[x]);
+            }
+            int incl = sum;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            if (lane == 31) red[w] = incl;
+            __syncthreads();
+            if (w == 0) {
+                const int v = lane < NWARP ? red[lane] : 0;
+                int vi = v;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, vi, d);
+                    if (lane >= d) vi += y;
+                }
+                if (lane < NWARP) red[lane] = vi - v;
+                if (lane == NWARP - 1) wtot = vi;
+            }
+            __syncthreads();
+            // emit this thread's words in column order, clearing the slots read
+            int64_t r = written + red[w] + incl - sum;
+#pragma unroll
+            for (int u = 0; u < PERT; u++) {
+                const int x = threadIdx.x * PERT + u;
+                if (x >= NW) continue;
+                unsigned word = bits[x];
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    const int idx = x * 32 + b;
+                    if (r < expect) {
+                        ccol[out + r] = (int)(w0 + idx);
+                        cval[out + r] = win[idx];
+                    } else {
+                        flag |= DERR_COUNT;
+                    }
+                    win[idx] = V(0);
+                    r++;
+                }
+            }
+            __syncthreads();
+            written += wtot;
+            __syncthreads();
+        }
+        if (written != expect) flag |= DERR_COUNT;
+    }
+    if (flag) atomicOr(err, flag);
+}
+
+size_t window_global_ws(int64_t max_alen, int nsm) { return (size_t)(max_alen > 0 ? max_alen : 1) * 8 * (size_t)nsm; }
+
 // ------------------------------------------------------------------ host side
 template <typename K>
 static int prep(K kern, size_t smem) {
@@ -734,14 +1206,31 @@ static int run_small_g(const NumTune &t, const NumP &a, const int4 *bdesc, int64
     }
 }
 
-template <int MODE>
-static int run_warp(const NumP &a, const int32_t *rows, int64_t count, DevState *st, int *err, Ctx &c) {
-    const size_t smem = (size_t)8 * 256 * (sizeof(SlotT<MODE>) + 4);
-    SG_TRY(prep(k_num_warp<MODE>, smem));
-    int64_t blocks = (count + 7) / 8;
+template <int BW, int NMAX, int WPB, int MODE>
+static int run_rank(const NumP &a, const int4 *bdesc, const int2 *bmm, const int32_t *rows, int64_t count,
+                    int min_span, DevState *st, int *err, const char *label, Ctx &c) {
+    const size_t smem = RankLayout<BW, NMAX, WPB, MODE>::bytes;
+    SG_TRY(prep(k_num_rank<BW, NMAX, WPB, MODE>, smem));
+    int64_t blocks = (count + WPB - 1) / WPB;
     blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
-    c.begin("numeric.bin3", count);
-    k_num_warp<MODE><<<(unsigned)blocks, 256, smem, c.s>>>(a, rows, count, st, err);
+    c.begin(label, count);
+    k_num_rank<BW, NMAX, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, bmm, rows, count,
+                                                                                min_span, st, err);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+template <int SMAX, int BW, int WPB, int MODE>
+static int run_wide(const NumP &a, const int4 *bdesc, const int2 *bmm, const int32_t *rows, int64_t count,
+                    int min_nnz, int min_span, DevState *st, int *err, const char *label, Ctx &c) {
+    const size_t smem = WideLayout<SMAX, BW, WPB, MODE>::bytes;
+    SG_TRY(prep(k_num_wide<SMAX, BW, WPB, MODE>, smem));
+    int64_t blocks = (count + WPB - 1) / WPB;
+    blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
+    c.begin(label, count);
+    k_num_wide<SMAX, BW, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, bmm, rows, count, min_nnz,
+                                                                                min_span, st, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -796,10 +1285,31 @@ static int run_huge(const NumP &a, const spgemm_csr &B, const int32_t *rows, int
     return SPGEMM_OK;
 }
 
+template <typename V>
+static int run_window(const NumP &a, const int32_t *rows, int64_t cnt, int *err, void *gws, size_t gws_bytes,
+                      int64_t max_alen, Ctx &c) {
+    constexpr int W = sizeof(V) == 8 ? 16384 : 32768;
+    const int64_t blocks = cnt < (int64_t)c.nsm ? cnt : (int64_t)c.nsm;
+    if (window_global_ws(max_alen, (int)blocks) > gws_bytes) {
+        set_error("numeric: cursor workspace too small");
+        return SPGEMM_ERR_INTERNAL;
+    }
+    const size_t smem = (size_t)W * sizeof(V) + (size_t)(W / 32) * 4;
+    SG_TRY(prep(k_num_window<V, W>, smem));
+    c.begin("numeric.bin6_window", cnt);
+    k_num_window<V, W><<<(unsigned)blocks, WIN_BS, smem, c.s>>>(
+        a.arp, a.acol, (const V *)a.aval, a.brp, a.bcol, (const V *)a.bval, a.crp, a.ccol, (V *)a.cval, rows,
+        cnt, err, max_alen, (int64_t *)gws);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
 template <int MODE>
 static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
-                   const int4 *bdesc, const int32_t *rows, const long long *counts, DevState *st,
-                   void *gws, size_t gws_bytes, int64_t max_row_nnz, const NumTune &t, Ctx &c) {
+                   const int4 *bdesc, const int2 *bmm, const int32_t *rows, const long long *counts, DevState *st,
+                   void *gws, size_t gws_bytes, int64_t max_row_nnz, const NumTune &t, bool b_sorted,
+                   int64_t max_alen, Ctx &c) {
     using V = typename std::conditional<MODE == MODE_F32, float, double>::type;
     int *err = &st->err;
     const int first_list = t.small_cap >= 32 ? 3 : 2;
@@ -813,25 +1323,39 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
         if (cnt == 0) continue;
         switch (b) {
             case 2:
-            case 3: SG_TRY(run_warp<MODE>(a, r, cnt, st, err, c)); break;
-            case 4: SG_TRY((run_block<128, 2048, V>(a, r, cnt, err, b, c))); break;
+            case 3:
+            case 4:
+                // dense rank accumulator for rows spanning at most 512, then 2048, blocks
+                // of 32 columns; hash map for wider spans (two map sizes)
+                SG_TRY((run_rank<512, 1024, 8, MODE>(a, bdesc, bmm, r, cnt, 0, st, err, "numeric.rank512", c)));
+                SG_TRY((run_rank<2048, 1024, 4, MODE>(a, bdesc, bmm, r, cnt, 512, st, err, "numeric.rank2048", c)));
+                if (b <= 3) {
+                    SG_TRY((run_wide<256, 1024, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 2048, st, err, "numeric.wide3", c)));
+                } else {
+                    SG_TRY((run_wide<512, 2048, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 2048, st, err, "numeric.wide4a", c)));
+                    SG_TRY((run_wide<2048, 2048, 4, MODE>(a, bdesc, bmm, r, cnt, 257, 2048, st, err, "numeric.wide4b", c)));
+                }
+                break;
             case 5: SG_TRY((run_block<256, 8192, V>(a, r, cnt, err, b, c))); break;
-            default: SG_TRY(run_huge<V>(a, B, r, cnt, err, gws, gws_bytes, max_row_nnz, c));
+            default:
+                if (b_sorted) SG_TRY(run_window<V>(a, r, cnt, err, gws, gws_bytes, max_alen, c));
+                else SG_TRY(run_huge<V>(a, B, r, cnt, err, gws, gws_bytes, max_row_nnz, c));
         }
     }
     return SPGEMM_OK;
 }
 
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
-                   const uint8_t *bins, const int4 *bdesc, const int32_t *rows,
+                   const uint8_t *bins, const int4 *bdesc, const int2 *bmm, const int32_t *rows,
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
-                   size_t gws_bytes, int64_t max_row_nnz, const NumTune &G, Ctx &c) {
+                   size_t gws_bytes, int64_t max_row_nnz, const NumTune &G, bool b_sorted,
+                   int64_t max_alen, Ctx &c) {
     NumP a{A.row_ptr, A.col_idx, A.values, B.row_ptr, B.col_idx, B.values, bsplit,
            C.row_ptr, C.col_idx, C.values};
     if (dtype == SPGEMM_F32)
-        return run_all<MODE_F32>(a, A, B, bins, bdesc, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+        return run_all<MODE_F32>(a, A, B, bins, bdesc, bmm, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
     if (f64_native)
-        return run_all<MODE_F64>(a, A, B, bins, bdesc, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+        return run_all<MODE_F64>(a, A, B, bins, bdesc, bmm, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
     SG_CUDA(cudaMemsetAsync(&st->b_out_of_range, 0, sizeof(int), c.s));
     if (B.nnz > 0) {
         int64_t blocks = (B.nnz + 255) / 256;
@@ -841,7 +1365,7 @@ int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm
         c.end();
         SG_CUDA(cudaGetLastError());
     }
-    return run_all<MODE_DW>(a, A, B, bins, bdesc, rows, counts, st, gws, gws_bytes, max_row_nnz, G, c);
+    return run_all<MODE_DW>(a, A, B, bins, bdesc, bmm, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
 }
 
 }  // namespace sg

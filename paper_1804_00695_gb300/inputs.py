@@ -244,42 +244,43 @@ def rmat_symmetric(scale: int, edge_factor: int = 16, abcd=(0.57, 0.19, 0.19, 0.
 
 def random_square(n: int, seed: int, rmin: int = 4, rmax: int = 32, dtype=np.float32) -> Csr:
     """n x n matrix, each row holding a uniform rmin..rmax distinct random
-    columns (uniform without replacement), N(0,1) values (Box-Muller)."""
+    columns (uniform without replacement: the first distinct ones of a row's
+    candidate draws), N(0,1) values (Box-Muller), columns ascending."""
     ncand = rmax + 16
     rows = np.arange(n, dtype=np.uint64)
     rlen = rmin + (uniform01(rows, seed, 1) * (rmax - rmin + 1)).astype(np.int64)
     rlen = np.minimum(rlen, min(rmax, n))
     cand_ctr = rows[:, None] * _U64(ncand) + np.arange(ncand, dtype=np.uint64)[None, :]
     cand = (uniform01(cand_ctr, seed, 2) * n).astype(np.int64)
-    cols_list = []
-    lens = np.zeros(n, dtype=np.int64)
-    # First rlen distinct candidates of each row, in draw order.
-    srt = np.sort(cand, axis=1)
-    dup_free = np.all(srt[:, 1:] != srt[:, :-1], axis=1)
-    out_rows = []
-    for i in range(n):
-        want = int(rlen[i])
-        if dup_free[i]:
-            sel = cand[i, :want]
-        else:
-            seen, sel_l = set(), []
-            for v in cand[i]:
-                if v not in seen:
-                    seen.add(int(v)); sel_l.append(int(v))
-                    if len(sel_l) == want:
-                        break
-            k = 0
-            while len(sel_l) < want:  # extremely rare: draw more from a further stream
-                v = int(uniform01(np.array([i * 1024 + k], dtype=np.uint64), seed, 3)[0] * n)
-                k += 1
-                if v not in seen:
-                    seen.add(v); sel_l.append(v)
-            sel = np.array(sel_l, dtype=np.int64)
-        out_rows.append(np.sort(sel))
-        lens[i] = len(sel)
+    # position of each candidate's first occurrence in its row
+    order = np.argsort(cand, axis=1, kind="stable")
+    sc = np.take_along_axis(cand, order, axis=1)
+    first = np.ones_like(sc, dtype=bool)
+    first[:, 1:] = sc[:, 1:] != sc[:, :-1]
+    keep = np.zeros_like(first)
+    np.put_along_axis(keep, order, first, axis=1)          # True at first occurrences
+    rank = np.cumsum(keep, axis=1) - 1                      # index among distinct draws
+    take = keep & (rank < rlen[:, None])
+    lens = take.sum(axis=1).astype(np.int64)
+    short = np.nonzero(lens < rlen)[0]
+    rows_sel, cols_sel = np.nonzero(take)
+    vals = cand[rows_sel, cols_sel]
+    extra_r, extra_c = [], []
+    for i in short:   # extremely rare: draw more from a further stream
+        seen = set(cand[i][keep[i]].tolist())
+        k = 0
+        while len(seen) < rlen[i]:
+            v = int(uniform01(np.array([int(i) * 1024 + k], dtype=np.uint64), seed, 3)[0] * n)
+            k += 1
+            if v not in seen:
+                seen.add(v); extra_r.append(i); extra_c.append(v)
+    r_all = np.concatenate([rows_sel.astype(np.int64), np.array(extra_r, dtype=np.int64)])
+    c_all = np.concatenate([vals, np.array(extra_c, dtype=np.int64)])
+    o = np.lexsort((c_all, r_all))
+    r_all, c_all = r_all[o], c_all[o]
     rp = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(lens, out=rp[1:])
-    col = np.concatenate(out_rows).astype(np.int32) if n else np.zeros(0, np.int32)
+    np.cumsum(np.bincount(r_all, minlength=n), out=rp[1:])
+    col = c_all.astype(np.int32)
     nnz = int(rp[-1])
     ctr = np.arange(nnz, dtype=np.uint64)
     u1 = uniform01(ctr, seed, 4)

@@ -162,6 +162,61 @@ def test_double_word_range_fallback(h):
         assert_matches(c, oracle.spgemm(a2, b2), "f64")
 
 
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_huge_rows_window_and_hash(h, shuffle):
+    """Rows with more than 4096 outputs: sorted rows of B take the windowed
+    dense accumulator, unsorted ones the two-level hash map."""
+    a = _spread_rows([3, 9000, 700, 15000], 20000, 17)
+    b = I.random_csr(20000, 70000, 0.0003, 18, shuffle_cols=shuffle)
+    for dt, tag in ((np.float64, "f64"), (np.float32, "f32")):
+        c = run(h, a, b, dt)
+        assert_matches(c, oracle_product(a, b, dt), tag)
+    sym, num = h.bin_counts()
+    assert num[6] > 0
+
+
+def _strided_rows(nrows, ncols, widths, mult, step, seed):
+    """Row i holds widths[i % len(widths)] columns (i*mult + t*step) mod ncols."""
+    rows, cols = [], []
+    for i in range(nrows):
+        w = widths[i % len(widths)]
+        cols.extend(((i * mult + np.arange(w, dtype=np.int64) * step) % ncols).tolist())
+        rows.extend([i] * w)
+    key = np.unique(np.array(rows, dtype=np.int64) * ncols + np.array(cols, dtype=np.int64))
+    rp = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(key // ncols, minlength=nrows), out=rp[1:])
+    return I.Csr(nrows, ncols, rp, (key % ncols).astype(np.int32),
+                 I.uniform01(np.arange(len(key), dtype=np.uint64), seed) - 0.5)
+
+
+@pytest.mark.parametrize("small_cap", [32, 16])
+@pytest.mark.parametrize("ncols", [9000, 50000, 300000])
+def test_medium_rows_every_span(h, ncols, small_cap):
+    """Rows of 17..1024 outputs whose columns span at most 512 blocks of 32
+    (first dense rank accumulator), 512..2048 blocks (second), or more (hash
+    maps), in FP32, double-word FP64 and native FP64."""
+    nb = 3000
+    a = _strided_rows(1200, nb, [1, 2, 5, 9, 17, 30, 44], 7, 11, 41)
+    b = _strided_rows(nb, ncols, [20, 23], 37, ncols // 23 + 1, 42)
+    h.set_option(sg.OPT_SMALL_CAP, small_cap)
+    h.set_timing(True)
+    h.reset_timings()
+    try:
+        for dt, tag, native in ((np.float64, "f64", 0), (np.float64, "f64", 1), (np.float32, "f32", 0)):
+            h.set_option(sg.OPT_F64_NATIVE, native)
+            c = run(h, a, b, dt)
+            assert_matches(c, oracle_product(a, b, dt), tag)
+        labels = set(h.timings())
+    finally:
+        h.set_option(sg.OPT_F64_NATIVE, 0)
+        h.set_option(sg.OPT_SMALL_CAP, 32)
+        h.set_timing(False)
+    sym, num = h.bin_counts()
+    assert num[2] > 0 and num[3] > 0 and num[4] > 0, num
+    want = {9000: "numeric.rank512", 50000: "numeric.rank2048", 300000: "numeric.wide"}[ncols]
+    assert any(l.startswith(want) for l in labels), labels
+
+
 def test_heavy_rows_random(h):
     """Rows whose products overlap heavily (many insertions per key)."""
     a = _spread_rows([5, 50, 500, 5000], 6000, 7)
