@@ -146,12 +146,13 @@ def chunked256(args, world, local):
     val = torch.empty(nnz, dtype=torch.float64).pin_memory()
     Cm = sg.HostCsr(a.nrows, a.ncols, rp, col, val)
     clocks = bench.ClockSampler(local)
-    times, stats = [], None
+    times, sym_times, stats = [], [], None
     clocks.start()
     for it in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rp2, nnz2 = h.chunked_symbolic(A, A, budget)
+        t1 = time.perf_counter()
         sym = h.chunked_stats()
         Cm.row_ptr.copy_(rp2)
         h.chunked_numeric_into(A, A, Cm, budget)
@@ -159,8 +160,17 @@ def chunked256(args, world, local):
         stats = h.chunked_stats()
         if it > 0:
             times.append(dt)
+            sym_times.append(t1 - t0)
     clk = clocks.stop()
     ms = 1e3 * statistics.median(times)
+    # per-kernel device time of one more (untimed) step
+    h.set_timing(True)
+    h.reset_timings()
+    h.chunked_symbolic(A, A, budget)
+    h.chunked_numeric_into(A, A, Cm, budget)
+    torch.cuda.synchronize()
+    kern = {k: round(v[2], 3) for k, v in h.timings().items()}
+    h.set_timing(False)
     size_a = 8 * (a.nrows + 1) + 12 * a.nnz
     size_c = 8 * (a.nrows + 1) + 12 * nnz
     minimal = 2 * size_a + size_c            # A and B in, C out, each once
@@ -175,6 +185,7 @@ def chunked256(args, world, local):
                         "traffic": moved, "note": "achieved = minimal bytes (A, B in and C out "
                         "once) over time; traffic = bytes actually copied (symbolic + numeric)"},
            "link_gbs_measured": link, "numeric_plan": stats, "symbolic_plan": sym,
+           "symbolic_ms": 1e3 * statistics.median(sym_times), "kernels_ms": kern,
            "clocks": clk})
 
 
@@ -240,6 +251,14 @@ def batched256(args, world, local):
         p0 += c.nnz
     bwd_loop = timed(lambda: [hh.backward(A, B, c, d) for (hh, A, B, c), d in zip(singles, dcs)],
                      max(1, args.steps // 2))
+    # per-kernel breakdown of one batched forward and backward (untimed pass)
+    h.set_timing(True)
+    h.reset_timings()
+    bt.run()
+    bt.backward(Cm, dc)
+    torch.cuda.synchronize()
+    kern = {k: round(v[2], 4) for k, v in h.timings().items()}
+    h.set_timing(False)
     gf = lambda ms: 2 * mults / (ms / 1e3) / 1e9
     _line(args, world, gf(fwd_batched), fwd_batched, "f32",
           {"workload": "256 products A_i*B_i, n_i log-uniform in [1024, 65536], 4-32 random "
@@ -251,4 +270,4 @@ def batched256(args, world, local):
            "numeric_speedup": num_loop / num_graph,
            "batched_backward_ms": bwd_batched, "loop_backward_ms": bwd_loop,
            "backward_speedup": bwd_loop / bwd_batched,
-           "loop_forward_gflops": gf(fwd_loop)})
+           "loop_forward_gflops": gf(fwd_loop), "kernels_ms": kern})

@@ -307,7 +307,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         if (second > 0) {
             SG_TRY(launch_scatter_bins(n, bins, C_row_ptr, rows, h->dstate, 0, c));
             SG_TRY(launch_symbolic(*A, *B, pairs, ccnt, rows, h->hstate->bin_count[0], C_row_ptr,
-                                   &h->dstate->err, w + o_gws, gws_bytes, c));
+                                   &h->dstate->err, w + o_gws, gws_bytes, minmax, c));
         }
         SG_TRY(launch_scan_counts(C_row_ptr, n, &h->dstate->nnz, w + o_tmp, c));
         SG_TRY(launch_numeric_binning(n, C_row_ptr, flops, bins, h->dstate, c));

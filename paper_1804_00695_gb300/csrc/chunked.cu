@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_fma_warp(
 // Same for rows with more than FMA_WARP_CAP entries: a block per row, map
 // and sort buffer in global memory (per block: 2^L slots, L from cap_max).
 template <typename V>
-__global__ void __launch_bounds__(256) k_fma_block(
+__global__ void __launch_bounds__(256, 1) k_fma_block(
     int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const V *__restrict__ aval, int64_t lo, int64_t hi, const int64_t *__restrict__ brp,
     const int32_t *__restrict__ bcol, const V *__restrict__ bval, const int64_t *__restrict__ crp,

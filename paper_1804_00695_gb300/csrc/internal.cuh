@@ -153,7 +153,7 @@ int launch_symbolic_first(const spgemm_csr &A, const uint8_t *bins, const int4 *
 // rows = concatenated bin lists.  Writes nnz(C_i) to crp[i+1].
 int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
                     const int32_t *ccnt, const int32_t *rows, const long long *counts,
-                    int64_t *crp, int *err, void *gws, size_t gws_bytes, Ctx &c);
+                    int64_t *crp, int *err, void *gws, size_t gws_bytes, const int2 *bmm, Ctx &c);
 size_t symbolic_global_ws(int64_t ncols_b, int nsm);
 
 // numeric.cu

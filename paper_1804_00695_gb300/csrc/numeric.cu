@@ -1,21 +1,24 @@
-// Numeric phase (Section 2.1): C_i = sum over stored a_ik of a_ik * B_k,
-// accumulated in hash maps from column to value (Section 2.1, "sparse
-// hashmap-based accumulators"); maps live in shared memory and, for the
-// largest rows, a second level in global memory takes what the first cannot
-// hold (Section 3.3).  Every map is sized from the row's exact count, known
-// from the symbolic phase.  Output rows have ascending columns.
+// Numeric phase (Section 2.1): C_i = sum over stored a_ik of a_ik * B_k.
+// Rows are binned by their exact output count (known from the symbolic
+// phase) and their products:
 //
-// Rows with at most 32 outputs (bins 1, 2) are taken in row order by groups
-// of G lanes; the lanes of a group walk one row of B at a time (coalesced
-// loads), so within a step they touch distinct columns and update their
-// accumulators without atomics; a __syncwarp separates the rows of B.
-// Bin 3 (<= 128 outputs) gives a warp per row the same way; bins 4-6 give a
-// block per row with atomic updates.
+// * bins 1-2 (<= 32 outputs): groups of G lanes per row, a shared-memory
+//   hash map from column to value per row (Section 2.1, "sparse
+//   hashmap-based accumulators"), products dealt evenly over the lanes;
+// * bins 3-4 (<= 1024 outputs): a warp per row with a dense rank
+//   accumulator over the row's column span (bitmap, prefix counts, values
+//   by rank) when the span is at most 2048 blocks of 32 columns, else a
+//   warp-level shared hash map;
+// * bin 5 (<= 4096 outputs): a block per row, shared hash map;
+// * bin 6 (more): a windowed dense accumulator when the rows of B are
+//   sorted, else a two-level hash map (shared, then global memory: Section
+//   3.3's multilevel memory).
 //
-// FP64 values are accumulated as double-words (two floats, 48 significand
-// bits: dword.cuh) in the FP32 pipeline unless an input lies outside the
-// double-word range, in which case that row (or, for B, the whole call) uses
-// native FP64; the block kernels accumulate in native precision.
+// Output rows have ascending columns.  FP64 values are accumulated as
+// double-words (two floats, 48 significand bits: dword.cuh) in the FP32
+// pipeline unless an input lies outside the double-word range, in which
+// case that row (or, for B, the whole call) uses native FP64; the block
+// kernels accumulate in native precision.
 #include <climits>
 #include <type_traits>
 #include "dword.cuh"
@@ -178,33 +181,43 @@ __device__ __forceinline__ void acc_slot(float *hi, float *lo, float *lo2, int s
 // stored a_ik are staged E at a time in shared memory with the prefix sums
 // of nnz(B_k), and in each step the G lanes take G consecutive products
 // (lane l the t-th, t = step*G + l), finding their a_ik with a cursor that
-// only moves forward.  Loads of B stay coalesced within each B_k.  Lanes of
-// a row that hold the same column in a step are merged with
-// __match_any_sync and only the lowest of them updates the slot, adding
-// the others' products one by one, so every slot has a single writer per
-// step and no atomics are needed; all lanes of the warp stay converged.
+// only moves forward.  Loads of B stay coalesced within each B_k.  Products
+// are added to their slot with shared-memory atomics; double-words keep
+// three levels whose rounding errors are recovered exactly from the old
+// values the atomics return.  The occupied slots are then compacted and
+// each row written in ascending column order (rank by counting).
+// Per-row-slot layout of k_num_small in 32-bit words: hi[SMAX], lo[SMAX],
+// lo2[SMAX], keys[SMAX], eq0[E] (int64), ea[E] (double), pre[E+1].  The
+// stride is padded to G (mod 32) words so that the 32/G row slots of a warp
+// start on different banks.
+template <int G>
+struct SmallLayout {
+    static constexpr int SMAX = 64, E = 32;
+    static constexpr int raw = 4 * SMAX + 2 * E + 2 * E + E + 1;
+    static constexpr int stride = G == 32 ? ((raw + 1) & ~1) : raw + ((G - raw % 32) + 32) % 32;
+    static_assert(stride % 2 == 0, "8-byte arrays need an even stride");
+};
+
 template <int G, int MODE>
-__global__ void __launch_bounds__(256) k_num_small(NumP a, const int4 *__restrict__ bdesc, int64_t n,
+__global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const int4 *__restrict__ bdesc, int64_t n,
                                                    const uint8_t *__restrict__ bins,
                                                    const DevState *st, int *err, int maxbin,
                                                    int slot_factor) {
-    constexpr int SMAX = 64, RPW = 32 / G, WPB = 8, PER = SMAX / G;
-    constexpr int E = 32, EL = E / G;   // entries staged per batch, per lane
+    constexpr int SMAX = SmallLayout<G>::SMAX, RPW = 32 / G, WPB = 8, PER = SMAX / G;
+    constexpr int E = SmallLayout<G>::E, EL = E / G;   // entries staged per batch, per lane
     using V = ValT<MODE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / G, gl = lane % G, gbase = g * G;
     const int rs = w * RPW + g;   // row slot in the block
-    constexpr int NR = WPB * RPW;
-    // layout (per row slot): hi[SMAX] lo[SMAX] lo2[SMAX] keys[SMAX] | eq0[E] ea[E] | pre[E+1]
-    float *hi = (float *)smem_raw + rs * SMAX;
-    float *lo = (float *)smem_raw + NR * SMAX + rs * SMAX;
-    float *lo2 = (float *)smem_raw + 2 * NR * SMAX + rs * SMAX;
-    int *keys = (int *)smem_raw + 3 * NR * SMAX + rs * SMAX;
-    long long *eq0 = (long long *)((int *)smem_raw + 4 * NR * SMAX) + rs * E;
-    double *ea = (double *)((long long *)((int *)smem_raw + 4 * NR * SMAX) + NR * E) + rs * E;
-    int *pre = (int *)((double *)((long long *)((int *)smem_raw + 4 * NR * SMAX) + NR * E) + NR * E) +
-               rs * (E + 1);
+    int *reg = (int *)smem_raw + rs * SmallLayout<G>::stride;
+    float *hi = (float *)reg;
+    float *lo = hi + SMAX;
+    float *lo2 = lo + SMAX;
+    int *keys = (int *)(lo2 + SMAX);
+    long long *eq0 = (long long *)(keys + SMAX);
+    double *ea = (double *)(eq0 + E);
+    int *pre = (int *)(ea + E);
     // native FP64 rows keep a double's low word in hi[] and its high word in lo[]
     const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
     const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
@@ -238,7 +251,11 @@ __global__ void __launch_bounds__(256) k_num_small(NumP a, const int4 *__restric
             nat = ((bad >> gbase) & lmask) != 0;
         }
         const int maxlen = __reduce_max_sync(0xffffffffu, plen);
-        const bool three = plen > DW2_MAX_TERMS;
+        // warps without native rows add with atomics (three levels for
+        // double-words); a warp holding a native row merges same-slot lanes
+        // with __match_any_sync and adds in turns
+        const bool wnat = MODE == MODE_F64 || __any_sync(0xffffffffu, nat);
+        const bool three = !wnat || plen > DW2_MAX_TERMS;
         for (int pb = 0; pb < maxlen; pb += E) {
             // stage entries [pb, pb+E): lane gl takes EL consecutive entries
             int cnt[EL];
@@ -308,6 +325,22 @@ __global__ void __launch_bounds__(256) k_num_small(NumP a, const int4 *__restric
                         px = __int_as_float(__double2loint(pd));
                         py = __int_as_float(__double2hiint(pd));
                     }
+                }
+                if (!wnat) {
+                    if (slot >= 0) {
+                        if (MODE == MODE_F32) {
+                            atomicAdd(&hi[slot], px);
+                        } else {
+                            float s1, e1, tt, f, s2, e2;
+                            const float o1 = atomicAdd(&hi[slot], px);
+                            two_sum(o1, px, s1, e1);
+                            two_sum(e1, py, tt, f);
+                            const float o2 = atomicAdd(&lo[slot], tt);
+                            two_sum(o2, tt, s2, e2);
+                            atomicAdd(&lo2[slot], __fadd_rn(e2, f));
+                        }
+                    }
+                    continue;
                 }
                 // lanes of this row holding the same slot update it in turns,
                 // ordered by their rank among those lanes
@@ -441,25 +474,31 @@ struct RankVal {
 template <int BW, int NMAX, int WPB, int MODE>
 struct RankLayout {
     static constexpr size_t per_warp =
-        ((size_t)BW * 6 + (size_t)NMAX * RankVal<MODE>::bytes + 32 * 16 + 33 * 4 + 64 + 15) & ~(size_t)15;
+        ((size_t)BW * 6 + (size_t)BW / 8 + (size_t)NMAX * RankVal<MODE>::bytes + 32 * 16 + 33 * 4 + 64 + 15) &
+        ~(size_t)15;
     static constexpr size_t bytes = per_warp * WPB;
 };
 
+// The bitmap words a row touches are listed by a summary bitmap (one bit
+// per word), so the prefix counts, the output and the clean-up visit only
+// those words: the work per row follows its outputs, not its span.  A row
+// leaves its bitmap words and summary zero for the next.
 template <int BW, int NMAX, int WPB, int MODE>
-__global__ void __launch_bounds__(WPB * 32) k_num_rank(NumP a, const int4 *__restrict__ bdesc,
+__global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__restrict__ bdesc,
                                                        const int2 *__restrict__ bmm,
                                                        const int32_t *__restrict__ rows, int64_t count,
                                                        int min_span_words, const DevState *st, int *err) {
     using Lay = RankLayout<BW, NMAX, WPB, MODE>;
     using V = ValT<MODE>;
-    constexpr int E = 32;
+    constexpr int E = 32, NS = BW / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *base = smem_raw + (size_t)w * Lay::per_warp;
     long long *eq0 = (long long *)base;
     double *ea = (double *)(eq0 + E);
     unsigned *bits = (unsigned *)(ea + E);
-    unsigned short *pref = (unsigned short *)(bits + BW);
+    unsigned *summ = bits + BW;
+    unsigned short *pref = (unsigned short *)(summ + NS);
     unsigned char *vbase = (unsigned char *)(((uintptr_t)(pref + BW) + 15) & ~(uintptr_t)15);
     float *vf = (float *)vbase;                              // FP32
     double *v8 = (double *)vbase;                            // native FP64
@@ -468,6 +507,9 @@ __global__ void __launch_bounds__(WPB * 32) k_num_rank(NumP a, const int4 *__res
     int *pre = (int *)(vbase + (size_t)NMAX * RankVal<MODE>::bytes);
     const bool b_bad = MODE == MODE_DW && st->b_out_of_range;
     int flag = 0;
+    for (int x = lane; x < BW; x += 32) bits[x] = 0;
+    for (int x = lane; x < NS; x += 32) summ[x] = 0;
+    __syncwarp();
     for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
         const int64_t out = a.crp[i];
@@ -484,12 +526,14 @@ __global__ void __launch_bounds__(WPB * 32) k_num_rank(NumP a, const int4 *__res
             for (int pp = lane; pp < plen; pp += 32) dw_split(((const double *)a.aval)[p0 + pp], ok);
             nat = !__all_sync(0xffffffffu, ok);
         }
-        for (int x = lane; x < nw; x += 32) bits[x] = 0;
         for (int x = lane; x < nn; x += 32) {
             if (MODE == MODE_F32) vf[x] = 0.f;
             else if (MODE == MODE_DW) { v2[x] = make_float2(0.f, 0.f); v3[x] = 0.f; }
             else v8[x] = 0.0;
         }
+        const int ns = (nw + 31) / 32;                 // summary words of the span
+        const int sper = (ns + 31) / 32;               // per lane, contiguous
+        const int s0 = min(ns, lane * sper), s1 = min(ns, s0 + sper);
         __syncwarp();
         for (int pass = 0; pass < 2; pass++) {
             for (int pb = 0; pb < plen; pb += E) {
@@ -519,71 +563,128 @@ __global__ void __launch_bounds__(WPB * 32) k_num_rank(NumP a, const int4 *__res
                 if (lane == 31) pre[E] = incl;
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
                 __syncwarp();
+                // two products per lane per step (t and t + 32), loads issued together
                 int e = 0;
-                for (int t0 = 0; t0 < total; t0 += 32) {
-                    const int tt = t0 + lane;
-                    if (tt < total) {
-                        while (pre[e + 1] <= tt) e++;
-                        const int64_t q = eq0[e] + (tt - pre[e]);
-                        const int col = a.bcol[q];
-                        const int wd = (col >> 5) - bmin;
-                        const unsigned bit = 1u << (col & 31);
-                        if (pass == 0) {
-                            atomicOr(&bits[wd], bit);
-                        } else {
-                            const int r = (int)pref[wd] + __popc(bits[wd] & (bit - 1));
-                            if (MODE == MODE_F32) {
-                                atomicAdd(&vf[r], (float)ea[e] * ((const float *)a.bval)[q]);
-                            } else if (MODE == MODE_DW && !nat) {
-                                const unsigned long long bb = (unsigned long long)__double_as_longlong(ea[e]);
-                                const float2 a2 = make_float2(__uint_as_float((unsigned)bb),
-                                                              __uint_as_float((unsigned)(bb >> 32)));
-                                dw_atomic_acc(v2, v3, r, dw_mul(a2, a.bsplit[q]));
-                            } else {
-                                atomicAdd(&v8[r], ea[e] * ((const double *)a.bval)[q]);
-                            }
+                for (int t0 = 0; t0 < total; t0 += 64) {
+                    const int ta = t0 + lane, tb = ta + 32;
+                    int ex = -1, ey = -1;
+                    int64_t qx = 0, qy = 0;
+                    if (ta < total) {
+                        while (pre[e + 1] <= ta) e++;
+                        ex = e;
+                        qx = eq0[e] + (ta - pre[e]);
+                    }
+                    if (tb < total) {
+                        while (pre[e + 1] <= tb) e++;
+                        ey = e;
+                        qy = eq0[e] + (tb - pre[e]);
+                    }
+                    const int colx = ex >= 0 ? a.bcol[qx] : 0;
+                    const int coly = ey >= 0 ? a.bcol[qy] : 0;
+                    if (pass == 0) {
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; h2++) {
+                            if ((h2 ? ey : ex) < 0) continue;
+                            const int col = h2 ? coly : colx;
+                            const int wd = (col >> 5) - bmin;
+                            if (atomicOr(&bits[wd], 1u << (col & 31)) == 0)
+                                atomicOr(&summ[wd >> 5], 1u << (wd & 31));
+                        }
+                    } else if (MODE == MODE_F32) {
+                        const float bx = ex >= 0 ? ((const float *)a.bval)[qx] : 0.f;
+                        const float by = ey >= 0 ? ((const float *)a.bval)[qy] : 0.f;
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; h2++) {
+                            const int ee = h2 ? ey : ex;
+                            if (ee < 0) continue;
+                            const int col = h2 ? coly : colx;
+                            const int wd = (col >> 5) - bmin;
+                            const int r = (int)pref[wd] + __popc(bits[wd] & ((1u << (col & 31)) - 1));
+                            atomicAdd(&vf[r], (float)ea[ee] * (h2 ? by : bx));
+                        }
+                    } else if (MODE == MODE_DW && !nat) {
+                        const float2 bx = ex >= 0 ? a.bsplit[qx] : make_float2(0.f, 0.f);
+                        const float2 by = ey >= 0 ? a.bsplit[qy] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; h2++) {
+                            const int ee = h2 ? ey : ex;
+                            if (ee < 0) continue;
+                            const int col = h2 ? coly : colx;
+                            const int wd = (col >> 5) - bmin;
+                            const int r = (int)pref[wd] + __popc(bits[wd] & ((1u << (col & 31)) - 1));
+                            const unsigned long long bb = (unsigned long long)__double_as_longlong(ea[ee]);
+                            const float2 a2 = make_float2(__uint_as_float((unsigned)bb),
+                                                          __uint_as_float((unsigned)(bb >> 32)));
+                            dw_atomic_acc(v2, v3, r, dw_mul(a2, h2 ? by : bx));
+                        }
+                    } else {
+                        const double bx = ex >= 0 ? ((const double *)a.bval)[qx] : 0.0;
+                        const double by = ey >= 0 ? ((const double *)a.bval)[qy] : 0.0;
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; h2++) {
+                            const int ee = h2 ? ey : ex;
+                            if (ee < 0) continue;
+                            const int col = h2 ? coly : colx;
+                            const int wd = (col >> 5) - bmin;
+                            const int r = (int)pref[wd] + __popc(bits[wd] & ((1u << (col & 31)) - 1));
+                            atomicAdd(&v8[r], ea[ee] * (h2 ? by : bx));
                         }
                     }
                 }
                 __syncwarp();
             }
             if (pass == 0) {
-                // prefix counts of the words: a contiguous run per lane, warp scan
-                const int per = (nw + 31) / 32;
-                const int x0 = min(nw, lane * per), x1 = min(nw, x0 + per);
+                // prefix counts of the touched words, in word order
                 int sum = 0;
-                for (int x = x0; x < x1; x++) sum += __popc(bits[x]);
+                for (int y = s0; y < s1; y++) {
+                    unsigned sw = summ[y];
+                    while (sw) {
+                        const int x = y * 32 + __ffs(sw) - 1;
+                        sw &= sw - 1;
+                        sum += __popc(bits[x]);
+                    }
+                }
                 int incl = sum;
                 for (int d = 1; d < 32; d <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl += y;
+                    const int yv = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += yv;
                 }
                 int run = incl - sum;
-                for (int x = x0; x < x1; x++) {
-                    pref[x] = (unsigned short)run;
-                    run += __popc(bits[x]);
+                for (int y = s0; y < s1; y++) {
+                    unsigned sw = summ[y];
+                    while (sw) {
+                        const int x = y * 32 + __ffs(sw) - 1;
+                        sw &= sw - 1;
+                        pref[x] = (unsigned short)run;
+                        run += __popc(bits[x]);
+                    }
                 }
                 if (__shfl_sync(0xffffffffu, incl, 31) != nn) flag |= DERR_COUNT;
                 __syncwarp();
             }
         }
-        // write the row in column order straight from the bitmap
-        const int per = (nw + 31) / 32;
-        const int x0 = min(nw, lane * per), x1 = min(nw, x0 + per);
-        for (int x = x0; x < x1; x++) {
-            unsigned word = bits[x];
-            int r = pref[x];
-            while (word) {
-                const int b = __ffs(word) - 1;
-                word &= word - 1;
-                if (r < nn) {
-                    a.ccol[out + r] = (bmin + x) * 32 + b;
-                    if (MODE == MODE_F32) ((float *)a.cval)[out + r] = vf[r];
-                    else if (MODE == MODE_DW && !nat) ((double *)a.cval)[out + r] = dw3_to_double(v2[r].x, v2[r].y, v3[r]);
-                    else ((double *)a.cval)[out + r] = v8[r];
+        // write the row in column order from the touched words, clearing them
+        for (int y = s0; y < s1; y++) {
+            unsigned sw = summ[y];
+            while (sw) {
+                const int x = y * 32 + __ffs(sw) - 1;
+                sw &= sw - 1;
+                unsigned word = bits[x];
+                int r = pref[x];
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    if (r < nn) {
+                        a.ccol[out + r] = (bmin + x) * 32 + b;
+                        if (MODE == MODE_F32) ((float *)a.cval)[out + r] = vf[r];
+                        else if (MODE == MODE_DW && !nat) ((double *)a.cval)[out + r] = dw3_to_double(v2[r].x, v2[r].y, v3[r]);
+                        else ((double *)a.cval)[out + r] = v8[r];
+                    }
+                    r++;
                 }
-                r++;
+                bits[x] = 0;
             }
+            summ[y] = 0;
         }
         __syncwarp();
     }
@@ -615,7 +716,7 @@ struct WideLayout {
 };
 
 template <int SMAX, int BW, int WPB, int MODE>
-__global__ void __launch_bounds__(WPB * 32) k_num_wide(NumP a, const int4 *__restrict__ bdesc,
+__global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__restrict__ bdesc,
                                                        const int2 *__restrict__ bmm,
                                                        const int32_t *__restrict__ rows, int64_t count,
                                                        int min_nnz, int min_span_words, const DevState *st,
@@ -911,7 +1012,7 @@ __global__ void __launch_bounds__(BS) k_num_block(
 constexpr int HUGE_BS = 512, HUGE_L1 = 4096, HUGE_PROBES = 16;
 
 template <typename V>
-__global__ void __launch_bounds__(HUGE_BS) k_num_huge(
+__global__ void __launch_bounds__(HUGE_BS, 1) k_num_huge(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol, const V *__restrict__ aval,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, const V *__restrict__ bval,
     const int64_t *__restrict__ crp, int32_t *__restrict__ ccol, V *__restrict__ cval,
@@ -1033,29 +1134,35 @@ __global__ void __launch_bounds__(HUGE_BS) k_num_huge(
 
 // Bin 6 when every row of B is sorted: a dense accumulator over windows of
 // W columns (Section 3.1's dense accumulator, kept in shared memory a window
-// at a time).  Each stored a_ik keeps a cursor into B_k; for a window, the
-// lanes of a warp advance the cursor over the entries of B_k that fall in it
-// and add a_ik * b_kj into win[j - w0] (atomically) while marking j in a
-// bitmap.  The window's entries then leave in column order: prefix counts of
-// the bitmap words give each its place, and the slot is cleared as it is
-// read.  Windows between the row's first and last reachable column are
-// visited in order, so the row is written sorted without a sort.  Global
-// memory per block: one 8-byte cursor per stored entry of the longest row.
-constexpr int WIN_BS = 512;
+// at a time).  Each stored a_ik keeps a cursor into B_k and the column it
+// points at.  For a window, a thread per a_ik whose next column falls in
+// the window adds a_ik * b_kj into win[j - w0] (atomically) while marking j
+// in a bitmap, until B_k leaves the window; rows of B longer than WIN_LONG
+// are walked by whole warps instead (32 entries per step).  The window's
+// entries then leave in column order: prefix counts of the bitmap words give
+// each its place, and the slot is cleared as it is read.  Windows between
+// the row's first and last reachable column are visited in order, so the
+// row is written sorted without a sort.  Global memory per block: a cursor,
+// a next column and a list slot per stored entry of the longest row.
+constexpr int WIN_BS = 512, WIN_BPSM = 2, WIN_LONG = 256;
 
 template <typename V, int W>
-__global__ void __launch_bounds__(WIN_BS) k_num_window(
+__global__ void __launch_bounds__(WIN_BS, WIN_BPSM) k_num_window(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol, const V *__restrict__ aval,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, const V *__restrict__ bval,
     const int64_t *__restrict__ crp, int32_t *__restrict__ ccol, V *__restrict__ cval,
-    const int32_t *__restrict__ rows, int64_t count, int *err, int64_t max_alen, int64_t *gcur) {
+    const int32_t *__restrict__ rows, int64_t count, int *err, int64_t max_alen, unsigned char *gws) {
     constexpr int NW = W / 32, NWARP = WIN_BS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *win = (V *)smem_raw;
     unsigned *bits = (unsigned *)(win + W);
-    __shared__ int bmin_s, bmax_s, wtot;
+    __shared__ int bmin_s, bmax_s, wtot, nlong;
     __shared__ int red[NWARP];
-    int64_t *cur = gcur + (size_t)blockIdx.x * (size_t)max_alen;
+    const size_t per = (size_t)max_alen;
+    int64_t *cpos = (int64_t *)gws + (size_t)blockIdx.x * per;
+    int32_t *cnext = (int32_t *)((int64_t *)gws + (size_t)gridDim.x * per) + (size_t)blockIdx.x * per;
+    int32_t *llist = (int32_t *)((int64_t *)gws + (size_t)gridDim.x * per) + (size_t)gridDim.x * per +
+                     (size_t)blockIdx.x * per;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int flag = 0;
     for (int x = threadIdx.x; x < W; x += WIN_BS) win[x] = V(0);
@@ -1066,31 +1173,60 @@ __global__ void __launch_bounds__(WIN_BS) k_num_window(
         if (threadIdx.x == 0) {
             bmin_s = INT_MAX;
             bmax_s = -1;
+            nlong = 0;
         }
         __syncthreads();
         int lmin = INT_MAX, lmax = -1;
         for (int64_t p = threadIdx.x; p < plen; p += WIN_BS) {
             const int k = acol[p0 + p];
             const int64_t q0 = brp[k], q1 = brp[k + 1];
-            cur[p] = q0;
+            cpos[p] = q0;
+            int nxt = INT_MAX;
             if (q1 > q0) {
-                lmin = min(lmin, bcol[q0]);
+                nxt = bcol[q0];
+                lmin = min(lmin, nxt);
                 lmax = max(lmax, bcol[q1 - 1]);
             }
+            if (q1 - q0 > WIN_LONG) {
+                llist[atomicAdd(&nlong, 1)] = (int)p;
+                nxt = INT_MAX;   // walked by warps
+            }
+            cnext[p] = nxt;
         }
         atomicMin(&bmin_s, lmin);
         atomicMax(&bmax_s, lmax);
         __syncthreads();
-        const int cmin = bmin_s, cmax = bmax_s;
+        const int cmin = bmin_s, cmax = bmax_s, nl = nlong;
         int64_t written = 0;
         for (int64_t w0 = cmax >= 0 ? ((int64_t)cmin / W) * W : 1; w0 <= cmax; w0 += W) {
             const int64_t w1 = w0 + W;
             for (int x = threadIdx.x; x < NW; x += WIN_BS) bits[x] = 0;
             __syncthreads();
-            for (int64_t p = w; p < plen; p += NWARP) {
+            // short rows of B: a thread per stored a_ik
+            for (int64_t p = threadIdx.x; p < plen; p += WIN_BS) {
+                int c = cnext[p];
+                if (c == INT_MAX || (int64_t)c >= w1) continue;   // INT_MAX: done or long
                 const int k = acol[p0 + p];
                 const V av = aval[p0 + p];
-                int64_t c = cur[p];
+                const int64_t q1 = brp[k + 1];
+                int64_t q = cpos[p];
+                while (true) {
+                    const int rel = (int)(c - w0);
+                    atomicAdd(&win[rel], av * bval[q]);
+                    atomicOr(&bits[rel >> 5], 1u << (rel & 31));
+                    if (++q >= q1) { c = INT_MAX; break; }
+                    c = bcol[q];
+                    if ((int64_t)c >= w1) break;
+                }
+                cpos[p] = q;
+                cnext[p] = c;
+            }
+            // long rows of B: a warp per stored a_ik, 32 entries per step
+            for (int j = w; j < nl; j += NWARP) {
+                const int p = llist[j];
+                const int k = acol[p0 + p];
+                const V av = aval[p0 + p];
+                int64_t c = cpos[p];
                 const int64_t q1 = brp[k + 1];
                 while (c < q1) {
                     const int64_t q = c + lane;
@@ -1105,10 +1241,10 @@ __global__ void __launch_bounds__(WIN_BS) k_num_window(
                     c += __popc(m);
                     if (m != 0xffffffffu) break;
                 }
-                if (lane == 0) cur[p] = c;
+                if (lane == 0) cpos[p] = c;
             }
             __syncthreads();
-            // prefix counts of the words, two per thread
+            // prefix counts of the words
             constexpr int PERT = (NW + WIN_BS - 1) / WIN_BS;
             int sum = 0;
 #pragma unroll
@@ -1164,7 +1300,11 @@ __global__ void __launch_bounds__(WIN_BS) k_num_window(
     if (flag) atomicOr(err, flag);
 }
 
-size_t window_global_ws(int64_t max_alen, int nsm) { return (size_t)(max_alen > 0 ? max_alen : 1) * 8 * (size_t)nsm; }
+// Cursor (8 B), next column (4 B) and long-row list slot (4 B) per stored
+// entry of the longest row, for every resident block.
+size_t window_global_ws(int64_t max_alen, int nsm) {
+    return (size_t)(max_alen > 0 ? max_alen : 1) * 16 * (size_t)nsm * WIN_BPSM;
+}
 
 // ------------------------------------------------------------------ host side
 template <typename K>
@@ -1181,7 +1321,7 @@ template <int G, int MODE>
 static int run_small(const NumP &a, const int4 *bdesc, int64_t n, const uint8_t *bins, DevState *st,
                      int *err, int maxbin, int slot_factor, Ctx &c) {
     constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
-    const size_t smem = (size_t)GPB * (64 * 16 + 32 * 16 + 33 * 4);
+    const size_t smem = (size_t)GPB * SmallLayout<G>::stride * 4;
     SG_TRY(prep(k_num_small<G, MODE>, smem));
     int64_t blocks = (n + GPB - 1) / GPB;
     const int64_t cap = (int64_t)c.nsm * 32;
@@ -1288,9 +1428,10 @@ static int run_huge(const NumP &a, const spgemm_csr &B, const int32_t *rows, int
 template <typename V>
 static int run_window(const NumP &a, const int32_t *rows, int64_t cnt, int *err, void *gws, size_t gws_bytes,
                       int64_t max_alen, Ctx &c) {
-    constexpr int W = sizeof(V) == 8 ? 16384 : 32768;
-    const int64_t blocks = cnt < (int64_t)c.nsm ? cnt : (int64_t)c.nsm;
-    if (window_global_ws(max_alen, (int)blocks) > gws_bytes) {
+    constexpr int W = sizeof(V) == 8 ? 8192 : 16384;
+    const int64_t cap = (int64_t)c.nsm * WIN_BPSM;
+    const int64_t blocks = cnt < cap ? cnt : cap;
+    if ((size_t)(max_alen > 0 ? max_alen : 1) * 16 * (size_t)blocks > gws_bytes) {
         set_error("numeric: cursor workspace too small");
         return SPGEMM_ERR_INTERNAL;
     }
@@ -1299,7 +1440,7 @@ static int run_window(const NumP &a, const int32_t *rows, int64_t cnt, int *err,
     c.begin("numeric.bin6_window", cnt);
     k_num_window<V, W><<<(unsigned)blocks, WIN_BS, smem, c.s>>>(
         a.arp, a.acol, (const V *)a.aval, a.brp, a.bcol, (const V *)a.bval, a.crp, a.ccol, (V *)a.cval, rows,
-        cnt, err, max_alen, (int64_t *)gws);
+        cnt, err, max_alen, (unsigned char *)gws);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;

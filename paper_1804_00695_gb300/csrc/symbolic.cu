@@ -8,10 +8,12 @@
 // takes every row with bound <= 4096 in row order with a 32-slot map per
 // row, G lanes sharing the row's stored a_ik; rows that do not fit are
 // marked and, with the rows whose bound exceeds 4096, handled by a second
-// pass from row lists: a warp with a 128- or 512-slot map (bins 2, 3), a
-// block with a 2048- or 8192-slot map (bins 4, 5), or a block with a dense
-// bitmap over all column blocks (bin 6; shared memory when it fits, global
-// memory otherwise).  Maps live in shared memory (Section 3.3).
+// pass from row lists.  In bins 2-5 a row whose column blocks span at most
+// 2048 blocks takes a warp with a bitmap over its span (k_sym_span); wider
+// rows take a warp with a 128- or 512-slot map (bins 2, 3) or a block with
+// a 2048- or 8192-slot map (bins 4, 5).  Bin 6 takes a block with a dense
+// bitmap over all column blocks (shared memory when it fits, global memory
+// otherwise).  Maps live in shared memory (Section 3.3).
 #include <climits>
 #include "internal.cuh"
 
@@ -40,33 +42,43 @@ __device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int L, in
     return false;
 }
 
+// Per-row-slot layout of k_sym_first in 32-bit words: keys[32], masks[32],
+// eq0[E] (int64), pre[E+1]; the stride is padded to G (mod 32) words so that
+// the row slots of a warp start on different banks.
+template <int G>
+struct SymFirstLayout {
+    static constexpr int S = SYM_FIRST_SLOTS, E = 32;
+    static constexpr int raw = 2 * S + 2 * E + E + 1;
+    static constexpr int stride = G == 32 ? ((raw + 1) & ~1) : raw + ((G - raw % 32) + 32) % 32;
+    static_assert(stride % 2 == 0, "8-byte arrays need an even stride");
+    static constexpr int o_keys = 0, o_masks = S, o_eq0 = 2 * S, o_pre = 2 * S + 2 * E;
+};
+
 // First pass: a warp takes 32/G consecutive rows, G lanes per row, 32-slot
-// map per row.  The compressed pairs a row visits are dealt out evenly: the
-// stored a_ik are staged E at a time in shared memory with the prefix sums
-// of pairs(B_k), and in each step the G lanes take G consecutive pairs,
-// finding their a_ik with a forward-only cursor; loads of pairs stay
-// coalesced within each B_k.  Insertions are atomic (CAS on the key, OR on
-// the mask), so lanes meeting the same block need no coordination.  A row
-// whose map fills up is marked crp[i+1] = -1 and counted in its second-pass
-// bin.
+// map per row.  The stored a_ik are staged E at a time in shared memory with
+// the prefix sums of pairs(B_k); each lane takes a contiguous run of the
+// batch's compressed pairs (ceil(total/G) of them), finds its first a_ik
+// once by bisection of the prefix sums and walks on in registers, so a pair
+// costs one load and one insertion.  Insertions are atomic (CAS on the key,
+// OR on the mask).  A row whose map fills up is marked crp[i+1] = -1 and
+// counted in its second-pass bin.
 template <int G>
 __global__ void __launch_bounds__(256) k_sym_first(
     int64_t n, const uint8_t *__restrict__ bins, const int64_t *__restrict__ arp,
     const int32_t *__restrict__ acol, const int4 *__restrict__ desc,
     const int2 *__restrict__ pairs, int64_t *__restrict__ crp, DevState *st) {
-    constexpr int S = SYM_FIRST_SLOTS, L = 5, RPW = 32 / G, WPB = 8, PER = S / G;
-    constexpr int E = 32, EL = E / G, NR = WPB * RPW;
-    __shared__ int keys_all[NR * S];
-    __shared__ unsigned masks_all[NR * S];
-    __shared__ long long eq0_all[NR * E];
-    __shared__ int pre_all[NR * (E + 1)];
+    using Lay = SymFirstLayout<G>;
+    constexpr int S = Lay::S, L = 5, RPW = 32 / G, WPB = 8, PER = S / G;
+    constexpr int E = Lay::E, EL = E / G, NR = WPB * RPW;
+    __shared__ __align__(16) int sm[NR * Lay::stride];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / G, gl = lane % G, gbase = g * G;
     const int rs = w * RPW + g;
-    int *keys = keys_all + rs * S;
-    unsigned *masks = masks_all + rs * S;
-    long long *eq0 = eq0_all + rs * E;
-    int *pre = pre_all + rs * (E + 1);
+    int *reg = sm + rs * Lay::stride;
+    int *keys = reg + Lay::o_keys;
+    unsigned *masks = (unsigned *)(reg + Lay::o_masks);
+    long long *eq0 = (long long *)(reg + Lay::o_eq0);
+    int *pre = reg + Lay::o_pre;
     const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
     const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
@@ -82,6 +94,7 @@ __global__ void __launch_bounds__(256) k_sym_first(
         }
         const int maxlen = __reduce_max_sync(0xffffffffu, plen);
         bool fail = false;
+        __syncwarp();
         for (int pb = 0; pb < maxlen; pb += E) {
             int cnt[EL];
             int lsum = 0;
@@ -112,15 +125,30 @@ __global__ void __launch_bounds__(256) k_sym_first(
             if (gl == G - 1) pre[E] = incl;
             int total = __shfl_sync(0xffffffffu, incl, gbase + G - 1);
             if (fail) total = 0;
-            const int maxtot = __reduce_max_sync(0xffffffffu, total);
             __syncwarp();
-            int e = 0;
-            for (int t0 = 0; t0 < maxtot; t0 += G) {
-                const int t = t0 + gl;
-                if (t < total) {
-                    while (pre[e + 1] <= t) e++;
-                    const int2 pr = pairs[eq0[e] + (t - pre[e])];
-                    fail |= !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
+            const int chunk = (total + G - 1) / G;
+            const int t0 = min(total, gl * chunk), t1 = min(total, t0 + chunk);
+            if (t0 < t1) {
+                int lo_e = 0, hi_e = E - 1;   // last e with pre[e] <= t0
+                while (lo_e < hi_e) {
+                    const int mid = (lo_e + hi_e + 1) >> 1;
+                    if (pre[mid] <= t0) lo_e = mid; else hi_e = mid - 1;
+                }
+                int e = lo_e;
+                int pe1 = pre[e + 1];
+                int64_t q = eq0[e] + (t0 - pre[e]);
+                int64_t qend = q + (pe1 - t0);
+                for (int t = t0; t < t1 && !fail; t++) {
+                    while (q == qend) {
+                        e++;
+                        const int pa = pre[e];
+                        pe1 = pre[e + 1];
+                        q = eq0[e];
+                        qend = q + (pe1 - pa);
+                    }
+                    const int2 pr = pairs[q];
+                    fail = !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
+                    q++;
                 }
             }
             const unsigned fl = __ballot_sync(0xffffffffu, fail);
@@ -143,13 +171,115 @@ __global__ void __launch_bounds__(256) k_sym_first(
     }
 }
 
+// Column-block span of row i of C from the block ranges of the rows of B it
+// reaches (bmm[k] = {first block, last block}); all lanes of the warp get it.
+__device__ __forceinline__ int sym_row_span(const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                                            const int2 *__restrict__ bmm, int64_t i, int &bmin) {
+    const int lane = threadIdx.x & 31;
+    int lo = INT_MAX, hi = -1;
+    for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += 32) {
+        const int2 m = bmm[acol[p]];
+        lo = min(lo, m.x);
+        hi = max(hi, m.y);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    bmin = lo;
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
+// Second pass for rows whose column blocks span at most BW blocks: a warp
+// per row ORs the compressed pairs into a bitmap over the span (one word
+// per block) and counts its bits; a summary bitmap (one bit per word) lists
+// the touched words so that the count and the clean-up visit only those.
+// The pairs of the row are dealt out over the lanes through prefix sums of
+// pairs(B_k), as in the first pass.  A union of compressed sets by bitwise
+// OR, with no hash map (Section 2.1).
+template <int BW, int WPB>
+struct SpanLayout {
+    static constexpr int NS = BW / 32, E = 32;
+    static constexpr int words = BW + NS + 2 * E + E + 2;   // bits, summ, eq0 (int64), pre
+};
+
+template <int BW, int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_sym_span(
+    const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
+    const int2 *__restrict__ pairs, const int2 *__restrict__ bmm, const int32_t *__restrict__ rows,
+    int64_t count, int64_t *__restrict__ crp) {
+    using Lay = SpanLayout<BW, WPB>;
+    constexpr int NS = Lay::NS, E = Lay::E;
+    extern __shared__ __align__(16) unsigned span_smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned *bits = span_smem + (size_t)w * Lay::words;
+    unsigned *summ = bits + BW;
+    long long *eq0 = (long long *)(summ + NS);
+    int *pre = (int *)(eq0 + E);
+    for (int x = lane; x < BW; x += 32) bits[x] = 0;
+    for (int x = lane; x < NS; x += 32) summ[x] = 0;
+    __syncwarp();
+    for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
+        const int i = rows[t];
+        int bmin;
+        const int nw = sym_row_span(arp, acol, bmm, i, bmin);
+        if (nw > BW) continue;
+        const int64_t p0 = arp[i];
+        const int plen = (int)(arp[i + 1] - p0);
+        for (int pb = 0; pb < plen; pb += E) {
+            int len = 0;
+            if (pb + lane < plen) {
+                const int k = acol[p0 + pb + lane];
+                len = ccnt[k];
+                eq0[lane] = brp[k];
+            }
+            int incl = len;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            pre[lane] = incl - len;
+            if (lane == 31) pre[E] = incl;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            int e = 0;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int tt = t0 + lane;
+                if (tt < total) {
+                    while (pre[e + 1] <= tt) e++;
+                    const int2 pr = pairs[eq0[e] + (tt - pre[e])];
+                    const int wd = pr.x - bmin;
+                    if (atomicOr(&bits[wd], (unsigned)pr.y) == 0) atomicOr(&summ[wd >> 5], 1u << (wd & 31));
+                }
+            }
+            __syncwarp();
+        }
+        const int ns = (nw + 31) / 32;
+        int c = 0;
+        for (int y = lane; y < ns; y += 32) {
+            unsigned sw = summ[y];
+            while (sw) {
+                const int x = y * 32 + __ffs(sw) - 1;
+                sw &= sw - 1;
+                c += __popc(bits[x]);
+                bits[x] = 0;
+            }
+            summ[y] = 0;
+        }
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (lane == 0) crp[i + 1] = c;
+        __syncwarp();
+    }
+}
+
 // A warp per row from a row list, S-slot map, lanes walk the pairs of B_k.
 template <int S>
 __global__ void __launch_bounds__(256) k_sym_warp(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
-    int64_t *__restrict__ crp, int *err) {
+    int64_t *__restrict__ crp, int *err, const int2 *__restrict__ bmm, int skip_span) {
     constexpr int L = __builtin_ctz(S), WPB = 8;
     extern __shared__ int smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -158,6 +288,10 @@ __global__ void __launch_bounds__(256) k_sym_warp(
     bool fail = false;
     for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
+        if (skip_span > 0) {
+            int bmin;
+            if (sym_row_span(arp, acol, bmm, i, bmin) <= skip_span) continue;
+        }
         for (int s = lane; s < S; s += 32) {
             keys[s] = -1;
             masks[s] = 0;
@@ -190,16 +324,28 @@ __global__ void __launch_bounds__(BS) k_sym_block(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
-    int64_t *__restrict__ crp, int *err) {
+    int64_t *__restrict__ crp, int *err, const int2 *__restrict__ bmm, int skip_span) {
     constexpr int L = __builtin_ctz(S);
     extern __shared__ int smem[];
     __shared__ int red[BS / 32];
+    __shared__ int span_s;
     int *keys = smem;
     unsigned *masks = (unsigned *)(smem + S);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     bool fail = false;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
         const int i = rows[t];
+        if (skip_span > 0) {
+            if (w == 0) {
+                int bmin;
+                const int sp = sym_row_span(arp, acol, bmm, i, bmin);
+                if (lane == 0) span_s = sp;
+            }
+            __syncthreads();
+            const int sp = span_s;
+            __syncthreads();
+            if (sp <= skip_span) continue;
+        }
         for (int s = threadIdx.x; s < S; s += BS) {
             keys[s] = -1;
             masks[s] = 0;
@@ -320,14 +466,15 @@ static const char *SYM_LABEL[NBINS] = {"", "", "symbolic.bin2", "symbolic.bin3",
 
 template <int S>
 static int run_warp(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt, const int2 *pairs,
-                    const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c) {
+                    const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c,
+                    const int2 *bmm, int skip_span) {
     size_t smem = (size_t)8 * S * 8;
     SG_TRY(prep(k_sym_warp<S>, smem));
     int64_t blocks = (count + 7) / 8;
     blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
     c.begin(SYM_LABEL[b], count);
     k_sym_warp<S><<<(unsigned)blocks, 256, smem, c.s>>>(A.row_ptr, A.col_idx, brp, ccnt, pairs, rows,
-                                                         count, crp, err);
+                                                         count, crp, err, bmm, skip_span);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -335,21 +482,26 @@ static int run_warp(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt
 
 template <int BS, int S>
 static int run_block(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt, const int2 *pairs,
-                     const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c) {
+                     const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c,
+                     const int2 *bmm, int skip_span) {
     size_t smem = (size_t)S * 8;
     SG_TRY(prep(k_sym_block<BS, S>, smem));
     int64_t blocks = count < (int64_t)c.nsm * 16 ? count : (int64_t)c.nsm * 16;
     c.begin(SYM_LABEL[b], count);
     k_sym_block<BS, S><<<(unsigned)blocks, BS, smem, c.s>>>(A.row_ptr, A.col_idx, brp, ccnt, pairs,
-                                                            rows, count, crp, err);
+                                                            rows, count, crp, err, bmm, skip_span);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
 }
 
+static const char *SPAN_LABEL[NBINS] = {"", "", "symbolic.span2", "symbolic.span3",
+                                        "symbolic.span4", "symbolic.span5", "", ""};
+constexpr int SPAN_BW = 2048;
+
 int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
                     const int32_t *ccnt, const int32_t *rows, const long long *counts,
-                    int64_t *crp, int *err, void *gws, size_t gws_bytes, Ctx &c) {
+                    int64_t *crp, int *err, void *gws, size_t gws_bytes, const int2 *bmm, Ctx &c) {
     const int nsm = c.nsm;
     int64_t off = 0;
     const int64_t *brp = B.row_ptr;
@@ -358,11 +510,24 @@ int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
         const int32_t *r = rows + off;
         off += cnt;
         if (cnt == 0) continue;
+        if (b <= 5) {
+            // rows spanning at most SPAN_BW column blocks: bitmap over the span
+            constexpr int WPB = 8;
+            const size_t smem = (size_t)WPB * SpanLayout<SPAN_BW, WPB>::words * 4;
+            SG_TRY(prep(k_sym_span<SPAN_BW, WPB>, smem));
+            int64_t blocks = (cnt + WPB - 1) / WPB;
+            blocks = blocks < (int64_t)nsm * 32 ? blocks : (int64_t)nsm * 32;
+            c.begin(SPAN_LABEL[b], cnt);
+            k_sym_span<SPAN_BW, WPB><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(
+                A.row_ptr, A.col_idx, brp, ccnt, pairs, bmm, r, cnt, crp);
+            c.end();
+            SG_CUDA(cudaGetLastError());
+        }
         switch (b) {
-            case 2: SG_TRY((run_warp<128>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
-            case 3: SG_TRY((run_warp<512>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
-            case 4: SG_TRY((run_block<128, 2048>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
-            case 5: SG_TRY((run_block<256, 8192>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c))); break;
+            case 2: SG_TRY((run_warp<128>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
+            case 3: SG_TRY((run_warp<512>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
+            case 4: SG_TRY((run_block<128, 2048>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
+            case 5: SG_TRY((run_block<256, 8192>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
             default: {
                 int64_t nwords = (B.ncols + 31) / 32;
                 bool shared = nwords <= SMEM_BITMAP_WORDS;

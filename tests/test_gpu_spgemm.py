@@ -217,6 +217,19 @@ def test_medium_rows_every_span(h, ncols, small_cap):
     assert any(l.startswith(want) for l in labels), labels
 
 
+def test_window_long_and_short_b_rows(h):
+    """Rows with more than 4096 outputs over sorted B whose rows are short
+    (walked by one thread per a_ik, a few entries per window) or long (more
+    than 256 entries, walked by whole warps), in FP32 and FP64."""
+    a = _strided_rows(40, 3000, [60, 97, 130], 13, 29, 71)
+    b = _strided_rows(3000, 200000, [3, 20, 400, 3000, 17], 101, 61, 72)
+    for dt, tag in ((np.float64, "f64"), (np.float32, "f32")):
+        c = run(h, a, b, dt)
+        assert_matches(c, oracle_product(a, b, dt), tag)
+    sym, num = h.bin_counts()
+    assert num[6] > 0, num
+
+
 def test_heavy_rows_random(h):
     """Rows whose products overlap heavily (many insertions per key)."""
     a = _spread_rows([5, 50, 500, 5000], 6000, 7)
