@@ -81,6 +81,8 @@ struct spgemm_handle_s {
     size_t arena_cap = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev[8] = {};
+    std::vector<int64_t> zeros;   // offsets of an empty C (chunked symbolic plan)
+    int *host_mm = nullptr;       // pinned, column ranges of A parts (chunked numeric)
     ChunkStats cstats;
     float chunk_ms = 0;
     // batched calls: stacked operands and the instance table
@@ -213,6 +215,7 @@ int spgemm_destroy(spgemm_handle h) {
         if (e) cudaEventDestroy(e);
     if (h->s_in) cudaStreamDestroy(h->s_in);
     if (h->s_out) cudaStreamDestroy(h->s_out);
+    if (h->host_mm) cudaFreeHost(h->host_mm);
     if (h->dstate) cudaFree(h->dstate);
     if (h->hstate) cudaFreeHost(h->hstate);
     delete h;
@@ -391,6 +394,7 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
         SG_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
         SG_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
         for (auto &e : h->ev) SG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        SG_CUDA(cudaMallocHost(&h->host_mm, 4 * sizeof(int)));
     }
     if (h->arena_cap != budget) {
         if (h->arena) {
@@ -417,6 +421,8 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
     env.s_out = h->s_out;
     for (int k = 0; k < 8; k++) env.ev[k] = h->ev[k];
     env.err = &h->dstate->err;
+    env.zeros = &h->zeros;
+    env.host_mm = h->host_mm;
     return SPGEMM_OK;
 }
 
@@ -426,21 +432,13 @@ int spgemm_chunked_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_c
     SG_TRY(check_csr(A, "A", false));
     SG_TRY(check_csr(B, "B", false));
     if (A->ncols != B->nrows) { set_error("dimension mismatch"); return SPGEMM_ERR_DIM; }
-    for (int64_t k = 0; k < A->nnz; k++)
-        if (A->col_idx[k] < 0 || A->col_idx[k] >= B->nrows) {
-            set_error("column %lld of A out of range", (long long)k);
-            return SPGEMM_ERR_INDEX;
-        }
-    for (int64_t k = 0; k < B->nnz; k++)
-        if (B->col_idx[k] < 0 || B->col_idx[k] >= B->ncols) {
-            set_error("column %lld of B out of range", (long long)k);
-            return SPGEMM_ERR_INDEX;
-        }
+    // column ranges are checked on the device as the parts arrive
     cudaStream_t s = (cudaStream_t)stream;
     SG_CUDA(cudaSetDevice(h->device));
     Ctx c = h->ctx(s);
     ChunkEnv env;
     SG_TRY(chunk_env(h, fast_mem_budget, s, env, c));
+    SG_CUDA(cudaMemsetAsync(h->dstate, 0, sizeof(DevState), s));
     h->cstats = ChunkStats();
     SG_TRY(chunked_symbolic(env, *A, *B, C_row_ptr, nnz_C, fast_mem_budget, h->cstats));
     SG_CUDA(cudaStreamSynchronize(s));

@@ -26,7 +26,7 @@ __device__ __forceinline__ int64_t find_col(const int32_t *__restrict__ col, int
 // G lanes per row of A: for each stored a_ik in turn the lanes walk B_k,
 // each looks up dC_ij, and the group reduces the dA term.
 template <typename V, int G>
-__global__ void __launch_bounds__(256) k_backward(
+__global__ void __launch_bounds__(256, 4) k_backward(
     int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const V *__restrict__ aval, const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol,
     const V *__restrict__ bval, const int64_t *__restrict__ crp, const int32_t *__restrict__ ccol,

@@ -52,6 +52,11 @@ __global__ void k_col_range(const int32_t *__restrict__ col, int64_t nnz, int *m
     }
 }
 
+__global__ void k_init_range(int *mm) {
+    mm[0] = INT_MAX;
+    mm[1] = -1;
+}
+
 template <typename V>
 __device__ __forceinline__ bool fma_insert(int *keys, V *vals, int L, int col, V v) {
     const unsigned msk = (1u << L) - 1;
@@ -118,6 +123,14 @@ __global__ void __launch_bounds__(256) k_fma_warp(
         const int64_t c0 = crp[i];
         const int cap = (int)(crp[i + 1] - c0);
         if (cap == 0 || cap > FMA_WARP_CAP) continue;
+        {   // rows with no stored a_ik in this B part keep their partial row as it is
+            bool any = false;
+            for (int64_t p = arp[i] + lane; p < arp[i + 1] && !any; p += 32) {
+                const int64_t k = acol[p];
+                any = k >= lo && k < hi;
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+        }
         int S = 32;
         while (S < 2 * cap) S <<= 1;
         const int L = __ffs(S) - 1;
@@ -202,6 +215,20 @@ __global__ void __launch_bounds__(256, 1) k_fma_block(
         const int64_t c0 = crp[i];
         const int64_t cap = crp[i + 1] - c0;
         if (cap <= FMA_WARP_CAP) continue;
+        {   // rows with no stored a_ik in this B part keep their partial row as it is
+            if (threadIdx.x == 0) nsh = 0;
+            __syncthreads();
+            bool any = false;
+            for (int64_t p = arp[i] + threadIdx.x; p < arp[i + 1] && !any; p += 256) {
+                const int64_t k = acol[p];
+                any = k >= lo && k < hi;
+            }
+            if (any) nsh = 1;
+            __syncthreads();
+            const bool skip = nsh == 0;
+            __syncthreads();
+            if (skip) continue;
+        }
         int L = 1;
         while ((1LL << L) < 2 * cap) L++;
         const int64_t S = 1LL << L;
@@ -271,7 +298,7 @@ constexpr int CNT_S = 2048, CNT_WPB = 8;
 __global__ void __launch_bounds__(256) k_count_warp(
     int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, int64_t *__restrict__ cnt,
-    int *overflow) {
+    int *overflow, int64_t nrows_b, int *err) {
     extern __shared__ int skeys[];
     __shared__ int scount[CNT_WPB];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -286,6 +313,10 @@ __global__ void __launch_bounds__(256) k_count_warp(
         const int64_t pe = arp[i + 1];
         for (int64_t p = arp[i]; p < pe && !full; p++) {
             const int k = acol[p];
+            if (k < 0 || (int64_t)k >= nrows_b) {
+                if (lane == 0) atomicOr(err, DERR_COL_RANGE);
+                continue;
+            }
             const int64_t q1 = brp[k + 1];
             for (int64_t q = brp[k] + lane; q < q1; q += 32) {
                 const int col = bcol[q];
@@ -321,8 +352,9 @@ __global__ void __launch_bounds__(256) k_count_warp(
 __global__ void __launch_bounds__(256) k_count_bitmap(
     int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ bcol, int64_t *__restrict__ cnt,
-    int64_t nwords, unsigned *gbits) {
+    int64_t nwords, unsigned *gbits, const int *overflow, int64_t nrows_b) {
     __shared__ long long red[8];
+    if (*(volatile const int *)overflow == 0) return;   // no row overflowed the warp sets
     unsigned *bits = gbits + (size_t)blockIdx.x * (size_t)nwords;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
@@ -332,6 +364,7 @@ __global__ void __launch_bounds__(256) k_count_bitmap(
         const int64_t pe = arp[i + 1];
         for (int64_t p = arp[i] + w; p < pe; p += 8) {
             const int k = acol[p];
+            if (k < 0 || (int64_t)k >= nrows_b) continue;   // flagged by k_count_warp
             for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
                 const int col = bcol[q];
                 atomicOr(&bits[col >> 5], 1u << (col & 31));
@@ -349,6 +382,24 @@ __global__ void __launch_bounds__(256) k_count_bitmap(
             cnt[i] = t;
         }
         __syncthreads();
+    }
+}
+
+// Column indices of a resident pattern must lie in [0, ncols).
+__global__ void k_check_cols(const int32_t *__restrict__ col, int64_t nnz, int64_t ncols, int *err) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= col[i] < 0 || (int64_t)col[i] >= ncols;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DERR_COL_RANGE);
+}
+
+// x[0..n] += *cin (the offset where this part of C starts); *cout = x[n].
+__global__ void k_add_carry(int64_t *x, int64_t n, const int64_t *cin, int64_t *cout) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) {
+        const int64_t v = x[i] + *cin;
+        x[i] = v;
+        if (i == n) *cout = v;
     }
 }
 
@@ -487,11 +538,34 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
         return (mr + 1) * 8 + mb * (int64_t)(4 + vb);
     };
     {
+        // Both operands are double buffered in Algorithm 2 (the next A/C part
+        // comes in while the current one is multiplied and the previous one
+        // goes out), the streamed A/C parts in Algorithm 3.  Parts that do
+        // not fit twice are cut again with BinarySearch (finer parts, same
+        // algorithm).  B parts are also cut to at most an eighth of an A/C
+        // part so that skipping the parts an A part does not reach is fine
+        // grained.
         const bool alg2 = p.algorithm == 2;
-        const int64_t outer = alg2 ? buf_ac(p.ac_cuts) : buf_b(p.b_cuts);
+        std::vector<int64_t> &outer_cuts = alg2 ? p.ac_cuts : p.b_cuts;
         std::vector<int64_t> &inner_cuts = alg2 ? p.b_cuts : p.ac_cuts;
+        auto outer_sz = [&]() { return alg2 ? buf_ac(outer_cuts) : buf_b(outer_cuts); };
+        auto inner_sz = [&]() { return alg2 ? buf_b(inner_cuts) : buf_ac(inner_cuts); };
+        const int nouter = alg2 ? 2 : 1;
+        double olimit = (double)avail * 0.30;
+        for (int iter = 0; alg2 && outer_sz() * nouter > (int64_t)((double)avail * 0.62); iter++) {
+            const bool ok = iter < 40 && cut_rows(A.row_ptr, C.row_ptr, A.nrows, vb, olimit, outer_cuts);
+            if (!ok) {
+                set_error("chunked: budget %zu too small for the outer parts", budget);
+                return SPGEMM_ERR_BUDGET;
+            }
+            olimit *= 0.85;
+        }
+        const int64_t outer = outer_sz() * nouter;
         double limit = (double)(avail - outer) / 2.0;
-        for (int iter = 0; (alg2 ? buf_b(inner_cuts) : buf_ac(inner_cuts)) * 2 + outer > avail; iter++) {
+        if (alg2) limit = std::min(limit, (double)outer / nouter / 8.0);
+        bool first = alg2;   // Algorithm 2: always cut B to the fine size
+        for (int iter = 0; first || inner_sz() * 2 + outer > avail; iter++) {
+            first = false;
             bool cut_ok = limit > 0 && iter < 40 &&
                           (alg2 ? cut_rows(B.row_ptr, nullptr, B.nrows, vb, limit, inner_cuts)
                                 : cut_rows(A.row_ptr, C.row_ptr, A.nrows, vb, limit, inner_cuts));
@@ -511,7 +585,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     // carve the arena
     Arena ar{(char *)env.arena, budget, 0};
     void *gws = gws_bytes ? ar.take(gws_bytes) : nullptr;
-    int *mm = (int *)ar.take(16);
+    int *mm = (int *)ar.take(4 * sizeof(int));
     int64_t max_ac_rows = 0, max_ac_a = 0, max_ac_c = 0, max_b_rows = 0, max_b_nnz = 0;
     for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
         const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1];
@@ -523,7 +597,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
         max_b_rows = std::max(max_b_rows, p.b_cuts[t + 1] - p.b_cuts[t]);
         max_b_nnz = std::max(max_b_nnz, B.row_ptr[p.b_cuts[t + 1]] - B.row_ptr[p.b_cuts[t]]);
     }
-    const int nbuf_ac = p.algorithm == 2 ? 1 : 2, nbuf_b = p.algorithm == 2 ? 2 : 1;
+    const int nbuf_ac = 2, nbuf_b = p.algorithm == 2 ? 2 : 1;
     PartBuf Ab[2], Cb[2], Bb[2];
     bool ok = mm != nullptr;
     for (int u = 0; u < nbuf_ac && ok; u++)
@@ -545,68 +619,83 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                    : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c);
     };
     if (p.algorithm == 2) {
-        for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+        // ev: [0..1] B part in, [2..3] B part used, [4..5] C part out,
+        //     [6..7] A/C part in (by slot); column ranges come back through
+        //     pinned host memory, read once the part's copy has landed
+        const size_t nac = p.ac_cuts.size() - 1;
+        int *hmm = env.host_mm;
+        size_t bcount = 0;
+        auto stage_ac = [&](size_t j) -> int {
+            const int slot = (int)(j & 1);
             const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
             const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
-            // the previous part's products must be done and its C part must have
-            // left the device before the buffers are reused
-            if (j > 0) {
-                SG_CUDA(cudaStreamWaitEvent(si, ev[6], 0));
-                SG_CUDA(cudaStreamWaitEvent(si, ev[4], 0));
-            }
-            stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[0].rp, Ab[0].col, Ab[0].val, si, &st);
+            // the part that used these buffers two steps ago has left the device
+            if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[4 + slot], 0));
+            stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st);
             SG_TRY(st);
             // C starts empty: only its offsets come in
-            SG_CUDA(cudaMemcpyAsync(Cb[0].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
+            SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
             stats.h2d += (rows + 1) * 8;
             if (rows > 0)
-                k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, si>>>(Cb[0].rp, rows + 1, C.row_ptr[r0]);
+                k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, si>>>(Cb[slot].rp, rows + 1, C.row_ptr[r0]);
             if (cn > 0) {
-                SG_CUDA(cudaMemsetAsync(Cb[0].col, 0xff, (size_t)cn * 4, si));
-                SG_CUDA(cudaMemsetAsync(Cb[0].val, 0, (size_t)cn * vb, si));
+                SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, si));
+                SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, si));
             }
             // column range of the A part decides which B parts it needs
-            const int init[2] = {INT_MAX, -1};
-            SG_CUDA(cudaMemcpyAsync(mm, init, 8, cudaMemcpyHostToDevice, si));
             const int64_t an = A.row_ptr[r1] - A.row_ptr[r0];
+            int *dmm = mm + 2 * slot;
+            k_init_range<<<1, 1, 0, si>>>(dmm);
             if (an > 0)
-                k_col_range<<<(unsigned)std::min<int64_t>((an + 255) / 256, (int64_t)c.nsm * 8), 256, 0, si>>>(Ab[0].col, an, mm);
-            int hmm[2];
-            SG_CUDA(cudaMemcpyAsync(hmm, mm, 8, cudaMemcpyDeviceToHost, si));
-            SG_CUDA(cudaStreamSynchronize(si));
+                k_col_range<<<(unsigned)std::min<int64_t>((an + 255) / 256, (int64_t)c.nsm * 8), 256, 0, si>>>(
+                    Ab[slot].col, an, dmm);
+            SG_CUDA(cudaMemcpyAsync(hmm + 2 * slot, dmm, 8, cudaMemcpyDeviceToHost, si));
+            SG_CUDA(cudaEventRecord(ev[6 + slot], si));
+            return SPGEMM_OK;
+        };
+        if (nac > 0) SG_TRY(stage_ac(0));
+        for (size_t j = 0; j < nac; j++) {
+            const int slot = (int)(j & 1);
+            const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
+            const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
+            // the host waits for this part's column range only; the device
+            // still has the previous part's products queued
+            SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
+            const int lo_c = hmm[2 * slot], hi_c = hmm[2 * slot + 1];
             std::vector<size_t> need;
             for (size_t t = 0; t + 1 < p.b_cuts.size(); t++)
-                if (hmm[1] >= 0 && p.b_cuts[t] <= hmm[1] && p.b_cuts[t + 1] > hmm[0]) need.push_back(t);
+                if (hi_c >= 0 && p.b_cuts[t] <= hi_c && p.b_cuts[t + 1] > lo_c) need.push_back(t);
             stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
+            SG_CUDA(cudaStreamWaitEvent(s, ev[6 + slot], 0));
             // stream the needed B parts, double buffered
-            for (size_t u = 0; u < need.size(); u++) {
-                const int slot = (int)(u & 1);
+            for (size_t u = 0; u < need.size(); u++, bcount++) {
+                const int bs = (int)(bcount & 1);
                 const size_t t = need[u];
-                if (u >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[2 + slot], 0));
-                stats.h2d += copy_rows_in(B, p.b_cuts[t], p.b_cuts[t + 1], vb, Bb[slot].rp, Bb[slot].col,
-                                          Bb[slot].val, si, &st);
+                if (bcount >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[2 + bs], 0));
+                stats.h2d += copy_rows_in(B, p.b_cuts[t], p.b_cuts[t + 1], vb, Bb[bs].rp, Bb[bs].col,
+                                          Bb[bs].val, si, &st);
                 SG_TRY(st);
-                SG_CUDA(cudaEventRecord(ev[slot], si));
-                SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
-                SG_TRY(fma(Ab[0], rows, p.b_cuts[t], p.b_cuts[t + 1], Bb[slot], Cb[0]));
-                SG_CUDA(cudaEventRecord(ev[2 + slot], s));
+                SG_CUDA(cudaEventRecord(ev[bs], si));
+                SG_CUDA(cudaStreamWaitEvent(s, ev[bs], 0));
+                SG_TRY(fma(Ab[slot], rows, p.b_cuts[t], p.b_cuts[t + 1], Bb[bs], Cb[slot]));
+                SG_CUDA(cudaEventRecord(ev[2 + bs], s));
             }
-            // finished part of C back to host memory (after its offsets and
-            // initial state, copied on si, and every product, on s)
-            SG_CUDA(cudaEventRecord(ev[7], si));
-            SG_CUDA(cudaEventRecord(ev[6], s));
-            SG_CUDA(cudaStreamWaitEvent(so, ev[6], 0));
-            SG_CUDA(cudaStreamWaitEvent(so, ev[7], 0));
+            // the next A/C part comes in behind this part's B parts
+            if (j + 1 < nac) SG_TRY(stage_ac(j + 1));
+            // finished part of C back to host memory
+            SG_CUDA(cudaEventRecord(ev[4 + slot], s));
+            SG_CUDA(cudaStreamWaitEvent(so, ev[4 + slot], 0));
             if (cn > 0) {
                 const int64_t p0 = C.row_ptr[r0];
-                SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[0].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
-                SG_CUDA(cudaMemcpyAsync((char *)C.values + (size_t)p0 * vb, Cb[0].val, (size_t)cn * vb,
+                SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[slot].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
+                SG_CUDA(cudaMemcpyAsync((char *)C.values + (size_t)p0 * vb, Cb[slot].val, (size_t)cn * vb,
                                         cudaMemcpyDeviceToHost, so));
                 stats.d2h += cn * (4 + vb);
             }
-            SG_CUDA(cudaEventRecord(ev[4], so));
-            SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
+            SG_CUDA(cudaEventRecord(ev[4 + slot], so));
         }
+        SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
+        SG_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
     } else {
         for (size_t t = 0; t + 1 < p.b_cuts.size(); t++) {
             const int64_t b0 = p.b_cuts[t], b1 = p.b_cuts[t + 1];
@@ -662,13 +751,15 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
 int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, int64_t *C_row_ptr,
                      int64_t *nnz_C, size_t budget, ChunkStats &stats) {
     Ctx &c = *env.ctx;
-    const cudaStream_t s = c.s, si = env.s_in;
+    const cudaStream_t s = c.s, si = env.s_in, so = env.s_out;
+    cudaEvent_t *ev = env.ev;   // [0..1] A part in, [2..3] counted, [4..5] offsets out, [6] B in
     const int64_t nwords = (B.ncols + 31) / 32;
     // pattern-only sizes; C contributes its offsets only
-    std::vector<int64_t> zeros((size_t)A.nrows + 1, 0);
+    std::vector<int64_t> &zeros = *env.zeros;
+    if ((int64_t)zeros.size() < A.nrows + 1) zeros.assign((size_t)A.nrows + 1, 0);
     ChunkPlan p;
     const size_t bitmap = r256((size_t)c.nsm * (size_t)nwords * 4);
-    const size_t reserve = bitmap + 4096;
+    const size_t reserve = bitmap + 8192;
     if (budget <= reserve) {
         set_error("chunked symbolic: budget %zu below the fixed working set %zu", budget, reserve);
         return SPGEMM_ERR_BUDGET;
@@ -680,7 +771,8 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
                   (long long)p.size_b);
         return SPGEMM_ERR_BUDGET;
     }
-    // A parts are double buffered: shrink them until B + 2 parts fit
+    // A parts are double buffered (with their counts and the scan's scratch):
+    // shrink them until B + 2 parts fit
     int64_t max_rows = 0, max_nnz = 0;
     for (int iter = 0; iter < 16; iter++) {
         max_rows = max_nnz = 0;
@@ -690,7 +782,8 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
         }
         const size_t need = r256((size_t)(B.nrows + 1) * 8) + r256((size_t)std::max<int64_t>(B.nnz, 1) * 4) +
                             2 * (r256((size_t)(max_rows + 1) * 8) + r256((size_t)std::max<int64_t>(max_nnz, 1) * 4) +
-                                 r256((size_t)max_rows * 8)) + reserve + 1024;
+                                 r256((size_t)(max_rows + 1) * 8) + r256(scan_tmp_bytes(max_rows))) +
+                            reserve + 4096;
         if (need <= budget) break;
         fast = fast * 3 / 4;
         SG_TRY(plan_chunks(A.row_ptr, A.nrows, zeros.data(), B.row_ptr, B.nrows, 0, 0, fast, p));
@@ -705,14 +798,17 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     stats.n_b = 1;
     Arena ar{(char *)env.arena, budget, 0};
     unsigned *bits = (unsigned *)ar.take(bitmap);
-    int *ovf = (int *)ar.take(16);
+    int *ovf = (int *)ar.take(2 * sizeof(int));
+    int64_t *carry = (int64_t *)ar.take(3 * sizeof(int64_t));   // two running offsets + scan total
     PartBuf Bp, Ap[2];
-    int64_t *cnt[2];
-    bool ok = bits && ovf && take_part(ar, Bp, B.nrows, B.nnz, 0);
+    int64_t *cnt[2] = {nullptr, nullptr};
+    void *tmp[2] = {nullptr, nullptr};
+    bool ok = bits && ovf && carry && take_part(ar, Bp, B.nrows, B.nnz, 0);
     for (int u = 0; u < 2 && ok; u++) {
         ok = take_part(ar, Ap[u], max_rows, max_nnz, 0);
-        cnt[u] = (int64_t *)ar.take((size_t)std::max<int64_t>(max_rows, 1) * 8);
-        ok = ok && cnt[u];
+        cnt[u] = (int64_t *)ar.take((size_t)(max_rows + 1) * 8);
+        tmp[u] = ar.take(scan_tmp_bytes(max_rows));
+        ok = ok && cnt[u] && tmp[u];
     }
     if (!ok) {
         set_error("chunked symbolic: parts do not fit the %zu-byte budget", budget);
@@ -720,51 +816,57 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     }
     stats.device_bytes = (int64_t)ar.used;
     int st = SPGEMM_OK;
+    // the pattern of B once, checked on the device
     stats.h2d += copy_rows_in(B, 0, B.nrows, 0, Bp.rp, Bp.col, nullptr, si, &st);
     SG_TRY(st);
-    SG_CUDA(cudaEventRecord(env.ev[6], si));
-    SG_CUDA(cudaStreamWaitEvent(s, env.ev[6], 0));
-    std::vector<int64_t> hcnt((size_t)std::max<int64_t>(max_rows, 1));
-    int64_t carry = 0;
+    if (B.nnz > 0)
+        k_check_cols<<<(unsigned)std::min<int64_t>((B.nnz + 255) / 256, (int64_t)c.nsm * 8), 256, 0, si>>>(
+            Bp.col, B.nnz, B.ncols, env.err);
+    SG_CUDA(cudaEventRecord(ev[6], si));
+    SG_CUDA(cudaStreamWaitEvent(s, ev[6], 0));
+    SG_CUDA(cudaMemsetAsync(carry, 0, 3 * sizeof(int64_t), s));
     C_row_ptr[0] = 0;
     const size_t smem = (size_t)CNT_WPB * CNT_S * 4;
     SG_CUDA(cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
+    const size_t nparts = p.ac_cuts.size() - 1;
+    // Part j: A rows in on s_in; counts, scan and running offset on s; the
+    // offsets out to C_row_ptr on s_out.  No host synchronisation inside.
+    for (size_t j = 0; j < nparts; j++) {
         const int slot = (int)(j & 1);
         const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
-        if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, env.ev[2 + slot], 0));
+        if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[4 + slot], 0));   // buffers free again
         stats.h2d += copy_rows_in(A, r0, r1, 0, Ap[slot].rp, Ap[slot].col, nullptr, si, &st);
         SG_TRY(st);
-        SG_CUDA(cudaEventRecord(env.ev[slot], si));
-        SG_CUDA(cudaStreamWaitEvent(s, env.ev[slot], 0));
-        if (rows == 0) continue;
-        SG_CUDA(cudaMemsetAsync(ovf, 0, 4, s));
-        const int64_t blocks = std::min<int64_t>((rows + CNT_WPB - 1) / CNT_WPB, (int64_t)c.nsm * 16);
-        c.begin("chunked.count", rows);
-        k_count_warp<<<(unsigned)blocks, 256, smem, s>>>(rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col,
-                                                         cnt[slot], ovf);
-        c.end();
-        SG_CUDA(cudaGetLastError());
-        int hovf = 0;
-        SG_CUDA(cudaMemcpyAsync(&hovf, ovf, 4, cudaMemcpyDeviceToHost, s));
-        SG_CUDA(cudaStreamSynchronize(s));
-        if (hovf > 0) {
-            c.begin("chunked.count_bitmap", rows);
-            k_count_bitmap<<<(unsigned)std::min<int64_t>(rows, (int64_t)c.nsm), 256, 0, s>>>(
-                rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col, cnt[slot], nwords, bits);
+        SG_CUDA(cudaEventRecord(ev[slot], si));
+        SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
+        int64_t *x = cnt[slot];
+        SG_CUDA(cudaMemsetAsync(x, 0, 8, s));
+        if (rows > 0) {
+            SG_CUDA(cudaMemsetAsync(&ovf[slot], 0, 4, s));
+            const int64_t blocks = std::min<int64_t>((rows + CNT_WPB - 1) / CNT_WPB, (int64_t)c.nsm * 16);
+            c.begin("chunked.count", rows);
+            k_count_warp<<<(unsigned)blocks, 256, smem, s>>>(rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col,
+                                                             x + 1, &ovf[slot], B.nrows, env.err);
             c.end();
             SG_CUDA(cudaGetLastError());
+            k_count_bitmap<<<(unsigned)std::min<int64_t>(rows, (int64_t)c.nsm), 256, 0, s>>>(
+                rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col, x + 1, nwords, bits, &ovf[slot], B.nrows);
+            SG_CUDA(cudaGetLastError());
+            SG_TRY(launch_scan_counts(x, rows, (long long *)&carry[2], tmp[slot], c));
         }
-        SG_CUDA(cudaMemcpyAsync(hcnt.data(), cnt[slot], (size_t)rows * 8, cudaMemcpyDeviceToHost, s));
-        SG_CUDA(cudaEventRecord(env.ev[2 + slot], s));
-        SG_CUDA(cudaStreamSynchronize(s));
+        k_add_carry<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(x, rows, &carry[j & 1],
+                                                                       &carry[(j + 1) & 1]);
+        SG_CUDA(cudaGetLastError());
+        SG_CUDA(cudaEventRecord(ev[2 + slot], s));
+        SG_CUDA(cudaStreamWaitEvent(so, ev[2 + slot], 0));
+        if (rows > 0)
+            SG_CUDA(cudaMemcpyAsync(C_row_ptr + r0 + 1, x + 1, (size_t)rows * 8, cudaMemcpyDeviceToHost, so));
         stats.d2h += rows * 8;
-        for (int64_t r = 0; r < rows; r++) {
-            carry += hcnt[(size_t)r];
-            C_row_ptr[r0 + r + 1] = carry;
-        }
+        SG_CUDA(cudaEventRecord(ev[4 + slot], so));
     }
-    *nnz_C = carry;
+    SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
+    SG_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
+    SG_CUDA(cudaMemcpyAsync(nnz_C, &carry[nparts & 1], 8, cudaMemcpyDeviceToHost, s));
     return SPGEMM_OK;
 }
 

@@ -215,6 +215,8 @@ struct ChunkEnv {
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev[8] = {};
     int *err = nullptr;
+    std::vector<int64_t> *zeros = nullptr;   // host scratch: offsets of an empty C
+    int *host_mm = nullptr;                  // pinned: column ranges of two A parts
 };
 struct ChunkStats {
     int algorithm = 0, branch = 0;

@@ -41,10 +41,36 @@ def bound_a(a, b, ref, dc):
     return ba
 
 
+def _wide_case():
+    """Rows of C spanning more than 2048 blocks of 32 columns (binary-search
+    path) next to narrow rows (shared-memory map path)."""
+    nb, ncols, per = 1500, 150000, 12
+    k = np.repeat(np.arange(nb), per)
+    t = np.tile(np.arange(per), nb)
+    wide = (k * 7919 + t * (ncols // per + 3)) % ncols       # rows of B spread over all columns
+    narrow = (k * 37 + t * 5) % 2000                          # rows of B within 2000 columns
+    cols = np.where(k < nb // 2, wide, narrow)
+    key = np.unique(k * ncols + cols)
+    rp = np.zeros(nb + 1, dtype=np.int64)
+    np.cumsum(np.bincount(key // ncols, minlength=nb), out=rp[1:])
+    b = I.Csr(nb, ncols, rp, (key % ncols).astype(np.int32),
+              I.uniform01(np.arange(len(key), dtype=np.uint64), 17) - 0.5)
+    d = I.random_csr(200, nb, 0.01, 16).to_dense() != 0
+    d[:100, : nb // 2] = False          # rows 0..99 reach only the narrow rows of B
+    d[np.arange(200), nb // 2 + np.arange(200)] = True
+    r, cidx = np.nonzero(d)
+    arp = np.zeros(201, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=200), out=arp[1:])
+    a = I.Csr(200, nb, arp, cidx.astype(np.int32), I.uniform01(np.arange(len(cidx), dtype=np.uint64), 18) - 0.5)
+    return a, b
+
+
 @pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 1e-5)])
-@pytest.mark.parametrize("case", ["random", "batch_like", "galerkin"])
+@pytest.mark.parametrize("case", ["random", "batch_like", "galerkin", "wide"])
 def test_backward_matches_oracle(h, dtype, tol, case):
-    if case == "random":
+    if case == "wide":
+        a, b = _wide_case()
+    elif case == "random":
         a = I.random_csr(300, 200, 0.04, 11, shuffle_cols=True)
         b = I.random_csr(200, 250, 0.05, 12, shuffle_cols=True)
     elif case == "batch_like":

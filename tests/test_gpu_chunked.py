@@ -121,8 +121,18 @@ def test_chunked_alg3_b_larger(h):
 
 def test_chunked_alg2_bytes_match_formula(h):
     """Algorithm 2 with every B part needed: bytes = size(A) + size(C) +
-    size(B)|P_AC| (the paper's copy cost) plus 8 bytes per extra boundary."""
-    a = I.random_csr(1500, 400, 0.05, 91)
+    size(B)|P_AC| (the paper's copy cost, on the parts the driver ran: it
+    cuts A/C parts again to double buffer them and B parts finer to skip
+    them precisely) plus 8 bytes per extra part boundary."""
+    a0 = I.random_csr(1500, 400, 0.05, 91)
+    # every row reaches the first and the last row of B, so no B part is skipped
+    d = a0.to_dense() != 0
+    d[:, 0] = d[:, -1] = True
+    rows, cols = np.nonzero(d)
+    rp = np.zeros(a0.nrows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=a0.nrows), out=rp[1:])
+    a = I.Csr(a0.nrows, a0.ncols, rp, cols.astype(np.int32),
+              I.uniform01(np.arange(len(cols), dtype=np.uint64), 93) - 0.5)
     b = I.random_csr(400, 600, 0.04, 92)
     ref = oracle.spgemm(a, b)
     budget, plan = find_budget(a.row_ptr, ref.row_ptr, b.row_ptr, 8, 2, 2, 2)
@@ -130,8 +140,11 @@ def test_chunked_alg2_bytes_match_formula(h):
     ref, st = run_chunked(h, a, b, budget)
     assert st["algorithm"] == 2 and st["skipped_b_parts"] == 0
     nac, nb = st["n_ac"], st["n_b"]
+    sa = CH.range_bytes(a.row_ptr, 0, a.nrows, 8)
+    sb = CH.range_bytes(b.row_ptr, 0, b.nrows, 8)
+    sc = CH.range_bytes(ref.row_ptr, 0, a.nrows, 8)
     extra = 2 * 8 * (nac - 1) + 8 * (nb - 1) * nac
-    assert st["h2d_bytes"] + st["d2h_bytes"] == st["cost_chunk1"] + extra
+    assert st["h2d_bytes"] + st["d2h_bytes"] == sa + sc + sb * nac + extra
 
 
 def test_chunked_banded_skips_b_parts(h):
