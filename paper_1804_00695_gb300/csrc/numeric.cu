@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
 #pragma unroll
         for (int t = 0; t < PER; t++) {
             const int sidx = gl + t * G;
+            if (t * G >= S) break;   // only the row's 2^L slots are used
             keys[sidx] = -1;
             hi[sidx] = 0.f;
             lo[sidx] = 0.f;
@@ -356,12 +357,16 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             }
             __syncwarp();
         }
-        // compact the occupied slots of each row to the front (read all, then write)
+        // compact the occupied slots of each row to the front (read all, then
+        // write); only as many slots as the warp's largest map
+        const int smax_w = __reduce_max_sync(0xffffffffu, S);
         int kq[PER];
         float hq[PER], lq[PER], l2q[PER];
 #pragma unroll
         for (int t = 0; t < PER; t++) {
             const int sidx = gl + t * G;
+            kq[t] = -1;
+            if (t * G >= smax_w) continue;
             kq[t] = sidx < S ? keys[sidx] : -1;
             hq[t] = hi[sidx];
             lq[t] = lo[sidx];
@@ -371,6 +376,7 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
         int cntr = 0;
 #pragma unroll
         for (int t = 0; t < PER; t++) {
+            if (t * G >= smax_w) break;   // warp-uniform
             const bool occ = kq[t] != -1;
             const unsigned m = (__ballot_sync(0xffffffffu, occ) >> gbase) & lmask;
             if (occ) {
