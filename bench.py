@@ -39,7 +39,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--grid", type=int, default=128, help="grid of the Galerkin workload (profiling cases)")
+    ap.add_argument("--chunk-grid", type=int, default=256, help="grid of the chunked workload (profiling cases)")
+    ap.add_argument("--budget", type=float, default=4e9, help="device budget of the chunked workload, bytes")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (profiling cases)")
+    ap.add_argument("--batch-max", type=int, default=65536, help="largest instance order of the batched workload")
     ap.add_argument("--workload", default="galerkin128",
                     choices=["galerkin128", "rmat20", "chunked256", "batched256"])
     return ap.parse_args()
@@ -350,6 +354,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    a_bytes = 8 * (a.nrows + 1) + 12 * a.nnz
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -357,7 +362,8 @@ def main():
                 "data": "synthetic (seeded generators)",
                 "config": {"workload": workload_name(args.grid), "grid": args.grid,
                            "mults": mults, "nnz_AP": int(ap_rp[-1]), "nnz_RAP": int(rap_rp[-1]),
-                           "l2": "inputs larger than L2 (A alone 686 MB), no flush",
+                           "l2": (f"inputs larger than L2 (A alone {a_bytes / 1e6:.0f} MB), no flush"
+                                  if a_bytes > 129e6 else "inputs smaller than L2, no flush"),
                            "parallelism": f"replicas x{world}"},
                 "pct_hbm_byte_roofline": 100 * step_frac,
                 "step_algorithmic_bytes": step_bytes,

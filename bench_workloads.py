@@ -133,10 +133,10 @@ def chunked256(args, world, local):
     import torch
     import paper_1804_00695_gb300 as sg
     from paper_1804_00695_gb300 import inputs as I
-    n = 256
+    n = args.chunk_grid
     a = I.laplace3d_27pt(n)
     A = sg.HostCsr.from_numpy(a)
-    budget = 4 * 10 ** 9
+    budget = int(args.budget)
     h = sg.Handle(local)
     mults = _mults(a, a.row_ptr)
     link = _link_bandwidth()
@@ -177,8 +177,8 @@ def chunked256(args, world, local):
     moved = stats["h2d_bytes"] + stats["d2h_bytes"] + sym["h2d_bytes"] + sym["d2h_bytes"]
     peak = max(link["bidir"], link["h2d"], link["d2h"])
     _line(args, world, 2 * mults / (ms / 1e3) / 1e9, ms, "f64",
-          {"workload": "chunked C = A*A, 27-point 3D Laplacian on 256^3, FP64, operands and C in "
-                       "pinned host memory, 4e9-byte device budget", "mults": mults, "nnz_C": nnz,
+          {"workload": f"chunked C = A*A, 27-point 3D Laplacian on {n}^3, FP64, operands and C in "
+                       f"pinned host memory, {budget:.3g}-byte device budget", "mults": mults, "nnz_C": nnz,
            "budget_bytes": budget},
           {"roofline": {"bound": "host-link", "achieved": minimal / (ms / 1e3) / 1e9, "peak": peak,
                         "unit": "GB/s", "frac": minimal / (ms / 1e3) / 1e9 / peak,
@@ -193,7 +193,7 @@ def batched256(args, world, local):
     import torch
     import paper_1804_00695_gb300 as sg
     from paper_1804_00695_gb300 import inputs as I
-    pairs = I.random_batch(256, 1024, 65536, 1, dtype=np.float32)
+    pairs = I.random_batch(args.batch_count, 1024, args.batch_max, 1, dtype=np.float32)
     As = [sg.Csr.from_host(a, "cuda") for a, _ in pairs]
     Bs = [sg.Csr.from_host(b, "cuda") for _, b in pairs]
     mults = sum(_mults(a, b.row_ptr) for a, b in pairs)
@@ -261,8 +261,8 @@ def batched256(args, world, local):
     h.set_timing(False)
     gf = lambda ms: 2 * mults / (ms / 1e3) / 1e9
     _line(args, world, gf(fwd_batched), fwd_batched, "f32",
-          {"workload": "256 products A_i*B_i, n_i log-uniform in [1024, 65536], 4-32 random "
-                       "columns per row, N(0,1) FP32", "mults": mults, "nnz_C": int(Cm.nnz),
+          {"workload": f"{args.batch_count} products A_i*B_i, n_i log-uniform in [1024, {args.batch_max}], "
+                       "4-32 random columns per row, N(0,1) FP32", "mults": mults, "nnz_C": int(Cm.nnz),
            "rows": int(sum(a.nrows for a, _ in pairs))},
           {"batched_forward_ms": fwd_batched, "loop_forward_ms": fwd_loop,
            "forward_speedup": fwd_loop / fwd_batched,
