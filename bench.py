@@ -138,6 +138,22 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(ms, dist, device):
+    """Step time of the job: the slowest rank's (every rank runs one replica
+    of the workload; with no process group, the local time)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_throughput(flops_per_replica, world, ms):
+    """Whole-job GFLOP/s: the work of all replicas over the slowest rank's time."""
+    return world * flops_per_replica / (ms / 1e3) / 1e9
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -261,11 +277,8 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     launches = h1.launch_count() + h2.launch_count() - l0
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 2 * mults / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, dist, dev)
+    value = replicas_throughput(2 * mults, world, ms)
 
     # per-kernel CUDA-event timings from the timed region
     tim = {}
@@ -349,10 +362,7 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / ke
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     a_bytes = 8 * (a.nrows + 1) + 12 * a.nnz
     if rank == 0:

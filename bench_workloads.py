@@ -39,7 +39,12 @@ def _mults(a, b_rp):
 
 
 def run(args, rank, world, local):
+    """The secondary workloads are measured on one GPU: under a multi-rank
+    launch rank 0 runs and reports them, the other ranks exit at once."""
     import torch
+    if world > 1 and rank != 0:
+        return
+    world = 1
     torch.cuda.set_device(local)
     if args.workload == "rmat20":
         return rmat20(args, world, local)
