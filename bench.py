@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--grid", type=int, default=128, help="grid of the Galerkin workload (profiling cases)")
     ap.add_argument("--chunk-grid", type=int, default=256, help="grid of the chunked workload (profiling cases)")
     ap.add_argument("--budget", type=float, default=4e9, help="device budget of the chunked workload, bytes")
+    ap.add_argument("--rmat-scale", type=int, default=20, help="scale of the R-MAT workload (profiling cases)")
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (profiling cases)")
     ap.add_argument("--batch-max", type=int, default=65536, help="largest instance order of the batched workload")
     ap.add_argument("--workload", default="galerkin128",

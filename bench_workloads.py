@@ -57,7 +57,7 @@ def rmat20(args, world, local):
     import torch
     import paper_1804_00695_gb300 as sg
     from paper_1804_00695_gb300 import inputs as I
-    g = I.rmat_symmetric(20, 16, seed=1)
+    g = I.rmat_symmetric(args.rmat_scale, 16, seed=1)
     A = sg.Csr.from_host(g, "cuda", np.float32)
     h = sg.Handle(local)
     mults = _mults(g, g.row_ptr)
@@ -90,8 +90,8 @@ def rmat20(args, world, local):
     step_bytes = bench.kernel_bytes(g, g.row_ptr, crp, np.ones(g.nrows, dtype=bool), 4)
     dom = max(tim.items(), key=lambda kv: kv[1][2])
     _line(args, world, 2 * mults / (ms / 1e3) / 1e9, ms, "f32",
-          {"workload": "C = A*A, A symmetrised R-MAT scale 20, edge factor 16, (a,b,c,d) = "
-                       "(.57,.19,.19,.05), seed 1, FP32", "mults": mults, "nnz_C": nnz},
+          {"workload": f"C = A*A, A symmetrised R-MAT scale {args.rmat_scale}, edge factor 16, "
+                       "(a,b,c,d) = (.57,.19,.19,.05), seed 1, FP32", "mults": mults, "nnz_C": nnz},
           {"pct_hbm_byte_roofline": 100 * step_bytes / (ms / 1e3) / 1e9 / hbm,
            "step_algorithmic_bytes": step_bytes,
            "dominant_kernel": {"label": dom[0], "ms_per_step": dom[1][2] / args.steps},

@@ -293,7 +293,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         // lanes per row from the mean number of compressed pairs a row visits
         const double mean_pairs = (double)A->nnz / (double)n *
                                   ((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1)) * 0.6;
-        const int gs = h->g_symbolic ? h->g_symbolic : lanes_for(mean_pairs / 8.0);
+        const int gs = h->g_symbolic ? h->g_symbolic : lanes_for(mean_pairs / 64.0);
         SG_TRY(launch_compress(*B, pairs, ccnt, minmax, desc, ana, &h->dstate->err, c,
                                &h->dstate->b_unsorted));
         SG_TRY(launch_analyze(*A, *B, ana, flops, bins, C_row_ptr, h->dstate, c));
@@ -373,7 +373,7 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     h->lastB = *B;
     h->lastC = *C;
     NumTune tune;
-    tune.G = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 12.0);
+    tune.G = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 40.0);
     tune.small_cap = h->small_cap;
     tune.slot_factor = h->slot_factor;
     const int first_list = tune.small_cap >= 32 ? 3 : 2;

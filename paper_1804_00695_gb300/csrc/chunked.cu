@@ -13,8 +13,8 @@
 //    with its partial C (none before the first B part) and back out.
 //
 // Partial rows live in the final layout of C (offsets from the symbolic
-// phase): the first m slots of a row hold its partial entries in ascending
-// column order, the rest hold column -1.  Copies run on two side streams
+// phase): the first m slots of a row hold its partial entries (in ascending
+// column order once the row's last B part is done), the rest hold column -1.  Copies run on two side streams
 // (host to device, device to host) and the streamed operand is double
 // buffered: while part t is multiplied, part t+1 is copied in.  Every
 // device byte of a call comes out of one arena of exactly the budget.
@@ -123,13 +123,25 @@ __global__ void __launch_bounds__(256) k_fma_warp(
         const int64_t c0 = crp[i];
         const int cap = (int)(crp[i + 1] - c0);
         if (cap == 0 || cap > FMA_WARP_CAP) continue;
-        {   // rows with no stored a_ik in this B part keep their partial row as it is
+        // Rows with no stored a_ik in this B part keep their partial row as it
+        // is.  B parts come in ascending row order, so the pass whose range
+        // holds the row's largest a_ik column is its last: only that pass
+        // sorts the row; earlier ones leave the partial row unsorted.
+        bool final_pass;
+        {
             bool any = false;
-            for (int64_t p = arp[i] + lane; p < arp[i + 1] && !any; p += 32) {
+            int64_t kmax = -1;
+            for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += 32) {
                 const int64_t k = acol[p];
-                any = k >= lo && k < hi;
+                any |= k >= lo && k < hi;
+                kmax = k > kmax ? k : kmax;
             }
             if (!__any_sync(0xffffffffu, any)) continue;
+            for (int d = 16; d > 0; d >>= 1) {
+                const int64_t o = __shfl_xor_sync(0xffffffffu, kmax, d);
+                kmax = o > kmax ? o : kmax;
+            }
+            final_pass = kmax < hi;
         }
         int S = 32;
         while (S < 2 * cap) S <<= 1;
@@ -182,11 +194,14 @@ __global__ void __launch_bounds__(256) k_fma_warp(
             flag |= DERR_COUNT;
             n = cap;
         }
-        int P = 1;
-        while (P < n) P <<= 1;
-        for (int e = n + lane; e < P; e += 32) keys[e] = INT_MAX;
+        if (final_pass) {
+            int P = 1;
+            while (P < n) P <<= 1;
+            for (int e = n + lane; e < P; e += 32) keys[e] = INT_MAX;
+            __syncwarp();
+            bitonic_kv<V>(keys, cval ? vals : nullptr, P, lane, 32, [] { __syncwarp(); });
+        }
         __syncwarp();
-        bitonic_kv<V>(keys, cval ? vals : nullptr, P, lane, 32, [] { __syncwarp(); });
         for (int e = lane; e < cap; e += 32) {
             ccol[c0 + e] = e < n ? keys[e] : -1;
             if (cval) cval[c0 + e] = e < n ? vals[e] : V(0);

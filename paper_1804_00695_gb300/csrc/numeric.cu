@@ -1144,11 +1144,12 @@ __global__ void __launch_bounds__(HUGE_BS, 1) k_num_huge(
 // points at.  For a window, a thread per a_ik whose next column falls in
 // the window adds a_ik * b_kj into win[j - w0] (atomically) while marking j
 // in a bitmap, until B_k leaves the window; rows of B longer than WIN_LONG
-// are walked by whole warps instead (32 entries per step).  The window's
-// entries then leave in column order: prefix counts of the bitmap words give
-// each its place, and the slot is cleared as it is read.  Windows between
-// the row's first and last reachable column are visited in order, so the
-// row is written sorted without a sort.  Global memory per block: a cursor,
+// are walked by whole warps instead (32 entries per step), each warp taking
+// the next such a_ik from a shared counter so the window's work stays
+// balanced.  The window's entries then leave in column order: prefix counts
+// of the bitmap words give each its place, and the slot is cleared as it is
+// read.  Windows between the row's first and last reachable column are
+// visited in order, so the row is written sorted without a sort.  Global memory per block: a cursor,
 // a next column and a list slot per stored entry of the longest row.
 constexpr int WIN_BS = 512, WIN_BPSM = 2, WIN_LONG = 256;
 
@@ -1162,7 +1163,7 @@ __global__ void __launch_bounds__(WIN_BS, WIN_BPSM) k_num_window(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *win = (V *)smem_raw;
     unsigned *bits = (unsigned *)(win + W);
-    __shared__ int bmin_s, bmax_s, wtot, nlong;
+    __shared__ int bmin_s, bmax_s, wtot, nlong, lnext;
     __shared__ int red[NWARP];
     const size_t per = (size_t)max_alen;
     int64_t *cpos = (int64_t *)gws + (size_t)blockIdx.x * per;
@@ -1207,6 +1208,7 @@ __global__ void __launch_bounds__(WIN_BS, WIN_BPSM) k_num_window(
         for (int64_t w0 = cmax >= 0 ? ((int64_t)cmin / W) * W : 1; w0 <= cmax; w0 += W) {
             const int64_t w1 = w0 + W;
             for (int x = threadIdx.x; x < NW; x += WIN_BS) bits[x] = 0;
+            if (threadIdx.x == 0) lnext = 0;
             __syncthreads();
             // short rows of B: a thread per stored a_ik
             for (int64_t p = threadIdx.x; p < plen; p += WIN_BS) {
@@ -1227,8 +1229,14 @@ __global__ void __launch_bounds__(WIN_BS, WIN_BPSM) k_num_window(
                 cpos[p] = q;
                 cnext[p] = c;
             }
-            // long rows of B: a warp per stored a_ik, 32 entries per step
-            for (int j = w; j < nl; j += NWARP) {
+            // long rows of B: a warp per stored a_ik, 32 entries per step; warps
+            // take the next a_ik from a shared counter so that the window's
+            // work is balanced across them
+            while (true) {
+                int j = 0;
+                if (lane == 0) j = atomicAdd(&lnext, 1);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                if (j >= nl) break;
                 const int p = llist[j];
                 const int k = acol[p0 + p];
                 const V av = aval[p0 + p];
