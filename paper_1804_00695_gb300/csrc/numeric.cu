@@ -7,8 +7,8 @@
 //   hashmap-based accumulators"), products dealt evenly over the lanes;
 // * bins 3-4 (<= 1024 outputs): a warp per row with a dense rank
 //   accumulator over the row's column span (bitmap, prefix counts, values
-//   by rank) when the span is at most 2048 blocks of 32 columns, else a
-//   warp-level shared hash map;
+//   by rank) when the span is at most 2048 blocks of 32 columns (three
+//   bitmap sizes), else a warp-level shared hash map;
 // * bin 5 (<= 4096 outputs): a block per row, shared hash map;
 // * bin 6 (more): a windowed dense accumulator when the rows of B are
 //   sorted, else a two-level hash map (shared, then global memory: Section
@@ -462,6 +462,20 @@ __device__ __forceinline__ int row_span_words(const NumP &a, const int2 *__restr
     return row_span_blocks(a, bmm, i, bmin);
 }
 
+// Which dense rank accumulator takes a row of bins 3-4 (0: none, the hash
+// maps of k_num_wide do): the smallest whose bitmap covers the row's span
+// of 32-column blocks and whose value array holds its outputs.  Smaller
+// tiers use less shared memory per warp, so more warps run per SM.
+constexpr int RANK_BW1 = 512, RANK_NMAX1 = 1024, RANK_BW2 = 1024, RANK_NMAX2 = 512, RANK_BW3 = 2048,
+              RANK_NMAX3 = 1024;
+__device__ __forceinline__ int rank_tier(int span, int nn) {
+    if (span <= 0) return 0;
+    if (span <= RANK_BW1 && nn <= RANK_NMAX1) return 1;
+    if (span <= RANK_BW2 && nn <= RANK_NMAX2) return 2;
+    if (span <= RANK_BW3 && nn <= RANK_NMAX3) return 3;
+    return 0;
+}
+
 // Rows of bins 2-4 whose columns fall within 32*BW consecutive columns: a
 // dense accumulator over the row's column span (the dense accumulator of
 // Section 3.1, restricted to the span and held in shared memory).  Pass 1
@@ -493,7 +507,7 @@ template <int BW, int NMAX, int WPB, int MODE>
 __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__restrict__ bdesc,
                                                        const int2 *__restrict__ bmm,
                                                        const int32_t *__restrict__ rows, int64_t count,
-                                                       int min_span_words, const DevState *st, int *err) {
+                                                       int tier, const DevState *st, int *err) {
     using Lay = RankLayout<BW, NMAX, WPB, MODE>;
     using V = ValT<MODE>;
     constexpr int E = 32, NS = BW / 32;
@@ -523,7 +537,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__
         if (nn > NMAX) continue;
         int bmin;
         const int nw = row_span_blocks(a, bmm, i, bmin);
-        if (nw > BW || nw <= min_span_words || nw == 0) continue;
+        if (nw > BW || nw == 0 || rank_tier(nw, nn) != tier) continue;
         const int64_t p0 = a.arp[i];
         const int plen = (int)(a.arp[i + 1] - p0);
         bool nat = MODE == MODE_F64 || b_bad;
@@ -753,7 +767,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__
         const int64_t out = a.crp[i];
         const int nn = (int)(a.crp[i + 1] - out);
         if (nn < min_nnz || nn > SMAX / 2) continue;
-        if (min_span_words > 0 && row_span_words(a, bmm, i) <= min_span_words) continue;
+        if (min_span_words > 0 && rank_tier(row_span_words(a, bmm, i), nn) != 0) continue;
         int S = next_pow2(2 * nn);
         S = S < 32 ? 32 : (S > SMAX ? SMAX : S);
         const int L = __ffs(S) - 1;
@@ -1151,7 +1165,7 @@ __global__ void __launch_bounds__(HUGE_BS, 1) k_num_huge(
 // read.  Windows between the row's first and last reachable column are
 // visited in order, so the row is written sorted without a sort.  Global memory per block: a cursor,
 // a next column and a list slot per stored entry of the longest row.
-constexpr int WIN_BS = 512, WIN_BPSM = 2, WIN_LONG = 256;
+constexpr int WIN_BS = 256, WIN_BPSM = 6, WIN_LONG = 256;
 
 template <typename V, int W>
 __global__ void __launch_bounds__(WIN_BS, WIN_BPSM) k_num_window(
@@ -1362,14 +1376,14 @@ static int run_small_g(const NumTune &t, const NumP &a, const int4 *bdesc, int64
 
 template <int BW, int NMAX, int WPB, int MODE>
 static int run_rank(const NumP &a, const int4 *bdesc, const int2 *bmm, const int32_t *rows, int64_t count,
-                    int min_span, DevState *st, int *err, const char *label, Ctx &c) {
+                    int tier, DevState *st, int *err, const char *label, Ctx &c) {
     const size_t smem = RankLayout<BW, NMAX, WPB, MODE>::bytes;
     SG_TRY(prep(k_num_rank<BW, NMAX, WPB, MODE>, smem));
     int64_t blocks = (count + WPB - 1) / WPB;
     blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
     c.begin(label, count);
     k_num_rank<BW, NMAX, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, bmm, rows, count,
-                                                                                min_span, st, err);
+                                                                                tier, st, err);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -1442,7 +1456,7 @@ static int run_huge(const NumP &a, const spgemm_csr &B, const int32_t *rows, int
 template <typename V>
 static int run_window(const NumP &a, const int32_t *rows, int64_t cnt, int *err, void *gws, size_t gws_bytes,
                       int64_t max_alen, Ctx &c) {
-    constexpr int W = sizeof(V) == 8 ? 8192 : 16384;
+    constexpr int W = sizeof(V) == 8 ? 4096 : 8192;
     const int64_t cap = (int64_t)c.nsm * WIN_BPSM;
     const int64_t blocks = cnt < cap ? cnt : cap;
     if ((size_t)(max_alen > 0 ? max_alen : 1) * 16 * (size_t)blocks > gws_bytes) {
@@ -1480,15 +1494,19 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
             case 2:
             case 3:
             case 4:
-                // dense rank accumulator for rows spanning at most 512, then 2048, blocks
-                // of 32 columns; hash map for wider spans (two map sizes)
-                SG_TRY((run_rank<512, 1024, 8, MODE>(a, bdesc, bmm, r, cnt, 0, st, err, "numeric.rank512", c)));
-                SG_TRY((run_rank<2048, 1024, 4, MODE>(a, bdesc, bmm, r, cnt, 512, st, err, "numeric.rank2048", c)));
+                // dense rank accumulators for the rows rank_takes accepts (two span
+                // limits), hash maps for the others (two map sizes)
+                SG_TRY((run_rank<RANK_BW1, RANK_NMAX1, 8, MODE>(a, bdesc, bmm, r, cnt, 1, st, err,
+                                                                 "numeric.rank512", c)));
+                SG_TRY((run_rank<RANK_BW2, RANK_NMAX2, 8, MODE>(a, bdesc, bmm, r, cnt, 2, st, err,
+                                                                 "numeric.rank1024", c)));
+                SG_TRY((run_rank<RANK_BW3, RANK_NMAX3, 4, MODE>(a, bdesc, bmm, r, cnt, 3, st, err,
+                                                                 "numeric.rank2048", c)));
                 if (b <= 3) {
-                    SG_TRY((run_wide<256, 1024, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 2048, st, err, "numeric.wide3", c)));
+                    SG_TRY((run_wide<256, 1024, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 1, st, err, "numeric.wide3", c)));
                 } else {
-                    SG_TRY((run_wide<512, 2048, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 2048, st, err, "numeric.wide4a", c)));
-                    SG_TRY((run_wide<2048, 2048, 4, MODE>(a, bdesc, bmm, r, cnt, 257, 2048, st, err, "numeric.wide4b", c)));
+                    SG_TRY((run_wide<512, 2048, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 1, st, err, "numeric.wide4a", c)));
+                    SG_TRY((run_wide<2048, 2048, 4, MODE>(a, bdesc, bmm, r, cnt, 257, 1, st, err, "numeric.wide4b", c)));
                 }
                 break;
             case 5: SG_TRY((run_block<256, 8192, V>(a, r, cnt, err, b, c))); break;

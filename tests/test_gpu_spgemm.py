@@ -190,11 +190,12 @@ def _strided_rows(nrows, ncols, widths, mult, step, seed):
 
 
 @pytest.mark.parametrize("small_cap", [32, 16])
-@pytest.mark.parametrize("ncols", [9000, 50000, 300000])
+@pytest.mark.parametrize("ncols", [9000, 25000, 50000, 300000])
 def test_medium_rows_every_span(h, ncols, small_cap):
     """Rows of 17..1024 outputs whose columns span at most 512 blocks of 32
-    (first dense rank accumulator), 512..2048 blocks (second), or more (hash
-    maps), in FP32, double-word FP64 and native FP64."""
+    (first dense rank accumulator), 512..1024 blocks with at most 512 outputs
+    (second), up to 2048 blocks (third), or more (hash maps), in FP32,
+    double-word FP64 and native FP64."""
     nb = 3000
     a = _strided_rows(1200, nb, [1, 2, 5, 9, 17, 30, 44], 7, 11, 41)
     b = _strided_rows(nb, ncols, [20, 23], 37, ncols // 23 + 1, 42)
@@ -213,7 +214,8 @@ def test_medium_rows_every_span(h, ncols, small_cap):
         h.set_timing(False)
     sym, num = h.bin_counts()
     assert num[2] > 0 and num[3] > 0 and num[4] > 0, num
-    want = {9000: "numeric.rank512", 50000: "numeric.rank2048", 300000: "numeric.wide"}[ncols]
+    want = {9000: "numeric.rank512", 25000: "numeric.rank1024", 50000: "numeric.rank2048",
+            300000: "numeric.wide"}[ncols]
     assert any(l.startswith(want) for l in labels), labels
 
 
