@@ -21,7 +21,9 @@
 //
 // The symbolic phase is chunked the same way with the pattern only; it keeps
 // the pattern of B resident (its Algorithm 4 plan must put all of B in one
-// part) and streams the rows of A, counting distinct columns per row.
+// part), compressed on the device into (block, mask) pairs (Section 2.1),
+// and streams the rows of A, counting the distinct columns of each row by
+// ORing masks per block.  A B with unsorted rows is counted on its columns.
 #include <climits>
 #include <cstring>
 #include <algorithm>
@@ -383,6 +385,163 @@ __global__ void __launch_bounds__(256) k_count_bitmap(
             for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
                 const int col = bcol[q];
                 atomicOr(&bits[col >> 5], 1u << (col & 31));
+            }
+        }
+        __syncthreads();
+        long long c = 0;
+        for (int64_t s = threadIdx.x; s < nwords; s += 256) c += __popc(bits[s]);
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (lane == 0) red[w] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int j = 0; j < 8; j++) t += red[j];
+            cnt[i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- compressed pattern of B (Section 2.1): (block = col/32, mask) pairs
+// Distinct 32-column blocks of each row of B, a thread per row (columns
+// ascending; a row that is not flags the call, which then counts columns).
+__global__ void k_pairs_count(int64_t nrows, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              int64_t *__restrict__ poff, int *unsorted) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int n = 0, prev = -1, pc = -1;
+    bool bad = false;
+    for (int64_t q = rp[r]; q < rp[r + 1]; q++) {
+        const int c = col[q];
+        bad |= c <= pc;
+        pc = c;
+        const int b = c >> 5;
+        n += b != prev;
+        prev = b;
+    }
+    poff[r + 1] = n;
+    if (bad) atomicOr(unsorted, 1);
+}
+
+// Pairs of each row at poff[r]..: blocks ascending, masks ORed.
+__global__ void k_pairs_write(int64_t nrows, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const int64_t *__restrict__ poff, int2 *__restrict__ pairs) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int64_t o = poff[r] - 1;
+    int prev = -1;
+    unsigned m = 0;
+    for (int64_t q = rp[r]; q < rp[r + 1]; q++) {
+        const int c = col[q], b = c >> 5;
+        if (b != prev) {
+            if (prev >= 0) pairs[o] = make_int2(prev, (int)m);
+            o++;
+            prev = b;
+            m = 0;
+        }
+        m |= 1u << (c & 31);
+    }
+    if (prev >= 0) pairs[o] = make_int2(prev, (int)m);
+}
+
+// Symbolic count of a part of A against the compressed pattern of B: a warp
+// per row ORs the pairs of its B_k into a shared map from block to mask
+// (CNTP_S slots), the pairs dealt out over the lanes through prefix sums of
+// pairs(B_k); the count is the sum of the masks' popcounts.  Rows whose
+// blocks overflow the map are marked -1 for k_count_pairs_bitmap.
+constexpr int CNTP_S = 512, CNTP_WPB = 8;
+
+__global__ void __launch_bounds__(256) k_count_pairs(
+    int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const int64_t *__restrict__ poff, const int2 *__restrict__ pairs, int64_t *__restrict__ cnt,
+    int *overflow, int64_t nrows_b, int *err) {
+    constexpr int E = 32, L = __builtin_ctz(CNTP_S);
+    __shared__ int keys_all[CNTP_WPB * CNTP_S];
+    __shared__ unsigned masks_all[CNTP_WPB * CNTP_S];
+    __shared__ long long eq0_all[CNTP_WPB * E];
+    __shared__ int pre_all[CNTP_WPB * (E + 1)];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *keys = keys_all + w * CNTP_S;
+    unsigned *masks = masks_all + w * CNTP_S;
+    long long *eq0 = eq0_all + w * E;
+    int *pre = pre_all + w * (E + 1);
+    for (int64_t i = (int64_t)blockIdx.x * CNTP_WPB + w; i < nrows; i += (int64_t)gridDim.x * CNTP_WPB) {
+        for (int s = lane; s < CNTP_S; s += 32) {
+            keys[s] = -1;
+            masks[s] = 0;
+        }
+        __syncwarp();
+        const int64_t p0 = arp[i];
+        const int plen = (int)(arp[i + 1] - p0);
+        bool fail = false;
+        for (int pb = 0; pb < plen; pb += E) {
+            int len = 0;
+            if (pb + lane < plen) {
+                const int k = acol[p0 + pb + lane];
+                if (k < 0 || (int64_t)k >= nrows_b) {
+                    atomicOr(err, DERR_COL_RANGE);
+                } else {
+                    eq0[lane] = poff[k];
+                    len = (int)(poff[k + 1] - poff[k]);
+                }
+            }
+            int incl = len;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            pre[lane] = incl - len;
+            if (lane == 31) pre[E] = incl;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            int e = 0;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                if (t < total && !fail) {
+                    while (pre[e + 1] <= t) e++;
+                    const int2 pr = pairs[eq0[e] + (t - pre[e])];
+                    fail = !sym_insert(keys, masks, L, pr.x, (unsigned)pr.y);
+                }
+            }
+            fail = __any_sync(0xffffffffu, fail);
+            __syncwarp();
+            if (fail) break;
+        }
+        int c = 0;
+        for (int s = lane; s < CNTP_S; s += 32) c += __popc(masks[s]);
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (lane == 0) {
+            if (fail) {
+                cnt[i] = -1;
+                atomicAdd(overflow, 1);
+            } else {
+                cnt[i] = c;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Rows marked -1: a block per row ORs the pairs into a bitmap over all
+// column blocks of B (global memory, one per block).
+__global__ void __launch_bounds__(256) k_count_pairs_bitmap(
+    int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+    const int64_t *__restrict__ poff, const int2 *__restrict__ pairs, int64_t *__restrict__ cnt,
+    int64_t nwords, unsigned *gbits, const int *overflow, int64_t nrows_b) {
+    __shared__ long long red[8];
+    if (*(volatile const int *)overflow == 0) return;
+    unsigned *bits = gbits + (size_t)blockIdx.x * (size_t)nwords;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+        if (cnt[i] >= 0) continue;
+        for (int64_t s = threadIdx.x; s < nwords; s += 256) bits[s] = 0;
+        __syncthreads();
+        for (int64_t p = arp[i] + w; p < arp[i + 1]; p += 8) {
+            const int k = acol[p];
+            if (k < 0 || (int64_t)k >= nrows_b) continue;
+            for (int64_t q = poff[k] + lane; q < poff[k + 1]; q += 32) {
+                const int2 pr = pairs[q];
+                atomicOr(&bits[pr.x], (unsigned)pr.y);
             }
         }
         __syncthreads();
@@ -767,14 +926,17 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
                      int64_t *nnz_C, size_t budget, ChunkStats &stats) {
     Ctx &c = *env.ctx;
     const cudaStream_t s = c.s, si = env.s_in, so = env.s_out;
-    cudaEvent_t *ev = env.ev;   // [0..1] A part in, [2..3] counted, [4..5] offsets out, [6] B in
+    cudaEvent_t *ev = env.ev;   // [0..1] A part in, [2..3] counted, [4..5] offsets out, [6] B in, [7] B compressed
     const int64_t nwords = (B.ncols + 31) / 32;
     // pattern-only sizes; C contributes its offsets only
     std::vector<int64_t> &zeros = *env.zeros;
     if ((int64_t)zeros.size() < A.nrows + 1) zeros.assign((size_t)A.nrows + 1, 0);
     ChunkPlan p;
     const size_t bitmap = r256((size_t)c.nsm * (size_t)nwords * 4);
-    const size_t reserve = bitmap + 8192;
+    const size_t poff_bytes = r256((size_t)(B.nrows + 1) * 8);
+    const size_t btmp_bytes = r256(scan_tmp_bytes(B.nrows));
+    const size_t raw_b = r256((size_t)(B.nrows + 1) * 8) + r256((size_t)std::max<int64_t>(B.nnz, 1) * 4);
+    const size_t reserve = bitmap + poff_bytes + btmp_bytes + 8192;
     if (budget <= reserve) {
         set_error("chunked symbolic: budget %zu below the fixed working set %zu", budget, reserve);
         return SPGEMM_ERR_BUDGET;
@@ -787,19 +949,18 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
         return SPGEMM_ERR_BUDGET;
     }
     // A parts are double buffered (with their counts and the scan's scratch):
-    // shrink them until B + 2 parts fit
+    // shrink them until the pattern of B and two parts fit
     int64_t max_rows = 0, max_nnz = 0;
+    size_t part_bytes = 0;
     for (int iter = 0; iter < 16; iter++) {
         max_rows = max_nnz = 0;
         for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
             max_rows = std::max(max_rows, p.ac_cuts[j + 1] - p.ac_cuts[j]);
             max_nnz = std::max(max_nnz, A.row_ptr[p.ac_cuts[j + 1]] - A.row_ptr[p.ac_cuts[j]]);
         }
-        const size_t need = r256((size_t)(B.nrows + 1) * 8) + r256((size_t)std::max<int64_t>(B.nnz, 1) * 4) +
-                            2 * (r256((size_t)(max_rows + 1) * 8) + r256((size_t)std::max<int64_t>(max_nnz, 1) * 4) +
-                                 r256((size_t)(max_rows + 1) * 8) + r256(scan_tmp_bytes(max_rows))) +
-                            reserve + 4096;
-        if (need <= budget) break;
+        part_bytes = r256((size_t)(max_rows + 1) * 8) + r256((size_t)std::max<int64_t>(max_nnz, 1) * 4) +
+                     r256((size_t)(max_rows + 1) * 8) + r256(scan_tmp_bytes(max_rows));
+        if (raw_b + 2 * part_bytes + reserve + 8 * 256 <= budget) break;
         fast = fast * 3 / 4;
         SG_TRY(plan_chunks(A.row_ptr, A.nrows, zeros.data(), B.row_ptr, B.nrows, 0, 0, fast, p));
         if (p.b_cuts.size() != 2 || iter == 15) {
@@ -811,27 +972,22 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     stats.branch = p.branch;
     stats.n_ac = (int64_t)p.ac_cuts.size() - 1;
     stats.n_b = 1;
+    // arena: fixed scratch from the bottom, the raw pattern of B at the top
     Arena ar{(char *)env.arena, budget, 0};
     unsigned *bits = (unsigned *)ar.take(bitmap);
-    int *ovf = (int *)ar.take(2 * sizeof(int));
-    int64_t *carry = (int64_t *)ar.take(3 * sizeof(int64_t));   // two running offsets + scan total
-    PartBuf Bp, Ap[2];
-    int64_t *cnt[2] = {nullptr, nullptr};
-    void *tmp[2] = {nullptr, nullptr};
-    bool ok = bits && ovf && carry && take_part(ar, Bp, B.nrows, B.nnz, 0);
-    for (int u = 0; u < 2 && ok; u++) {
-        ok = take_part(ar, Ap[u], max_rows, max_nnz, 0);
-        cnt[u] = (int64_t *)ar.take((size_t)(max_rows + 1) * 8);
-        tmp[u] = ar.take(scan_tmp_bytes(max_rows));
-        ok = ok && cnt[u] && tmp[u];
-    }
-    if (!ok) {
-        set_error("chunked symbolic: parts do not fit the %zu-byte budget", budget);
+    int *flags = (int *)ar.take(4 * sizeof(int));   // overflow per slot, unsorted rows of B
+    int64_t *carry = (int64_t *)ar.take(4 * sizeof(int64_t));   // running offsets, scan totals
+    int64_t *poff = (int64_t *)ar.take(poff_bytes);
+    void *btmp = ar.take(btmp_bytes);
+    const size_t top = (budget - raw_b) & ~(size_t)255;
+    if (!bits || !flags || !carry || !poff || !btmp || ar.used > top) {
+        set_error("chunked symbolic: budget %zu too small", budget);
         return SPGEMM_ERR_BUDGET;
     }
-    stats.device_bytes = (int64_t)ar.used;
+    PartBuf Bp;
+    Bp.rp = (int64_t *)((char *)env.arena + top);
+    Bp.col = (int32_t *)((char *)Bp.rp + r256((size_t)(B.nrows + 1) * 8));
     int st = SPGEMM_OK;
-    // the pattern of B once, checked on the device
     stats.h2d += copy_rows_in(B, 0, B.nrows, 0, Bp.rp, Bp.col, nullptr, si, &st);
     SG_TRY(st);
     if (B.nnz > 0)
@@ -839,7 +995,53 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
             Bp.col, B.nnz, B.ncols, env.err);
     SG_CUDA(cudaEventRecord(ev[6], si));
     SG_CUDA(cudaStreamWaitEvent(s, ev[6], 0));
-    SG_CUDA(cudaMemsetAsync(carry, 0, 3 * sizeof(int64_t), s));
+    // compress the pattern of B into (block, mask) pairs (Section 2.1): count,
+    // offsets, and the host learns the pair count (one synchronisation)
+    SG_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
+    SG_CUDA(cudaMemsetAsync(carry, 0, 4 * sizeof(int64_t), s));
+    SG_CUDA(cudaMemsetAsync(poff, 0, 8, s));
+    if (B.nrows > 0) {
+        k_pairs_count<<<(unsigned)((B.nrows + 255) / 256), 256, 0, s>>>(B.nrows, Bp.rp, Bp.col, poff, &flags[2]);
+        SG_CUDA(cudaGetLastError());
+        SG_TRY(launch_scan_counts(poff, B.nrows, (long long *)&carry[3], btmp, c));
+    }
+    long long hbuf[2] = {0, 0};
+    SG_CUDA(cudaMemcpyAsync(&hbuf[0], &carry[3], 8, cudaMemcpyDeviceToHost, s));
+    int hunsorted = 0;
+    SG_CUDA(cudaMemcpyAsync(&hunsorted, &flags[2], 4, cudaMemcpyDeviceToHost, s));
+    SG_CUDA(cudaStreamSynchronize(s));
+    const int64_t npairs = hbuf[0];
+    const size_t pairs_bytes = r256((size_t)std::max<int64_t>(npairs, 1) * 8);
+    bool use_pairs = !hunsorted && ar.used + pairs_bytes + 2 * part_bytes + 8 * 256 <= budget &&
+                     ar.used + pairs_bytes <= top;
+    int2 *pairs = nullptr;
+    if (use_pairs) {
+        pairs = (int2 *)ar.take(pairs_bytes);
+        if (B.nrows > 0) {
+            k_pairs_write<<<(unsigned)((B.nrows + 255) / 256), 256, 0, s>>>(B.nrows, Bp.rp, Bp.col, poff, pairs);
+            SG_CUDA(cudaGetLastError());
+        }
+        // A parts may overwrite the raw pattern from here on
+        SG_CUDA(cudaEventRecord(ev[7], s));
+        SG_CUDA(cudaStreamWaitEvent(si, ev[7], 0));
+    }
+    const size_t peak_with_raw = ar.used + (budget - top);
+    PartBuf Ap[2];
+    int64_t *cnt[2] = {nullptr, nullptr};
+    void *tmp[2] = {nullptr, nullptr};
+    bool ok = true;
+    for (int u = 0; u < 2 && ok; u++) {
+        ok = take_part(ar, Ap[u], max_rows, max_nnz, 0);
+        cnt[u] = (int64_t *)ar.take((size_t)(max_rows + 1) * 8);
+        tmp[u] = ar.take(scan_tmp_bytes(max_rows));
+        ok = ok && cnt[u] && tmp[u];
+    }
+    if (!ok || (!use_pairs && ar.used > top)) {
+        set_error("chunked symbolic: parts do not fit the %zu-byte budget", budget);
+        return SPGEMM_ERR_BUDGET;
+    }
+    // peak: the raw pattern of B lived beside the fixed scratch (and the pairs)
+    stats.device_bytes = (int64_t)std::max(ar.used, peak_with_raw);
     C_row_ptr[0] = 0;
     const size_t smem = (size_t)CNT_WPB * CNT_S * 4;
     SG_CUDA(cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -857,16 +1059,28 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
         int64_t *x = cnt[slot];
         SG_CUDA(cudaMemsetAsync(x, 0, 8, s));
         if (rows > 0) {
-            SG_CUDA(cudaMemsetAsync(&ovf[slot], 0, 4, s));
-            const int64_t blocks = std::min<int64_t>((rows + CNT_WPB - 1) / CNT_WPB, (int64_t)c.nsm * 16);
-            c.begin("chunked.count", rows);
-            k_count_warp<<<(unsigned)blocks, 256, smem, s>>>(rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col,
-                                                             x + 1, &ovf[slot], B.nrows, env.err);
-            c.end();
-            SG_CUDA(cudaGetLastError());
-            k_count_bitmap<<<(unsigned)std::min<int64_t>(rows, (int64_t)c.nsm), 256, 0, s>>>(
-                rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col, x + 1, nwords, bits, &ovf[slot], B.nrows);
-            SG_CUDA(cudaGetLastError());
+            SG_CUDA(cudaMemsetAsync(&flags[slot], 0, 4, s));
+            if (use_pairs) {
+                const int64_t blocks = std::min<int64_t>((rows + CNTP_WPB - 1) / CNTP_WPB, (int64_t)c.nsm * 16);
+                c.begin("chunked.count", rows);
+                k_count_pairs<<<(unsigned)blocks, 256, 0, s>>>(rows, Ap[slot].rp, Ap[slot].col, poff, pairs, x + 1,
+                                                               &flags[slot], B.nrows, env.err);
+                c.end();
+                SG_CUDA(cudaGetLastError());
+                k_count_pairs_bitmap<<<(unsigned)std::min<int64_t>(rows, (int64_t)c.nsm), 256, 0, s>>>(
+                    rows, Ap[slot].rp, Ap[slot].col, poff, pairs, x + 1, nwords, bits, &flags[slot], B.nrows);
+                SG_CUDA(cudaGetLastError());
+            } else {
+                const int64_t blocks = std::min<int64_t>((rows + CNT_WPB - 1) / CNT_WPB, (int64_t)c.nsm * 16);
+                c.begin("chunked.count", rows);
+                k_count_warp<<<(unsigned)blocks, 256, smem, s>>>(rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col,
+                                                                 x + 1, &flags[slot], B.nrows, env.err);
+                c.end();
+                SG_CUDA(cudaGetLastError());
+                k_count_bitmap<<<(unsigned)std::min<int64_t>(rows, (int64_t)c.nsm), 256, 0, s>>>(
+                    rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col, x + 1, nwords, bits, &flags[slot], B.nrows);
+                SG_CUDA(cudaGetLastError());
+            }
             SG_TRY(launch_scan_counts(x, rows, (long long *)&carry[2], tmp[slot], c));
         }
         k_add_carry<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(x, rows, &carry[j & 1],

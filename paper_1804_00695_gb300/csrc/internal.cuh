@@ -93,6 +93,29 @@ __device__ __forceinline__ unsigned hash_slot(int key, int log2S) {
     return ((unsigned)key * 0x9E3779B1u) >> (32 - log2S);
 }
 
+// Insert block `blk` with mask m into a map of 2^L slots; false if full.
+__device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int L, int blk, unsigned m) {
+    const unsigned msk = (1u << L) - 1;
+    unsigned h = hash_slot(blk, L);
+#pragma unroll 1
+    for (int probe = 0; probe <= (int)msk; probe++) {
+        int k = ((volatile int *)keys)[h];
+        if (k == blk) {
+            atomicOr(&masks[h], m);
+            return true;
+        }
+        if (k == -1) {
+            int old = atomicCAS(&keys[h], -1, blk);
+            if (old == -1 || old == blk) {
+                atomicOr(&masks[h], m);
+                return true;
+            }
+        }
+        h = (h + 1) & msk;
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------- launch context
 // Every kernel launch goes through a Ctx: it carries the stream and SM count,
 // counts launches, and (when timing is on) brackets each launch with CUDA

@@ -19,28 +19,6 @@
 
 namespace sg {
 
-// Insert block `blk` with mask m into a map of 2^L slots; false if full.
-__device__ __forceinline__ bool sym_insert(int *keys, unsigned *masks, int L, int blk, unsigned m) {
-    const unsigned msk = (1u << L) - 1;
-    unsigned h = hash_slot(blk, L);
-#pragma unroll 1
-    for (int probe = 0; probe <= (int)msk; probe++) {
-        int k = ((volatile int *)keys)[h];
-        if (k == blk) {
-            atomicOr(&masks[h], m);
-            return true;
-        }
-        if (k == -1) {
-            int old = atomicCAS(&keys[h], -1, blk);
-            if (old == -1 || old == blk) {
-                atomicOr(&masks[h], m);
-                return true;
-            }
-        }
-        h = (h + 1) & msk;
-    }
-    return false;
-}
 
 // Per-row-slot layout of k_sym_first in 32-bit words: keys[32], masks[32],
 // eq0[E] (int64), pre[E+1]; the stride is padded to G (mod 32) words so that

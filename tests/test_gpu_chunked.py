@@ -164,3 +164,28 @@ def test_chunked_budget_errors(h):
     with pytest.raises(sg.SpgemmError) as ei:
         h.chunked(A, sg.HostCsr.from_numpy(I.random_csr(40, 30, 0.2, 96)), 512)
     assert ei.value.status == 5
+
+
+def test_chunked_symbolic_compressed_and_fallbacks(h):
+    """Chunked counts from the compressed pattern of B, with rows whose blocks
+    overflow the per-warp map (bitmap path), and from the columns when B has
+    unsorted rows; every count against the oracle."""
+    nb, ncols = 600, 100000
+    k = np.repeat(np.arange(nb), 10)
+    t = np.tile(np.arange(10), nb)
+    key = np.unique(k * ncols + (k * 7919 + t * 9973) % ncols)
+    rp = np.zeros(nb + 1, dtype=np.int64)
+    np.cumsum(np.bincount(key // ncols, minlength=nb), out=rp[1:])
+    b = I.Csr(nb, ncols, rp, (key % ncols).astype(np.int32), np.ones(len(key)))
+    d = I.random_csr(40, nb, 0.02, 97).to_dense() != 0
+    d[0, :] = True                         # a row reaching every row of B: ~6000 blocks
+    r, cidx = np.nonzero(d)
+    arp = np.zeros(41, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=40), out=arp[1:])
+    a = I.Csr(40, nb, arp, cidx.astype(np.int32), np.ones(len(cidx)))
+    ref = oracle.spgemm(a, b)
+    for bb in (b, I.random_csr(nb, 900, 0.05, 98, shuffle_cols=True)):
+        ref = oracle.spgemm(a, bb)
+        rp_c, nnz = h.chunked_symbolic(sg.HostCsr.from_numpy(a), sg.HostCsr.from_numpy(bb), 1 << 26)
+        assert nnz == ref.nnz
+        assert np.array_equal(rp_c.numpy(), ref.row_ptr)
