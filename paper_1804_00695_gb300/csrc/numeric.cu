@@ -245,22 +245,22 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
         }
         // rows with an A value outside the double-word range accumulate natively
         bool nat = MODE == MODE_F64 || b_bad;
+        // rows longer than one staging batch check their A values for the
+        // double-word range first; shorter rows find out while staging
         if (MODE == MODE_DW && !nat) {
             bool ok = true;
-            for (int pp = gl; pp < plen; pp += G) dw_split(((const double *)a.aval)[p0 + pp], ok);
+            if (plen > E)
+                for (int pp = gl; pp < plen; pp += G) dw_split(((const double *)a.aval)[p0 + pp], ok);
             const unsigned bad = __ballot_sync(0xffffffffu, !ok);
             nat = ((bad >> gbase) & lmask) != 0;
         }
         const int maxlen = __reduce_max_sync(0xffffffffu, plen);
-        // warps without native rows add with atomics (three levels for
-        // double-words); a warp holding a native row merges same-slot lanes
-        // with __match_any_sync and adds in turns
-        const bool wnat = MODE == MODE_F64 || __any_sync(0xffffffffu, nat);
-        const bool three = !wnat || plen > DW2_MAX_TERMS;
+        bool wnat = MODE == MODE_F64, three = false;
         for (int pb = 0; pb < maxlen; pb += E) {
             // stage entries [pb, pb+E): lane gl takes EL consecutive entries
             int cnt[EL];
             int lsum = 0;
+            bool split_ok = true;
 #pragma unroll
             for (int u = 0; u < EL; u++) {
                 const int e = gl * EL + u;
@@ -273,8 +273,7 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
                     eq0[e] = desc_start(d);
                     const V av = ((const V *)a.aval)[p0 + pidx];
                     if (MODE == MODE_DW && !nat) {
-                        bool dummy = true;
-                        const float2 s2 = dw_split((double)av, dummy);
+                        const float2 s2 = dw_split((double)av, split_ok);
                         ea[e] = __longlong_as_double(((long long)__float_as_uint(s2.y) << 32) |
                                                      (long long)__float_as_uint(s2.x));
                     } else {
@@ -283,6 +282,25 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
                 }
                 cnt[u] = len;
                 lsum += len;
+            }
+            if (pb == 0) {
+                if (MODE == MODE_DW) {
+                    // a short row with a value out of range: native, staged again
+                    const unsigned bad = __ballot_sync(0xffffffffu, !split_ok);
+                    if (!nat && ((bad >> gbase) & lmask) != 0) {
+                        nat = true;
+#pragma unroll
+                        for (int u = 0; u < EL; u++) {
+                            const int e = gl * EL + u;
+                            if (e < plen) ea[e] = ((const double *)a.aval)[p0 + e];
+                        }
+                    }
+                }
+                // warps without native rows add with atomics (three levels for
+                // double-words); a warp holding a native row merges same-slot
+                // lanes with __match_any_sync and adds in turns
+                wnat = MODE == MODE_F64 || __any_sync(0xffffffffu, nat);
+                three = !wnat || plen > DW2_MAX_TERMS;
             }
             // exclusive scan of the lanes' sums within the row's group
             int incl = lsum;

@@ -147,11 +147,14 @@ def test_lane_options_galerkin(h, native, lanes):
         h.set_option(sg.OPT_LANES_SYMBOLIC, 0)
 
 
-def test_double_word_range_fallback(h):
+@pytest.mark.parametrize("shape", [(60, 50, 70, 0.2), (40, 200, 30, 0.3)])
+def test_double_word_range_fallback(h, shape):
     """Values outside the double-word range (tiny, huge) take the native
-    path and still meet the FP64 tolerance; zeros are exact."""
-    a = I.random_csr(60, 50, 0.2, 31)
-    b = I.random_csr(50, 70, 0.2, 32)
+    path and still meet the FP64 tolerance; zeros are exact.  Rows of A
+    shorter and longer than one staging batch (32 entries)."""
+    m, k, n, dens = shape
+    a = I.random_csr(m, k, dens, 31)
+    b = I.random_csr(k, n, dens, 32)
     av = a.val.copy()
     av[::7] *= 1e-30      # below 2^-60: those rows go native
     bv = b.val.copy()
