@@ -177,6 +177,9 @@ SPGEMM_API int spgemm_plan_chunks(const int64_t *A_row_ptr, int64_t nrows_A, con
  * stream; parts of B that the part of A does not reach are skipped) and
  * Algorithm 3 (parts of B stay while A and C stream, partial C going out
  * and in).  Each step is the row-range fused multiply-add of Section 3.2.2.
+ * In Algorithm 2, when the rows of B a part of A reaches fit one streaming
+ * buffer, that window of rows is copied once instead of the fixed parts and
+ * the part is multiplied in one pass (same result, fewer bytes and passes).
  * The streamed operand is double buffered on side streams.  Values of C are
  * accumulated natively (FP64 or FP32).  The call returns once all copies and
  * kernels are enqueued (it waits once per part of A for its column range);
@@ -187,7 +190,8 @@ SPGEMM_API int spgemm_plan_chunks(const int64_t *A_row_ptr, int64_t nrows_A, con
  *
  * spgemm_chunked_stats reports the last chunked call: algorithm (2 or 3),
  * Algorithm 4 branch, parts, both copy-cost formulas, bytes actually copied
- * each way, B parts skipped, and device bytes in use. */
+ * each way, B parts skipped, device bytes in use, and the parts of A whose
+ * rows of B came as one window. */
 typedef struct spgemm_chunk_stats {
     int algorithm, branch;
     int64_t n_ac, n_b;
@@ -195,6 +199,7 @@ typedef struct spgemm_chunk_stats {
     int64_t h2d_bytes, d2h_bytes;
     int64_t skipped_b_parts;
     int64_t device_bytes;
+    int64_t b_windows;
 } spgemm_chunk_stats;
 SPGEMM_API int spgemm_chunked_symbolic(spgemm_handle handle, const spgemm_csr *A, const spgemm_csr *B,
                                        int64_t *C_row_ptr, int64_t *nnz_C, size_t fast_mem_budget,

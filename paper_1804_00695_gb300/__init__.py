@@ -50,7 +50,8 @@ class ChunkPlanRec(C.Structure):
 class ChunkStatsRec(C.Structure):
     _fields_ = [("algorithm", C.c_int), ("branch", C.c_int), ("n_ac", C.c_int64), ("n_b", C.c_int64),
                 ("cost_chunk1", C.c_int64), ("cost_chunk2", C.c_int64), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("skipped_b_parts", C.c_int64), ("device_bytes", C.c_int64)]
+                ("d2h_bytes", C.c_int64), ("skipped_b_parts", C.c_int64), ("device_bytes", C.c_int64),
+                ("b_windows", C.c_int64)]
 
 
 class CsrDesc(C.Structure):

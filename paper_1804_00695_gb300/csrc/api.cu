@@ -483,6 +483,7 @@ int spgemm_chunked_stats(spgemm_handle h, spgemm_chunk_stats *out) {
     out->d2h_bytes = x.d2h;
     out->skipped_b_parts = x.skipped_b;
     out->device_bytes = x.device_bytes;
+    out->b_windows = x.b_windows;
     return SPGEMM_OK;
 }
 

@@ -637,6 +637,20 @@ static bool take_part(Arena &ar, PartBuf &b, int64_t rows, int64_t nnz, int vb) 
     return b.rp && b.col && (vb == 0 || b.val);
 }
 
+// A buffer laid out for rows (offsets) and nnz entries (columns, values).
+static size_t carve_bytes(int64_t rows, int64_t nnz, int vb) {
+    return r256((size_t)(rows + 1) * 8) + r256((size_t)std::max<int64_t>(nnz, 1) * 4) +
+           (size_t)std::max<int64_t>(nnz, 1) * vb;
+}
+
+static PartBuf carve(char *base, int64_t rows, int vb, int64_t nnz) {
+    PartBuf b;
+    b.rp = (int64_t *)base;
+    b.col = (int32_t *)(base + r256((size_t)(rows + 1) * 8));
+    b.val = vb ? (void *)((char *)b.col + r256((size_t)std::max<int64_t>(nnz, 1) * 4)) : nullptr;
+    return b;
+}
+
 template <typename V>
 static int launch_fma(const PartBuf &A, int64_t nrows, int64_t lo, int64_t hi, const PartBuf &B,
                       const PartBuf &Cp, bool values, int64_t fma_blocks, int64_t slots, void *gws,
@@ -771,12 +785,27 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
         max_b_rows = std::max(max_b_rows, p.b_cuts[t + 1] - p.b_cuts[t]);
         max_b_nnz = std::max(max_b_nnz, B.row_ptr[p.b_cuts[t + 1]] - B.row_ptr[p.b_cuts[t]]);
     }
-    const int nbuf_ac = 2, nbuf_b = p.algorithm == 2 ? 2 : 1;
+    const int nbuf_ac = 2;
     PartBuf Ab[2], Cb[2], Bb[2];
     bool ok = mm != nullptr;
     for (int u = 0; u < nbuf_ac && ok; u++)
         ok = take_part(ar, Ab[u], max_ac_rows, max_ac_a, vb) && take_part(ar, Cb[u], max_ac_rows, max_ac_c, vb);
-    for (int u = 0; u < nbuf_b && ok; u++) ok = take_part(ar, Bb[u], max_b_rows, max_b_nnz, vb);
+    // Algorithm 2: two byte buffers for the streamed rows of B, as large as
+    // the budget leaves (at least a fixed part each); a part of B or a window
+    // of rows is laid out in them per copy.  Algorithm 3: one fixed part.
+    char *binner[2] = {nullptr, nullptr};
+    size_t inner_cap = 0;
+    if (p.algorithm == 2) {
+        const size_t need_fixed = carve_bytes(max_b_rows, max_b_nnz, vb);
+        const size_t left = budget > ar.used + 4096 ? budget - ar.used - 4096 : 0;
+        inner_cap = std::max(need_fixed, (left / 2) & ~(size_t)255);
+        for (int u = 0; u < 2 && ok; u++) {
+            binner[u] = (char *)ar.take(inner_cap);
+            ok = binner[u] != nullptr;
+        }
+    } else {
+        ok = ok && take_part(ar, Bb[0], max_b_rows, max_b_nnz, vb);
+    }
     if (!ok) {
         set_error("chunked: parts do not fit the %zu-byte budget", budget);
         return SPGEMM_ERR_BUDGET;
@@ -836,22 +865,30 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             // still has the previous part's products queued
             SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
             const int lo_c = hmm[2 * slot], hi_c = hmm[2 * slot + 1];
-            std::vector<size_t> need;
-            for (size_t t = 0; t + 1 < p.b_cuts.size(); t++)
-                if (hi_c >= 0 && p.b_cuts[t] <= hi_c && p.b_cuts[t + 1] > lo_c) need.push_back(t);
-            stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
+            // the rows of B this part reaches, as (r0, r1) copies: one window
+            // when it fits a buffer, else the fixed parts it overlaps
+            std::vector<std::pair<int64_t, int64_t>> need;
+            if (hi_c >= 0 && carve_bytes(hi_c + 1 - lo_c, B.row_ptr[hi_c + 1] - B.row_ptr[lo_c], vb) <= inner_cap) {
+                need.push_back({(int64_t)lo_c, (int64_t)hi_c + 1});
+                stats.b_windows++;
+            } else {
+                for (size_t t = 0; t + 1 < p.b_cuts.size(); t++)
+                    if (hi_c >= 0 && p.b_cuts[t] <= hi_c && p.b_cuts[t + 1] > lo_c)
+                        need.push_back({p.b_cuts[t], p.b_cuts[t + 1]});
+                stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
+            }
             SG_CUDA(cudaStreamWaitEvent(s, ev[6 + slot], 0));
-            // stream the needed B parts, double buffered
+            // stream the needed rows of B, double buffered
             for (size_t u = 0; u < need.size(); u++, bcount++) {
                 const int bs = (int)(bcount & 1);
-                const size_t t = need[u];
+                const int64_t b0 = need[u].first, b1 = need[u].second;
+                Bb[bs] = carve(binner[bs], b1 - b0, vb, B.row_ptr[b1] - B.row_ptr[b0]);
                 if (bcount >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[2 + bs], 0));
-                stats.h2d += copy_rows_in(B, p.b_cuts[t], p.b_cuts[t + 1], vb, Bb[bs].rp, Bb[bs].col,
-                                          Bb[bs].val, si, &st);
+                stats.h2d += copy_rows_in(B, b0, b1, vb, Bb[bs].rp, Bb[bs].col, Bb[bs].val, si, &st);
                 SG_TRY(st);
                 SG_CUDA(cudaEventRecord(ev[bs], si));
                 SG_CUDA(cudaStreamWaitEvent(s, ev[bs], 0));
-                SG_TRY(fma(Ab[slot], rows, p.b_cuts[t], p.b_cuts[t + 1], Bb[bs], Cb[slot]));
+                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[bs], Cb[slot]));
                 SG_CUDA(cudaEventRecord(ev[2 + bs], s));
             }
             // the next A/C part comes in behind this part's B parts

@@ -244,7 +244,7 @@ struct ChunkEnv {
 struct ChunkStats {
     int algorithm = 0, branch = 0;
     int64_t n_ac = 0, n_b = 0, cost1 = 0, cost2 = 0, h2d = 0, d2h = 0, skipped_b = 0,
-            device_bytes = 0;
+            device_bytes = 0, b_windows = 0;
 };
 int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_csr &B,
                     spgemm_csr &C, size_t budget, ChunkStats &stats);

@@ -139,11 +139,13 @@ def test_chunked_alg2_bytes_match_formula(h):
     assert budget is not None
     ref, st = run_chunked(h, a, b, budget)
     assert st["algorithm"] == 2 and st["skipped_b_parts"] == 0
-    nac, nb = st["n_ac"], st["n_b"]
+    nac, nb, nw = st["n_ac"], st["n_b"], st["b_windows"]
     sa = CH.range_bytes(a.row_ptr, 0, a.nrows, 8)
     sb = CH.range_bytes(b.row_ptr, 0, b.nrows, 8)
     sc = CH.range_bytes(ref.row_ptr, 0, a.nrows, 8)
-    extra = 2 * 8 * (nac - 1) + 8 * (nb - 1) * nac
+    # parts of A whose rows of B came as one window (here all of B) copy B
+    # whole; the others copy its fixed parts, re-sending one offset per boundary
+    extra = 2 * 8 * (nac - 1) + 8 * (nb - 1) * (nac - nw)
     assert st["h2d_bytes"] + st["d2h_bytes"] == sa + sc + sb * nac + extra
 
 
@@ -155,7 +157,12 @@ def test_chunked_banded_skips_b_parts(h):
     budget, plan = find_budget(a.row_ptr, ref.row_ptr, a.row_ptr, 8, 2, 3, 4)
     assert budget is not None
     ref, st = run_chunked(h, a, a, budget)
-    assert st["algorithm"] == 2 and st["skipped_b_parts"] > 0
+    assert st["algorithm"] == 2 and (st["skipped_b_parts"] > 0 or st["b_windows"] > 0)
+    # fewer bytes of B than every part of A taking all of B
+    sa = CH.range_bytes(a.row_ptr, 0, a.nrows, 8)
+    sb = CH.range_bytes(a.row_ptr, 0, a.nrows, 8)
+    sc = CH.range_bytes(ref.row_ptr, 0, a.nrows, 8)
+    assert st["h2d_bytes"] + st["d2h_bytes"] < sa + sc + sb * st["n_ac"]
 
 
 def test_chunked_budget_errors(h):
