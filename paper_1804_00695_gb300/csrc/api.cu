@@ -80,7 +80,7 @@ struct spgemm_handle_s {
     void *arena = nullptr;
     size_t arena_cap = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};
     std::vector<int64_t> zeros;   // offsets of an empty C (chunked symbolic plan)
     int *host_mm = nullptr;       // pinned, column ranges of A parts (chunked numeric)
     ChunkStats cstats;
@@ -419,7 +419,7 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
     env.arena = h->arena;
     env.s_in = h->s_in;
     env.s_out = h->s_out;
-    for (int k = 0; k < 8; k++) env.ev[k] = h->ev[k];
+    for (int k = 0; k < 12; k++) env.ev[k] = h->ev[k];
     env.err = &h->dstate->err;
     env.zeros = &h->zeros;
     env.host_mm = h->host_mm;

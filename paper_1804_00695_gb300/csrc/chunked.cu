@@ -110,16 +110,27 @@ __device__ __forceinline__ void bitonic_kv(int *k, V *v, int P, int tid, int NT,
 // written back sorted, padded with -1.
 constexpr int FMA_WARP_CAP = 256, FMA_S = 512, FMA_WPB = 8;
 
+constexpr int FMA_E = 32;   // stored a_ik staged per batch
+template <typename V>
+struct FmaLayout {   // per warp: vals[FMA_S], keys[FMA_S], eq0[E], ea[E], pre[E+1]
+    static constexpr size_t per_warp =
+        ((size_t)FMA_S * (sizeof(V) + 4) + FMA_E * 8 + FMA_E * sizeof(V) + (FMA_E + 1) * 4 + 15) & ~(size_t)15;
+};
+
 template <typename V>
 __global__ void __launch_bounds__(256) k_fma_warp(
     int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const V *__restrict__ aval, int64_t lo, int64_t hi, const int64_t *__restrict__ brp,
     const int32_t *__restrict__ bcol, const V *__restrict__ bval, const int64_t *__restrict__ crp,
-    int32_t *__restrict__ ccol, V *__restrict__ cval, int *err) {
+    int32_t *__restrict__ ccol, V *__restrict__ cval, int *err, int fresh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    V *vals = (V *)smem_raw + w * FMA_S;
-    int *keys = (int *)((V *)smem_raw + FMA_WPB * FMA_S) + w * FMA_S;
+    unsigned char *base = smem_raw + (size_t)w * FmaLayout<V>::per_warp;
+    V *vals = (V *)base;
+    int *keys = (int *)(vals + FMA_S);
+    long long *eq0 = (long long *)(keys + FMA_S);
+    V *ea = (V *)(eq0 + FMA_E);
+    int *pre = (int *)(ea + FMA_E);
     int flag = 0;
     for (int64_t i = (int64_t)blockIdx.x * FMA_WPB + w; i < nrows; i += (int64_t)gridDim.x * FMA_WPB) {
         const int64_t c0 = crp[i];
@@ -153,22 +164,44 @@ __global__ void __launch_bounds__(256) k_fma_warp(
             if (cval) vals[s] = V(0);
         }
         __syncwarp();
-        for (int t = lane; t < cap; t += 32) {
-            const int c = ccol[c0 + t];
-            if (c >= 0 && !fma_insert<V>(keys, cval ? vals : nullptr, L, c, cval ? cval[c0 + t] : V(0)))
-                flag |= DERR_PROBE;
-        }
-        const int64_t pe = arp[i + 1];
-        for (int64_t p = arp[i]; p < pe; p++) {
-            const int64_t k = acol[p];
-            if (k < lo || k >= hi) continue;
-            const V av = aval ? aval[p] : V(0);
-            const int64_t q1 = brp[k - lo + 1];
-            for (int64_t q = brp[k - lo] + lane; q < q1; q += 32)
-                if (!fma_insert<V>(keys, cval ? vals : nullptr, L, bcol[q], cval ? av * bval[q] : V(0)))
+        if (!fresh) {   // the partial row of earlier parts of B
+            for (int t = lane; t < cap; t += 32) {
+                const int c = ccol[c0 + t];
+                if (c >= 0 && !fma_insert<V>(keys, cval ? vals : nullptr, L, c, cval ? cval[c0 + t] : V(0)))
                     flag |= DERR_PROBE;
+            }
         }
-        __syncwarp();
+        // the products of the stored a_ik in [lo, hi), dealt out over the 32
+        // lanes through prefix sums of nnz(B_k) (E stored entries at a time)
+        const int64_t ps = arp[i], pe = arp[i + 1];
+        for (int64_t pb = ps; pb < pe; pb += FMA_E) {
+            int len = 0;
+            if (pb + lane < pe) {
+                const int64_t k = acol[pb + lane];
+                if (k >= lo && k < hi) {
+                    eq0[lane] = brp[k - lo];
+                    len = (int)(brp[k - lo + 1] - brp[k - lo]);
+                    ea[lane] = aval ? aval[pb + lane] : V(0);
+                }
+            }
+            int incl = len;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            pre[lane] = incl - len;
+            if (lane == 31) pre[FMA_E] = incl;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            int e = 0;
+            for (int t = lane; t < total; t += 32) {
+                while (pre[e + 1] <= t) e++;
+                const int64_t q = eq0[e] + (t - pre[e]);
+                if (!fma_insert<V>(keys, cval ? vals : nullptr, L, bcol[q], cval ? ea[e] * bval[q] : V(0)))
+                    flag |= DERR_PROBE;
+            }
+            __syncwarp();
+        }
         // compact in place (read everything first), sort, write back
         constexpr int PER = FMA_S / 32;
         int kq[PER];
@@ -176,6 +209,8 @@ __global__ void __launch_bounds__(256) k_fma_warp(
 #pragma unroll
         for (int u = 0; u < PER; u++) {
             const int s = lane + 32 * u;
+            kq[u] = -1;
+            if (32 * u >= S) continue;
             kq[u] = s < S ? keys[s] : -1;
             vq[u] = (s < S && cval) ? vals[s] : V(0);
         }
@@ -183,6 +218,7 @@ __global__ void __launch_bounds__(256) k_fma_warp(
         int n = 0;
 #pragma unroll
         for (int u = 0; u < PER; u++) {
+            if (32 * u >= S) break;   // S is the warp's (one row per warp)
             const bool occ = kq[u] != -1;
             const unsigned m = __ballot_sync(0xffffffffu, occ);
             if (occ) {
@@ -654,8 +690,8 @@ static PartBuf carve(char *base, int64_t rows, int vb, int64_t nnz) {
 template <typename V>
 static int launch_fma(const PartBuf &A, int64_t nrows, int64_t lo, int64_t hi, const PartBuf &B,
                       const PartBuf &Cp, bool values, int64_t fma_blocks, int64_t slots, void *gws,
-                      int *err, Ctx &c) {
-    const size_t smem = (size_t)FMA_WPB * FMA_S * (sizeof(V) + 4);
+                      int *err, Ctx &c, bool fresh) {
+    const size_t smem = (size_t)FMA_WPB * FmaLayout<V>::per_warp;
     SG_CUDA(cudaFuncSetAttribute(k_fma_warp<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t blocks = (nrows + FMA_WPB - 1) / FMA_WPB;
     blocks = std::min<int64_t>(blocks, (int64_t)c.nsm * 16);
@@ -663,7 +699,8 @@ static int launch_fma(const PartBuf &A, int64_t nrows, int64_t lo, int64_t hi, c
         c.begin("chunked.fma", nrows);
         k_fma_warp<V><<<(unsigned)blocks, 256, smem, c.s>>>(
             nrows, A.rp, A.col, values ? (const V *)A.val : nullptr, lo, hi, B.rp, B.col,
-            values ? (const V *)B.val : nullptr, Cp.rp, Cp.col, values ? (V *)Cp.val : nullptr, err);
+            values ? (const V *)B.val : nullptr, Cp.rp, Cp.col, values ? (V *)Cp.val : nullptr, err,
+            fresh ? 1 : 0);
         c.end();
         SG_CUDA(cudaGetLastError());
     }
@@ -815,16 +852,19 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     const cudaStream_t si = env.s_in, so = env.s_out;
     cudaEvent_t *ev = env.ev;   // [0..1] copied-in, [2..3] compute done, [4..5] copied-out
     int *err = env.err;
+    // fresh: the C part holds no partial entries yet (first multiply-add of it)
     auto fma = [&](const PartBuf &Ap, int64_t rows, int64_t lo, int64_t hi, const PartBuf &Bp,
-                   const PartBuf &Cp) -> int {
+                   const PartBuf &Cp, bool fresh) -> int {
         return dtype == SPGEMM_F64
-                   ? launch_fma<double>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c)
-                   : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c);
+                   ? launch_fma<double>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, fresh)
+                   : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, fresh);
     };
     if (p.algorithm == 2) {
-        // ev: [0..1] B part in, [2..3] B part used, [4..5] C part out,
-        //     [6..7] A/C part in (by slot); column ranges come back through
-        //     pinned host memory, read once the part's copy has landed
+        // ev (by buffer slot): [0..1] rows of B in, [2..3] rows of B used,
+        // [4..5] C part out, [6..7] A part in (with its column range in
+        // pinned host memory), [8..9] C part ready, [10..11] A part used.
+        // An A buffer is reused once its products are done, a C buffer once
+        // its part has left the device, so neither waits for the other.
         const size_t nac = p.ac_cuts.size() - 1;
         int *hmm = env.host_mm;
         size_t bcount = 0;
@@ -832,20 +872,10 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             const int slot = (int)(j & 1);
             const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
             const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
-            // the part that used these buffers two steps ago has left the device
-            if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[4 + slot], 0));
+            if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[10 + slot], 0));
             stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st);
             SG_TRY(st);
-            // C starts empty: only its offsets come in
-            SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
-            stats.h2d += (rows + 1) * 8;
-            if (rows > 0)
-                k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, si>>>(Cb[slot].rp, rows + 1, C.row_ptr[r0]);
-            if (cn > 0) {
-                SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, si));
-                SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, si));
-            }
-            // column range of the A part decides which B parts it needs
+            // column range of the A part decides which rows of B it needs
             const int64_t an = A.row_ptr[r1] - A.row_ptr[r0];
             int *dmm = mm + 2 * slot;
             k_init_range<<<1, 1, 0, si>>>(dmm);
@@ -854,6 +884,17 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                     Ab[slot].col, an, dmm);
             SG_CUDA(cudaMemcpyAsync(hmm + 2 * slot, dmm, 8, cudaMemcpyDeviceToHost, si));
             SG_CUDA(cudaEventRecord(ev[6 + slot], si));
+            // C starts empty: only its offsets come in (behind the copy out of
+            // the part that used this buffer, on the same stream)
+            SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, so));
+            stats.h2d += (rows + 1) * 8;
+            if (rows > 0)
+                k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, so>>>(Cb[slot].rp, rows + 1, C.row_ptr[r0]);
+            if (cn > 0) {
+                SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, so));
+                SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, so));
+            }
+            SG_CUDA(cudaEventRecord(ev[8 + slot], so));
             return SPGEMM_OK;
         };
         if (nac > 0) SG_TRY(stage_ac(0));
@@ -878,6 +919,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
             }
             SG_CUDA(cudaStreamWaitEvent(s, ev[6 + slot], 0));
+            SG_CUDA(cudaStreamWaitEvent(s, ev[8 + slot], 0));
             // stream the needed rows of B, double buffered
             for (size_t u = 0; u < need.size(); u++, bcount++) {
                 const int bs = (int)(bcount & 1);
@@ -888,14 +930,14 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 SG_TRY(st);
                 SG_CUDA(cudaEventRecord(ev[bs], si));
                 SG_CUDA(cudaStreamWaitEvent(s, ev[bs], 0));
-                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[bs], Cb[slot]));
+                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[bs], Cb[slot], u == 0));
                 SG_CUDA(cudaEventRecord(ev[2 + bs], s));
             }
-            // the next A/C part comes in behind this part's B parts
+            SG_CUDA(cudaEventRecord(ev[10 + slot], s));   // A part used, C part complete
+            // the next A part comes in behind this part's rows of B
             if (j + 1 < nac) SG_TRY(stage_ac(j + 1));
             // finished part of C back to host memory
-            SG_CUDA(cudaEventRecord(ev[4 + slot], s));
-            SG_CUDA(cudaStreamWaitEvent(so, ev[4 + slot], 0));
+            SG_CUDA(cudaStreamWaitEvent(so, ev[10 + slot], 0));
             if (cn > 0) {
                 const int64_t p0 = C.row_ptr[r0];
                 SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[slot].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
@@ -938,7 +980,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 }
                 SG_CUDA(cudaEventRecord(ev[slot], si));
                 SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
-                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[0], Cb[slot]));
+                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[0], Cb[slot], t == 0));
                 SG_CUDA(cudaEventRecord(ev[2 + slot], s));
                 SG_CUDA(cudaStreamWaitEvent(so, ev[2 + slot], 0));
                 if (cn > 0) {

@@ -236,7 +236,7 @@ struct ChunkEnv {
     Ctx *ctx = nullptr;
     void *arena = nullptr;        // exactly the budget, device
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};
     int *err = nullptr;
     std::vector<int64_t> *zeros = nullptr;   // host scratch: offsets of an empty C
     int *host_mm = nullptr;                  // pinned: column ranges of two A parts
