@@ -1028,10 +1028,11 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
         return SPGEMM_ERR_BUDGET;
     }
     // A parts are double buffered (with their counts and the scan's scratch):
-    // shrink them until the pattern of B and two parts fit
+    // if two of them and the pattern of B do not fit, the parts of A are cut
+    // again, finer, with BinarySearch (the plan keeps B whole)
     int64_t max_rows = 0, max_nnz = 0;
     size_t part_bytes = 0;
-    for (int iter = 0; iter < 16; iter++) {
+    auto measure = [&]() {
         max_rows = max_nnz = 0;
         for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
             max_rows = std::max(max_rows, p.ac_cuts[j + 1] - p.ac_cuts[j]);
@@ -1039,13 +1040,21 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
         }
         part_bytes = r256((size_t)(max_rows + 1) * 8) + r256((size_t)std::max<int64_t>(max_nnz, 1) * 4) +
                      r256((size_t)(max_rows + 1) * 8) + r256(scan_tmp_bytes(max_rows));
-        if (raw_b + 2 * part_bytes + reserve + 8 * 256 <= budget) break;
-        fast = fast * 3 / 4;
-        SG_TRY(plan_chunks(A.row_ptr, A.nrows, zeros.data(), B.row_ptr, B.nrows, 0, 0, fast, p));
-        if (p.b_cuts.size() != 2 || iter == 15) {
+    };
+    measure();
+    const size_t fixed = raw_b + reserve + 8 * 256;
+    if (fixed >= budget) {
+        set_error("chunked symbolic: budget %zu too small for the pattern of B", budget);
+        return SPGEMM_ERR_BUDGET;
+    }
+    double limit = (double)(budget - fixed) / 2.0 * 0.8;
+    for (int iter = 0; fixed + 2 * part_bytes > budget; iter++) {
+        if (iter == 40 || limit < 64 || !cut_rows(A.row_ptr, zeros.data(), A.nrows, 0, limit, p.ac_cuts)) {
             set_error("chunked symbolic: budget %zu too small", budget);
             return SPGEMM_ERR_BUDGET;
         }
+        measure();
+        limit *= 0.85;
     }
     stats.algorithm = p.algorithm;
     stats.branch = p.branch;

@@ -196,3 +196,24 @@ def test_chunked_symbolic_compressed_and_fallbacks(h):
         rp_c, nnz = h.chunked_symbolic(sg.HostCsr.from_numpy(a), sg.HostCsr.from_numpy(bb), 1 << 26)
         assert nnz == ref.nnz
         assert np.array_equal(rp_c.numpy(), ref.row_ptr)
+
+
+def test_chunked_symbolic_tight_budget_recuts_a(h):
+    """A budget that holds the pattern of B but not two of Algorithm 4's A
+    parts: the parts of A are cut again, finer; counts still exact."""
+    a = I.laplace3d_27pt(20)
+    ref = oracle.spgemm(a, a)
+    A = sg.HostCsr.from_numpy(a)
+    raw_b = 8 * (a.nrows + 1) + 4 * a.nnz
+    hit = False
+    for budget in (int(raw_b * f) for f in (1.35, 1.45, 1.6, 1.8, 2.2)):
+        try:
+            rp, nnz = h.chunked_symbolic(A, A, budget)
+        except sg.SpgemmError as e:
+            assert e.status == 5
+            continue
+        assert nnz == ref.nnz and np.array_equal(rp.numpy(), ref.row_ptr)
+        st = h.chunked_stats()
+        assert st["device_bytes"] <= budget
+        hit = hit or st["n_ac"] >= 3
+    assert hit
