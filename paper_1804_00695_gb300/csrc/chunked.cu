@@ -108,7 +108,7 @@ __device__ __forceinline__ void bitonic_kv(int *k, V *v, int P, int tid, int NT,
 // the products of the stored a_ik with lo <= k < hi (other columns of A are
 // skipped; they need not be sorted) are merged in a shared-memory map, then
 // written back sorted, padded with -1.
-constexpr int FMA_WARP_CAP = 256, FMA_S = 512, FMA_WPB = 8;
+constexpr int FMA_WARP_CAP = 256, FMA_S = 512, FMA_WPB = 8, FMA_BMAP = 64, FMA_BMAP_L = 6;
 
 constexpr int FMA_E = 32;   // stored a_ik staged per batch
 template <typename V>
@@ -232,17 +232,93 @@ __global__ void __launch_bounds__(256) k_fma_warp(
             flag |= DERR_COUNT;
             n = cap;
         }
-        if (final_pass) {
+        __syncwarp();
+        bool written = false;
+        if (final_pass && n <= FMA_WARP_CAP && cval) {
+            // Sorted write through the row's 32-column blocks (the compressed
+            // form of Section 2.1): the blocks of the n columns go into a small
+            // map (in the free upper half of keys[]), only the blocks are
+            // sorted, and a column's place is the number of columns in smaller
+            // blocks plus the popcount of its block's mask below it.
+            int *bk = keys + FMA_S / 2;                    // block keys
+            unsigned *bm = (unsigned *)(bk + FMA_BMAP);    // block masks
+            int *bf = (int *)(bm + FMA_BMAP);              // first place of the block
+            int *bx = bf + FMA_BMAP;                       // blocks, sorted
+            for (int u = lane; u < FMA_BMAP; u += 32) {
+                bk[u] = -1;
+                bm[u] = 0;
+            }
+            __syncwarp();
+            bool ok = true;
+            for (int e = lane; e < n; e += 32) {
+                const int c = keys[e];
+                ok &= sym_insert(bk, bm, FMA_BMAP_L, c >> 5, 1u << (c & 31));
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            __syncwarp();
+            if (ok) {
+                int nb = 0;
+#pragma unroll
+                for (int u = 0; u < FMA_BMAP / 32; u++) {
+                    const int k = bk[lane + 32 * u];
+                    const bool occ = k != -1;
+                    const unsigned m = __ballot_sync(0xffffffffu, occ);
+                    if (occ) bx[nb + __popc(m & ((1u << lane) - 1))] = k;
+                    nb += __popc(m);
+                }
+                int PB = 1;
+                while (PB < nb) PB <<= 1;
+                for (int e = nb + lane; e < PB; e += 32) bx[e] = INT_MAX;
+                __syncwarp();
+                bitonic_kv<int>(bx, nullptr, PB, lane, 32, [] { __syncwarp(); });
+                // first place of each block: popcounts of the blocks before it
+                int run = 0;
+                for (int j0 = 0; j0 < nb; j0 += 32) {
+                    const int j = j0 + lane;
+                    unsigned h = 0;
+                    int pc = 0;
+                    if (j < nb) {
+                        h = hash_slot(bx[j], FMA_BMAP_L);
+                        for (int g = 0; g < FMA_BMAP && bk[h] != bx[j]; g++) h = (h + 1) & (FMA_BMAP - 1);
+                        pc = __popc(bm[h]);
+                    }
+                    int incl = pc;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d) incl += y;
+                    }
+                    if (j < nb) bf[h] = run + incl - pc;
+                    run += __shfl_sync(0xffffffffu, incl, 31);
+                }
+                __syncwarp();
+                for (int e = lane; e < n; e += 32) {
+                    const int c = keys[e], blk = c >> 5;
+                    unsigned h = hash_slot(blk, FMA_BMAP_L);
+                    for (int g = 0; g < FMA_BMAP && bk[h] != blk; g++) h = (h + 1) & (FMA_BMAP - 1);
+                    const int place = bf[h] + __popc(bm[h] & ((1u << (c & 31)) - 1));
+                    ccol[c0 + place] = c;
+                    cval[c0 + place] = vals[e];
+                }
+                for (int e = n + lane; e < cap; e += 32) {
+                    ccol[c0 + e] = -1;
+                    cval[c0 + e] = V(0);
+                }
+                written = true;
+            }
+        }
+        if (!written && final_pass) {
             int P = 1;
             while (P < n) P <<= 1;
             for (int e = n + lane; e < P; e += 32) keys[e] = INT_MAX;
             __syncwarp();
             bitonic_kv<V>(keys, cval ? vals : nullptr, P, lane, 32, [] { __syncwarp(); });
+            __syncwarp();
         }
-        __syncwarp();
-        for (int e = lane; e < cap; e += 32) {
-            ccol[c0 + e] = e < n ? keys[e] : -1;
-            if (cval) cval[c0 + e] = e < n ? vals[e] : V(0);
+        if (!written) {
+            for (int e = lane; e < cap; e += 32) {
+                ccol[c0 + e] = e < n ? keys[e] : -1;
+                if (cval) cval[c0 + e] = e < n ? vals[e] : V(0);
+            }
         }
         __syncwarp();
     }
