@@ -459,20 +459,15 @@ __global__ void __launch_bounds__(BS) k_sym_bitmap(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
-    int64_t *__restrict__ crp, int64_t nwords, unsigned *gbits, bool use_summ) {
-    // dynamic shared memory: the summary (one bit per bitmap word, when used),
-    // then the bitmap itself unless it lives in global memory (gbits)
+    int64_t *__restrict__ crp, int64_t nwords, unsigned *gbits) {
     extern __shared__ unsigned sbits[];
     __shared__ long long red[BS / 32];
-    const int64_t nsum = use_summ ? (nwords + 31) / 32 : 0;
-    unsigned *summ = sbits;
-    unsigned *bits = gbits ? gbits + (size_t)blockIdx.x * (size_t)nwords : sbits + nsum;
+    unsigned *bits = gbits ? gbits + (size_t)blockIdx.x * (size_t)nwords : sbits;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t s = threadIdx.x; s < nwords; s += BS) bits[s] = 0;
-    for (int64_t s = threadIdx.x; s < nsum; s += BS) summ[s] = 0;
-    __syncthreads();
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
         const int i = rows[t];
+        for (int64_t s = threadIdx.x; s < nwords; s += BS) bits[s] = 0;
+        __syncthreads();
         const int64_t pe = arp[i + 1];
         for (int64_t p = arp[i] + w; p < pe; p += BS / 32) {
             const int k = acol[p];
@@ -480,31 +475,12 @@ __global__ void __launch_bounds__(BS) k_sym_bitmap(
             const int n = ccnt[k];
             for (int q = lane; q < n; q += 32) {
                 int2 pr = pairs[q0 + q];
-                if (atomicOr(&bits[pr.x], (unsigned)pr.y) == 0 && use_summ)
-                    atomicOr(&summ[pr.x >> 5], 1u << (pr.x & 31));
+                atomicOr(&bits[pr.x], (unsigned)pr.y);
             }
         }
         __syncthreads();
-        // count, leaving the bitmap (and the summary) zero for the next row:
-        // with a summary only the touched words are visited
         long long c = 0;
-        if (use_summ) {
-            for (int64_t y = threadIdx.x; y < nsum; y += BS) {
-                unsigned sw = summ[y];
-                while (sw) {
-                    const int64_t x = y * 32 + __ffs(sw) - 1;
-                    sw &= sw - 1;
-                    c += __popc(bits[x]);
-                    bits[x] = 0;
-                }
-                summ[y] = 0;
-            }
-        } else {
-            for (int64_t s = threadIdx.x; s < nwords; s += BS) {
-                c += __popc(bits[s]);
-                bits[s] = 0;
-            }
-        }
+        for (int64_t s = threadIdx.x; s < nwords; s += BS) c += __popc(bits[s]);
         for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
         if (lane == 0) red[w] = c;
         __syncthreads();
@@ -518,7 +494,7 @@ __global__ void __launch_bounds__(BS) k_sym_bitmap(
 }
 
 constexpr int BITMAP_BS = 512;
-constexpr int64_t SMEM_BITMAP_WORDS = 53248;  // 208 KiB of shared memory (plus its 1/32 summary)
+constexpr int64_t SMEM_BITMAP_WORDS = 53248;  // 208 KiB of shared memory
 
 size_t symbolic_global_ws(int64_t ncols_b, int nsm) {
     int64_t nwords = (ncols_b + 31) / 32;
@@ -635,9 +611,7 @@ int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
             default: {
                 int64_t nwords = (B.ncols + 31) / 32;
                 bool shared = nwords <= SMEM_BITMAP_WORDS;
-                const int64_t nsum = (nwords + 31) / 32;
-                const bool use_summ = nsum <= 16384;   // summary in shared memory
-                size_t smem = (use_summ ? (size_t)nsum * 4 : 0) + (shared ? (size_t)nwords * 4 : 0);
+                size_t smem = shared ? (size_t)nwords * 4 : 0;
                 SG_TRY(prep(k_sym_bitmap<BITMAP_BS>, smem));
                 int64_t blocks = cnt < (int64_t)nsm ? cnt : (int64_t)nsm;
                 if (!shared && gws_bytes < (size_t)blocks * (size_t)nwords * 4) {
@@ -647,7 +621,7 @@ int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
                 c.begin(SYM_LABEL[b], cnt);
                 k_sym_bitmap<BITMAP_BS><<<(unsigned)blocks, BITMAP_BS, smem, c.s>>>(
                     A.row_ptr, A.col_idx, brp, ccnt, pairs, r, cnt, crp, nwords,
-                    shared ? nullptr : (unsigned *)gws, use_summ);
+                    shared ? nullptr : (unsigned *)gws);
                 c.end();
                 SG_CUDA(cudaGetLastError());
             }
