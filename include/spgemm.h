@@ -113,12 +113,14 @@ SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr 
                    const spgemm_csr *B, spgemm_csr *C, void *stream);
 
 /* Options of a handle.
- *  SPGEMM_OPT_F64_NATIVE (0/1, default 0): FP64 products are accumulated as
- *    double-words (a pair of floats, 48 significand bits) in the FP32 units,
- *    which meets |c - c_exact| <= (7 + 5n) 2^-48 sum|a_ik||b_kj| for an entry
- *    with n terms; rows whose inputs lie outside [2^-60, 2^60] in magnitude
- *    (zeros excepted) and rows wider than 128 entries accumulate in native
- *    FP64.  1 = native FP64 everywhere.
+ *  SPGEMM_OPT_F64_NATIVE (0/1, default 1): 1 = FP64 products and sums in
+ *    native FP64.  0 = double-word accumulation in the FP32 units (pairs of
+ *    floats, 48 significand bits, three levels where several lanes add to
+ *    one entry), within 1e-12 sum|a_ik||b_kj| of the exact entry; rows of A
+ *    (or, for B, the whole call) with a non-zero value outside [2^-32, 2^32)
+ *    in magnitude accumulate natively.  Native is the faster of the two on
+ *    GB300 for the kernels measured (their time goes to latency, not to the
+ *    FP64 units); the chunked calls always accumulate natively.
  *  SPGEMM_OPT_LANES_NUMERIC / SPGEMM_OPT_LANES_SYMBOLIC (0, 4, 8, 16, 32;
  *    default 0 = from the mean products per row): lanes that share a row in
  *    the kernels for rows with few outputs (a warp holds 32/lanes rows).

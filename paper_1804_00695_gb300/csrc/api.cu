@@ -73,7 +73,7 @@ struct spgemm_handle_s {
     int64_t max_alen = 0;     // longest row of A
     int small_cap = 32, slot_factor = 2;
     // options
-    bool f64_native = false;
+    bool f64_native = true;
     int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from the mean products per row)
     double mean_flops = 0;
     // chunked calls: budget arena, side streams, events, last statistics

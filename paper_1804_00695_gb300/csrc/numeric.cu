@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
     float *hi = (float *)reg;
     float *lo = hi + SMAX;
     float *lo2 = lo + SMAX;
+    double *dv = (double *)reg;   // native FP64 slots (hi and lo together)
     int *keys = (int *)(lo2 + SMAX);
     long long *eq0 = (long long *)(keys + SMAX);
     double *ea = (double *)(eq0 + E);
@@ -239,9 +240,13 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             const int sidx = gl + t * G;
             if (t * G >= S) break;   // only the row's 2^L slots are used
             keys[sidx] = -1;
-            hi[sidx] = 0.f;
-            lo[sidx] = 0.f;
-            lo2[sidx] = 0.f;
+            if (MODE == MODE_F64) {
+                dv[sidx] = 0.0;      // native FP64: one double per slot over hi|lo
+            } else {
+                hi[sidx] = 0.f;
+                lo[sidx] = 0.f;
+                lo2[sidx] = 0.f;
+            }
         }
         // rows with an A value outside the double-word range accumulate natively
         bool nat = MODE == MODE_F64 || b_bad;
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             nat = ((bad >> gbase) & lmask) != 0;
         }
         const int maxlen = __reduce_max_sync(0xffffffffu, plen);
-        bool wnat = MODE == MODE_F64, three = false;
+        bool wnat = false, three = false;
         for (int pb = 0; pb < maxlen; pb += E) {
             // stage entries [pb, pb+E): lane gl takes EL consecutive entries
             int cnt[EL];
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
                 // warps without native rows add with atomics (three levels for
                 // double-words); a warp holding a native row merges same-slot
                 // lanes with __match_any_sync and adds in turns
-                wnat = MODE == MODE_F64 || __any_sync(0xffffffffu, nat);
+                wnat = MODE == MODE_DW && __any_sync(0xffffffffu, nat);
                 three = !wnat || plen > DW2_MAX_TERMS;
             }
             // exclusive scan of the lanes' sums within the row's group
@@ -349,6 +354,8 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
                     if (slot >= 0) {
                         if (MODE == MODE_F32) {
                             atomicAdd(&hi[slot], px);
+                        } else if (MODE == MODE_F64) {
+                            atomicAdd(&dv[slot], __hiloint2double(__float_as_int(py), __float_as_int(px)));
                         } else {
                             float s1, e1, tt, f, s2, e2;
                             const float o1 = atomicAdd(&hi[slot], px);
@@ -386,9 +393,15 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             kq[t] = -1;
             if (t * G >= smax_w) continue;
             kq[t] = sidx < S ? keys[sidx] : -1;
-            hq[t] = hi[sidx];
-            lq[t] = lo[sidx];
-            l2q[t] = lo2[sidx];
+            if (MODE == MODE_F64) {
+                const double d = dv[sidx];
+                hq[t] = __int_as_float(__double2loint(d));
+                lq[t] = __int_as_float(__double2hiint(d));
+            } else {
+                hq[t] = hi[sidx];
+                lq[t] = lo[sidx];
+                l2q[t] = lo2[sidx];
+            }
         }
         __syncwarp();
         int cntr = 0;
@@ -400,9 +413,13 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             if (occ) {
                 const int pos = cntr + __popc(m & ((1u << gl) - 1));
                 keys[pos] = kq[t];
-                hi[pos] = hq[t];
-                lo[pos] = lq[t];
-                lo2[pos] = l2q[t];
+                if (MODE == MODE_F64) {
+                    dv[pos] = __hiloint2double(__float_as_int(lq[t]), __float_as_int(hq[t]));
+                } else {
+                    hi[pos] = hq[t];
+                    lo[pos] = lq[t];
+                    lo2[pos] = l2q[t];
+                }
             }
             cntr += __popc(m);
         }
@@ -420,6 +437,8 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             a.ccol[out + r] = key;
             if (MODE == MODE_F32)
                 ((float *)a.cval)[out + r] = hi[e];
+            else if (MODE == MODE_F64)
+                ((double *)a.cval)[out + r] = dv[e];
             else if (MODE == MODE_DW && !nat)
                 ((double *)a.cval)[out + r] = three ? dw3_to_double(hi[e], lo[e], lo2[e])
                                                     : dw_to_double(hi[e], lo[e]);

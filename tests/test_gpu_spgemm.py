@@ -123,9 +123,9 @@ def test_every_bin_both_phases(h, ncols):
     assert all(sym[b] > 0 for b in range(1, 7)), sym
     c = run(h, a, eye, np.float32)
     assert_matches(c, oracle_product(a, eye, np.float32), "f32")
-    h.set_option(sg.OPT_F64_NATIVE, 1)
+    h.set_option(sg.OPT_F64_NATIVE, 0)   # double-word accumulation
     c = run(h, a, eye)
-    h.set_option(sg.OPT_F64_NATIVE, 0)
+    h.set_option(sg.OPT_F64_NATIVE, 1)
     assert_matches(c, oracle.spgemm(a, eye), "f64")
 
 
@@ -142,7 +142,7 @@ def test_lane_options_galerkin(h, native, lanes):
             c = run(h, x, y)
             assert_matches(c, oracle.spgemm(x, y), "f64")
     finally:
-        h.set_option(sg.OPT_F64_NATIVE, 0)
+        h.set_option(sg.OPT_F64_NATIVE, 1)
         h.set_option(sg.OPT_LANES_NUMERIC, 0)
         h.set_option(sg.OPT_LANES_SYMBOLIC, 0)
 
@@ -156,13 +156,17 @@ def test_double_word_range_fallback(h, shape):
     a = I.random_csr(m, k, dens, 31)
     b = I.random_csr(k, n, dens, 32)
     av = a.val.copy()
-    av[::7] *= 1e-30      # below 2^-60: those rows go native
+    av[::7] *= 1e-30      # below 2^-32: those rows go native
     bv = b.val.copy()
-    for scale_b in (1.0, 1e25):   # 1e25 > 2^60: the whole call goes native
-        a2 = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, av)
-        b2 = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, bv * scale_b)
-        c = run(h, a2, b2)
-        assert_matches(c, oracle.spgemm(a2, b2), "f64")
+    h.set_option(sg.OPT_F64_NATIVE, 0)   # double-word accumulation
+    try:
+        for scale_b in (1.0, 1e25):   # 1e25 > 2^32: the whole call goes native
+            a2 = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, av)
+            b2 = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, bv * scale_b)
+            c = run(h, a2, b2)
+            assert_matches(c, oracle.spgemm(a2, b2), "f64")
+    finally:
+        h.set_option(sg.OPT_F64_NATIVE, 1)
 
 
 @pytest.mark.parametrize("shuffle", [False, True])
@@ -212,7 +216,7 @@ def test_medium_rows_every_span(h, ncols, small_cap):
             assert_matches(c, oracle_product(a, b, dt), tag)
         labels = set(h.timings())
     finally:
-        h.set_option(sg.OPT_F64_NATIVE, 0)
+        h.set_option(sg.OPT_F64_NATIVE, 1)
         h.set_option(sg.OPT_SMALL_CAP, 32)
         h.set_timing(False)
     sym, num = h.bin_counts()
@@ -261,12 +265,12 @@ def test_edge_cases(h):
     assert_matches(c, oracle.spgemm(a, b1), "f64")
     # A * I = A (sorted): exact in native FP64, within tolerance as double-words
     eye = I.Csr(30, 30, np.arange(31, dtype=np.int64), np.arange(30, dtype=np.int32), np.ones(30))
+    h.set_option(sg.OPT_F64_NATIVE, 0)
     c = run(h, a, eye)
+    h.set_option(sg.OPT_F64_NATIVE, 1)
     assert np.array_equal(c.col.cpu().numpy(), a.col)
     assert np.all(np.abs(c.val.cpu().numpy() - a.val) <= 1e-12 * np.abs(a.val))
-    h.set_option(sg.OPT_F64_NATIVE, 1)
     c = run(h, a, eye)
-    h.set_option(sg.OPT_F64_NATIVE, 0)
     assert np.array_equal(c.col.cpu().numpy(), a.col) and np.array_equal(c.val.cpu().numpy(), a.val)
     # explicit zeros stay in the pattern
     az = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.zeros(a.nnz))
