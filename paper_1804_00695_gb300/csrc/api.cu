@@ -373,7 +373,7 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     h->lastB = *B;
     h->lastC = *C;
     NumTune tune;
-    tune.G = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 40.0);
+    tune.G = h->g_numeric ? h->g_numeric : lanes_for(h->mean_flops / 80.0);
     tune.small_cap = h->small_cap;
     tune.slot_factor = h->slot_factor;
     const int first_list = tune.small_cap >= 32 ? 3 : 2;
