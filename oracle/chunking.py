@@ -12,16 +12,16 @@ Readings taken where the paper leaves details open:
     the longest run of rows, starting where the previous part ended, whose
     size does not exceed pSize (found by bisection on the cumulative sizes).
     A single row larger than pSize is a budget error.
-  * "Find the balanced partition size" for a portion: np = ceil(size / portion)
+  * the balanced part size of a portion: np = ceil(size / portion)
     parts, pSize = size / np.
-  * "Add left over from big to small portion": small += big - used, where used
+  * the leftover of the large portion goes to the small one: small += big - used, where used
     is the size of the operand placed whole (branches 1 and 2) or of the
     largest part cut from the big portion (branches 3 and 4).
   * Branch 1 calls Algorithm 3 (B in place) and branch 2 Algorithm 2 (A and C
     in place), as written; branches 3 and 4 take the algorithm with the lower
     copy cost, Algorithm 2 on a tie.
-  * Line "we use the rest for C" in the text describing Algorithm 2 is read as
-    "the rest for B".
+  * Where the text describing Algorithm 2 gives the rest of the fast memory to
+    C, it is read as giving it to B (A and C already have the large portion).
 """
 from __future__ import annotations
 

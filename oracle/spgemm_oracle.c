@@ -13,7 +13,7 @@
  * of A of a_ik times row k of B, with rows of A processed one after another
  * and each row of B read through in stored order (Section 2.1, Figure 1).
  * The symbolic phase counts the distinct columns of each row of C and the
- * numeric phase produces the values (Section 2.1, "two-phase").
+ * numeric phase produces the values (the two phases of Section 2.1).
  *
  * The accumulator is the dense accumulator that Section 3.1 contrasts with
  * the hashmap accumulator: a value array and a marker array as long as the

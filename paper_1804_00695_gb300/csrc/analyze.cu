@@ -7,17 +7,17 @@ namespace sg {
 
 // ---------------------------------------------------------------- compression
 // One thread per row of M: consecutive stored columns that fall in the same
-// 32-column block are merged into one (block, mask) pair (Section 2.1,
-// "compression ... encode multiple columns ... with fewer integers").  Rows
-// need not be sorted; a sorted row yields one pair per block, ascending.
-// The row's descriptors are written alongside: desc = {first entry (int64),
-// entries, pairs} for the product kernels and ana = {entries, pairs, first
-// block, last block} for the analysis, so each later visit of row k costs
-// one 16-byte load.
+// 32-column block are merged into one (block, mask) pair, so that a set of
+// columns is held in fewer integers and unions become bitwise ORs (the
+// compression of Section 2.1).  Rows need not be sorted; a sorted row yields
+// one pair per block, ascending.  The row's descriptors are written
+// alongside: desc = {first entry (int64), entries, pairs} for the product
+// kernels, ana = {entries, pairs} for the analysis, and the row's first and
+// last block (minmax) for the span tests.
 __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
                            const int32_t *__restrict__ col, int2 *__restrict__ pairs,
                            int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
-                           int4 *__restrict__ desc, int4 *__restrict__ ana, int *err,
+                           int4 *__restrict__ desc, int2 *__restrict__ ana, int *err,
                            int *unsorted_flag) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
@@ -50,13 +50,13 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
     if (minmax) minmax[r] = make_int2(bmin, bmax);
     const int len = (int)(end - beg);
     if (desc) desc[r] = make_int4((int)(unsigned)(uint64_t)beg, (int)((uint64_t)beg >> 32), len, n);
-    if (ana) ana[r] = make_int4(len, n, bmin, bmax);
+    if (ana) ana[r] = make_int2(len, n);
     if (bad) atomicOr(err, DERR_COL_RANGE);
     if (unsorted && unsorted_flag) atomicOr(unsorted_flag, 1);
 }
 
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
-                    int4 *ana, int *err, Ctx &c, int *unsorted) {
+                    int2 *ana, int *err, Ctx &c, int *unsorted) {
     if (M.nrows == 0) return SPGEMM_OK;
     int64_t blocks = (M.nrows + 255) / 256;
     c.begin("compress", M.nrows);
@@ -80,15 +80,15 @@ __device__ __forceinline__ void warp_hist(unsigned long long *hist, bool has, in
 }
 
 // Eight lanes per row of A.  For row i: flops_i = sum_k nnz(B_k) (the number
-// of accumulator insertions, Section 3.1), cpairs_i = sum_k pairs(B_k), and
-// the span of compressed blocks the row can reach.  The symbolic
-// accumulator needs at most min(cpairs_i, span_i, ceil(ncols/32)) keys.
+// of accumulator insertions, Section 3.1) and cpairs_i = sum_k pairs(B_k).
+// The symbolic accumulator needs at most min(cpairs_i, ceil(ncols/32)) keys
+// (the second pass narrows rows down by their column span itself).
 // Empty rows get their count (0) here; rows for the dense bitmap (bin 6)
 // are marked -1 for the second pass.
 constexpr int AN_G = 8;
 __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
                           const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
-                          const int4 *__restrict__ ana, int64_t *__restrict__ flops,
+                          const int2 *__restrict__ ana, int64_t *__restrict__ flops,
                           uint8_t *__restrict__ bins, int64_t *__restrict__ crp, DevState *st) {
     __shared__ unsigned long long hist[NBINS];
     __shared__ unsigned long long fsum;
@@ -101,33 +101,25 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / AN_G;
     bool live = i < nrows;
     long long f = 0, cp = 0;
-    int bmin = INT_MAX, bmax = INT_MIN;
     bool bad = false;
     if (live) {
         for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += AN_G) {
             int k = acol[p];
             if (k < 0 || (int64_t)k >= nrows_b) { bad = true; continue; }
-            const int4 d = ana[k];
+            const int2 d = ana[k];
             f += d.x;
             cp += d.y;
-            bmin = min(bmin, d.z);
-            bmax = max(bmax, d.w);
         }
     }
     for (int d = AN_G / 2; d > 0; d >>= 1) {
         f += __shfl_xor_sync(gmask, f, d, AN_G);
         cp += __shfl_xor_sync(gmask, cp, d, AN_G);
-        bmin = min(bmin, __shfl_xor_sync(gmask, bmin, d, AN_G));
-        bmax = max(bmax, __shfl_xor_sync(gmask, bmax, d, AN_G));
     }
     if (bad) atomicOr(&st->err, DERR_COL_RANGE);
     int b = BIN_EMPTY;
     const bool lead = live && lane == 0;
     if (lead) {
-        long long keys = cp;
-        if (bmax >= bmin) keys = min(keys, (long long)(bmax - bmin) + 1);
-        else keys = 0;
-        keys = min(keys, (long long)nwords);
+        const long long keys = min(cp, (long long)nwords);
         b = sym_bin(keys, cp);
         flops[i] = f;
         bins[i] = (uint8_t)b;
@@ -155,7 +147,7 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
     }
 }
 
-int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int4 *ana, int64_t *flops,
+int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int2 *ana, int64_t *flops,
                    uint8_t *bins, int64_t *crp, DevState *st, Ctx &c) {
     if (A.nrows == 0) return SPGEMM_OK;
     int64_t threads = A.nrows * AN_G;

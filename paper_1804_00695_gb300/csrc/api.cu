@@ -272,7 +272,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         const size_t o_rows = align_up((size_t)n);
         const size_t o_desc = o_rows + align_up((size_t)n * 4);
         const size_t o_ana = ws_persist(n, B->nrows);
-        const size_t o_flops = o_ana + align_up((size_t)B->nrows * 16);
+        const size_t o_flops = o_ana + align_up((size_t)B->nrows * 8);
         const size_t o_pairs = o_flops + align_up((size_t)n * 8);
         const size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
         const size_t o_mm = o_desc + align_up((size_t)B->nrows * 16);   // persistent, after desc
@@ -288,7 +288,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         int32_t *ccnt = (int32_t *)(w + o_ccnt);
         int2 *minmax = (int2 *)(w + o_mm);
         int4 *desc = (int4 *)(w + o_desc);
-        int4 *ana = (int4 *)(w + o_ana);
+        int2 *ana = (int2 *)(w + o_ana);
         Ctx c = h->ctx(s);
         // lanes per row from the mean number of compressed pairs a row visits
         const double mean_pairs = (double)A->nnz / (double)n *

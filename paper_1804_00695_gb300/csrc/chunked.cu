@@ -1,5 +1,5 @@
 // Multi-memory chunking of Section 3.3.1: operands in host memory are moved
-// through a fixed device budget ("fast memory") in row parts chosen by
+// through a fixed device budget (the fast memory) in row parts chosen by
 // Algorithm 4, and multiplied part by part with the row-range fused
 // multiply-add of Section 3.2.2: C2_i = sum over stored a_ik with k in the B
 // part's row range of a_ik * B_k, plus the partial row C1_i already held.

@@ -145,10 +145,10 @@ struct Ctx {
 // pairs[M.row_ptr[k] .. M.row_ptr[k] + ccnt[k]), each {block, mask};
 // minmax[k] = {first block, last block} ({INT_MAX, INT_MIN} for empty rows);
 // desc[k] = {row_ptr[k] low, high 32 bits, entries, pairs};
-// ana[k] = {entries, pairs, first block, last block}.  Any output may be NULL.
+// ana[k] = {entries, pairs}.  Any output may be NULL.
 // `unsorted` (may be null) is set to 1 if a row of M is not strictly ascending.
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
-                    int4 *ana, int *err, Ctx &c, int *unsorted = nullptr);
+                    int2 *ana, int *err, Ctx &c, int *unsorted = nullptr);
 __device__ __forceinline__ int64_t desc_start(int4 d) {
     return (int64_t)(((uint64_t)(unsigned)d.y << 32) | (uint64_t)(unsigned)d.x);
 }
@@ -157,7 +157,7 @@ size_t scan_tmp_bytes(int64_t n);
 // (x[0] = 0); *total (device) = x[n].
 int launch_scan_counts(int64_t *x, int64_t n, long long *total, void *tmp, Ctx &c);
 // Per row i of A: flops, symbolic bin; empty rows get crp[i+1] = 0.
-int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int4 *ana, int64_t *flops,
+int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int2 *ana, int64_t *flops,
                    uint8_t *bins, int64_t *crp, DevState *st, Ctx &c);
 // Numeric bin of every row from its output count crp[i+1]-crp[i] and flops.
 int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, uint8_t *bins,

@@ -3,8 +3,8 @@
 // phase) and their products:
 //
 // * bins 1-2 (<= 32 outputs): groups of G lanes per row, a shared-memory
-//   hash map from column to value per row (Section 2.1, "sparse
-//   hashmap-based accumulators"), products dealt evenly over the lanes;
+//   hash map from column to value per row (the sparse hash accumulators of
+//   Section 2.1), products dealt evenly over the lanes;
 // * bins 3-4 (<= 1024 outputs): a warp per row with a dense rank
 //   accumulator over the row's column span (bitmap, prefix counts, values
 //   by rank) when the span is at most 2048 blocks of 32 columns (three

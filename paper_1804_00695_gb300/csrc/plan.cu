@@ -10,9 +10,10 @@
 //  - BinarySearch cuts greedily from the top: each part is the longest run of
 //    rows from the previous cut whose size does not exceed pSize (bisection
 //    on the cumulative sizes); a row larger than pSize is a budget error.
-//  - "balanced partition size" for a portion: np = ceil(size/portion) parts,
+//  - the balanced part size of a portion: np = ceil(size/portion) parts,
 //    pSize = size/np.
-//  - "Add left over from big to small portion": small += big - used, used =
+//  - the leftover of the large portion goes to the small one:
+//    small += big - used, used =
 //    the operand placed whole (branches 1, 2) or the largest part cut from
 //    the big portion (branches 3, 4).
 //  - Branch 1 calls Algorithm 3 and branch 2 Algorithm 2 as written;
