@@ -279,10 +279,12 @@ class Handle:
         return cnt, pairs
 
     # -- chunked product, operands in (pinned) host memory ----------------------
-    def chunked_symbolic(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None):
-        """Row offsets of C (host int64 tensor, pinned) and nnz(C)."""
+    def chunked_symbolic(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None, out=None):
+        """Row offsets of C (host int64 tensor, pinned; `out` if given) and nnz(C)."""
         torch = _torch()
-        rp = torch.empty(A.nrows + 1, dtype=torch.int64).pin_memory()
+        rp = out if out is not None else torch.empty(A.nrows + 1, dtype=torch.int64).pin_memory()
+        if rp.dtype != torch.int64 or rp.numel() != A.nrows + 1 or rp.device.type != "cpu":
+            raise ValueError("out must be a host int64 tensor of nrows(A) + 1 entries")
         nnz = C.c_int64()
         da, db = A.desc(), B.desc()
         _check(_lib.spgemm_chunked_symbolic(self._h, C.byref(da), C.byref(db), rp.data_ptr(),
@@ -300,6 +302,7 @@ class Handle:
         _check(_lib.spgemm_chunked_numeric(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc),
                                            budget, _stream(stream)))
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        self.check(stream)
         return Cm
 
     def chunked_numeric_into(self, A: "HostCsr", B: "HostCsr", Cm: "HostCsr", budget: int, stream=None):
@@ -309,6 +312,7 @@ class Handle:
                                            budget, _stream(stream)))
         torch = _torch()
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        self.check(stream)
 
     def chunked(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None) -> "HostCsr":
         rp, nnz = self.chunked_symbolic(A, B, budget, stream)

@@ -84,6 +84,7 @@ struct spgemm_handle_s {
     std::vector<int64_t> zeros;   // offsets of an empty C (chunked symbolic plan)
     int *host_mm = nullptr;       // pinned, column ranges of A parts (chunked numeric)
     ChunkStats cstats;
+    ChunkCache ccache;            // recorded by the last chunked symbolic call
     float chunk_ms = 0;
     // batched calls: stacked operands and the instance table
     char *bws = nullptr;
@@ -164,6 +165,11 @@ static int device_errors(int err) {
     if (err & DERR_COL_RANGE) {
         set_error("column index out of range (A column >= nrows(B) or B column >= ncols(B))");
         return SPGEMM_ERR_INDEX;
+    }
+    if (err & DERR_WINDOW) {
+        set_error("chunked numeric: a column of A lies outside the rows of B copied for its part "
+                  "(A changed after spgemm_chunked_symbolic)");
+        return SPGEMM_ERR_NOT_SYMBOLIC;
     }
     if (err & (DERR_PROBE | DERR_COUNT)) {
         set_error("device bound exceeded (hash probe limit or row count mismatch), code %d", err);
@@ -416,6 +422,7 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
     SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[7], 0));
     SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[7], 0));
     env.ctx = &c;
+    env.cache = &h->ccache;
     env.arena = h->arena;
     env.s_in = h->s_in;
     env.s_out = h->s_out;
@@ -440,10 +447,25 @@ int spgemm_chunked_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_c
     SG_TRY(chunk_env(h, fast_mem_budget, s, env, c));
     SG_CUDA(cudaMemsetAsync(h->dstate, 0, sizeof(DevState), s));
     h->cstats = ChunkStats();
+    ChunkCache &cc = h->ccache;
+    cc.valid = false;
     SG_TRY(chunked_symbolic(env, *A, *B, C_row_ptr, nnz_C, fast_mem_budget, h->cstats));
     SG_CUDA(cudaStreamSynchronize(s));
     SG_TRY(fetch_state(h, s));
-    return device_errors(h->hstate->err);
+    SG_TRY(device_errors(h->hstate->err));
+    cc.a_rp = A->row_ptr;
+    cc.a_col = A->col_idx;
+    cc.a_nrows = A->nrows;
+    cc.a_ncols = A->ncols;
+    cc.a_nnz = A->nnz;
+    cc.b_rp = B->row_ptr;
+    cc.b_col = B->col_idx;
+    cc.b_nrows = B->nrows;
+    cc.b_ncols = B->ncols;
+    cc.b_nnz = B->nnz;
+    cc.c_rp = C_row_ptr;
+    cc.valid = true;
+    return SPGEMM_OK;
 }
 
 int spgemm_chunked_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_csr *B,

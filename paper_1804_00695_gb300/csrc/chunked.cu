@@ -59,6 +59,56 @@ __global__ void k_init_range(int *mm) {
     mm[1] = -1;
 }
 
+__global__ void k_init_ranges(int2 *br, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) br[i] = make_int2(INT_MAX, -1);
+}
+
+// Column range of every block of CHUNK_RB rows of A that the resident part
+// [r0, r1) touches (a CTA per block; rp rebased to the part, so the entries
+// of a block's rows are one contiguous run).  Parts that share a block merge
+// through the atomics.
+__global__ void __launch_bounds__(256) k_block_range(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                     int64_t r0, int64_t r1, int2 *br) {
+    __shared__ int red[2][8];
+    const int64_t b = (r0 >> CHUNK_RB_L) + blockIdx.x;
+    const int64_t lo_row = max(b << CHUNK_RB_L, r0) - r0, hi_row = min((b + 1) << CHUNK_RB_L, r1) - r0;
+    int lo = INT_MAX, hi = -1;
+    for (int64_t p = rp[lo_row] + threadIdx.x; p < rp[hi_row]; p += blockDim.x) {
+        const int c = col[p];
+        lo = min(lo, c);
+        hi = max(hi, c);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = lo;
+        red[1][threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            lo = min(lo, red[0][w]);
+            hi = max(hi, red[1][w]);
+        }
+        if (hi >= 0) {
+            atomicMin(&br[b].x, lo);
+            atomicMax(&br[b].y, hi);
+        }
+    }
+}
+
+// *mx = max(*mx, max_i cnt[i]), i < n (row counts of C, before their scan).
+__global__ void k_max_count(const int64_t *__restrict__ cnt, int64_t n, long long *mx) {
+    long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (long long)cnt[i]);
+    for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
+}
+
 template <typename V>
 __device__ __forceinline__ bool fma_insert(int *keys, V *vals, int L, int col, V v) {
     const unsigned msk = (1u << L) - 1;
@@ -109,6 +159,10 @@ __device__ __forceinline__ void bitonic_kv(int *k, V *v, int P, int tid, int NT,
 // skipped; they need not be sorted) are merged in a shared-memory map, then
 // written back sorted, padded with -1.
 constexpr int FMA_WARP_CAP = 256, FMA_S = 512, FMA_WPB = 8, FMA_BMAP = 64, FMA_BMAP_L = 6;
+// mode bits of the multiply-add kernels
+constexpr int FMA_FRESH = 1;    // the C part holds no partial entries yet (its first pass)
+constexpr int FMA_STRICT = 2;   // every column of A must lie in [lo, hi) (one window of B per part)
+constexpr int FMA_BIG_OK = 4;   // rows longer than FMA_WARP_CAP are taken by the block kernel
 
 constexpr int FMA_E = 32;   // stored a_ik staged per batch
 template <typename V>
@@ -122,8 +176,9 @@ __global__ void __launch_bounds__(256) k_fma_warp(
     int64_t nrows, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const V *__restrict__ aval, int64_t lo, int64_t hi, const int64_t *__restrict__ brp,
     const int32_t *__restrict__ bcol, const V *__restrict__ bval, const int64_t *__restrict__ crp,
-    int32_t *__restrict__ ccol, V *__restrict__ cval, int *err, int fresh) {
+    int32_t *__restrict__ ccol, V *__restrict__ cval, int *err, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const bool fresh = mode & FMA_FRESH;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *base = smem_raw + (size_t)w * FmaLayout<V>::per_warp;
     V *vals = (V *)base;
@@ -134,21 +189,25 @@ __global__ void __launch_bounds__(256) k_fma_warp(
     int flag = 0;
     for (int64_t i = (int64_t)blockIdx.x * FMA_WPB + w; i < nrows; i += (int64_t)gridDim.x * FMA_WPB) {
         const int64_t c0 = crp[i];
-        const int cap = (int)(crp[i + 1] - c0);
-        if (cap == 0 || cap > FMA_WARP_CAP) continue;
+        const int64_t cap64 = crp[i + 1] - c0;
+        if (cap64 > FMA_WARP_CAP && !(mode & FMA_BIG_OK)) flag |= DERR_COUNT;
+        const int cap = (int)cap64;
+        if (cap == 0 || cap64 > FMA_WARP_CAP) continue;
         // Rows with no stored a_ik in this B part keep their partial row as it
         // is.  B parts come in ascending row order, so the pass whose range
         // holds the row's largest a_ik column is its last: only that pass
         // sorts the row; earlier ones leave the partial row unsorted.
         bool final_pass;
         {
-            bool any = false;
+            bool any = false, out = false;
             int64_t kmax = -1;
             for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += 32) {
                 const int64_t k = acol[p];
                 any |= k >= lo && k < hi;
+                out |= k < lo || k >= hi;
                 kmax = k > kmax ? k : kmax;
             }
+            if ((mode & FMA_STRICT) && out) flag |= DERR_WINDOW;
             if (!__any_sync(0xffffffffu, any)) continue;
             for (int d = 16; d > 0; d >>= 1) {
                 const int64_t o = __shfl_xor_sync(0xffffffffu, kmax, d);
@@ -707,10 +766,23 @@ static int64_t part_bytes(const int64_t *rp, int64_t r0, int64_t r1, int vb) {
     return (r1 - r0 + 1) * 8 + (rp[r1] - rp[r0]) * (int64_t)(4 + vb);
 }
 
-// Device copy of rows [r0, r1) of a host CSR matrix into (rp, col, val),
-// offsets rebased to 0; returns the bytes moved.
+// Offsets of a part copied in as they are, rebased to 0 on stream s.
+static int rebase_rows(int64_t *rp, int64_t rows, int64_t p0, cudaStream_t s) {
+    if (rows > 0)
+        k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(rp, rows + 1, p0);
+    else
+        SG_CUDA(cudaMemsetAsync(rp, 0, 8, s));
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
+// Device copy of rows [r0, r1) of a host CSR matrix into (rp, col, val);
+// returns the bytes moved.  With `rebase` the offsets are rebased to 0 on the
+// copy stream, else the caller rebases them (rebase_rows with p0 =
+// M.row_ptr[r0]) on the stream that uses them, so that no kernel waits in the
+// copy stream's queue behind the kernels that occupy the GPU.
 static int64_t copy_rows_in(const spgemm_csr &M, int64_t r0, int64_t r1, int vb, int64_t *rp,
-                            int32_t *col, void *val, cudaStream_t s, int *status) {
+                            int32_t *col, void *val, cudaStream_t s, int *status, bool rebase = true) {
     const int64_t p0 = M.row_ptr[r0], p1 = M.row_ptr[r1];
     int64_t bytes = (r1 - r0 + 1) * 8;
     cudaError_t e = cudaMemcpyAsync(rp, M.row_ptr + r0, (size_t)(r1 - r0 + 1) * 8, cudaMemcpyHostToDevice, s);
@@ -723,16 +795,12 @@ static int64_t copy_rows_in(const spgemm_csr &M, int64_t r0, int64_t r1, int vb,
             bytes += (p1 - p0) * vb;
         }
     }
-    if (e == cudaSuccess && r1 > r0) {
-        k_rebase<<<(unsigned)((r1 - r0 + 1 + 255) / 256), 256, 0, s>>>(rp, r1 - r0 + 1, p0);
-        e = cudaGetLastError();
-    } else if (e == cudaSuccess) {
-        e = cudaMemsetAsync(rp, 0, 8, s);
-    }
     if (e != cudaSuccess) {
         set_error("chunked copy: %s", cudaGetErrorString(e));
         *status = SPGEMM_ERR_CUDA;
+        return bytes;
     }
+    if (rebase) *status = rebase_rows(rp, r1 - r0, p0, s);
     return bytes;
 }
 
@@ -766,7 +834,7 @@ static PartBuf carve(char *base, int64_t rows, int vb, int64_t nnz) {
 template <typename V>
 static int launch_fma(const PartBuf &A, int64_t nrows, int64_t lo, int64_t hi, const PartBuf &B,
                       const PartBuf &Cp, bool values, int64_t fma_blocks, int64_t slots, void *gws,
-                      int *err, Ctx &c, bool fresh) {
+                      int *err, Ctx &c, int mode) {
     const size_t smem = (size_t)FMA_WPB * FmaLayout<V>::per_warp;
     SG_CUDA(cudaFuncSetAttribute(k_fma_warp<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t blocks = (nrows + FMA_WPB - 1) / FMA_WPB;
@@ -776,7 +844,7 @@ static int launch_fma(const PartBuf &A, int64_t nrows, int64_t lo, int64_t hi, c
         k_fma_warp<V><<<(unsigned)blocks, 256, smem, c.s>>>(
             nrows, A.rp, A.col, values ? (const V *)A.val : nullptr, lo, hi, B.rp, B.col,
             values ? (const V *)B.val : nullptr, Cp.rp, Cp.col, values ? (V *)Cp.val : nullptr, err,
-            fresh ? 1 : 0);
+            mode | (fma_blocks > 0 ? FMA_BIG_OK : 0));
         c.end();
         SG_CUDA(cudaGetLastError());
     }
@@ -798,9 +866,23 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     const int vb = dtype == SPGEMM_F64 ? 8 : 4;
     Ctx &c = *env.ctx;
     const cudaStream_t s = c.s;
-    // the largest row of C decides whether the block kernel and its maps are needed
+    // What the chunked symbolic call of this product recorded: the column
+    // ranges of A's row blocks (for A's host arrays) and the longest row of C
+    // (for A, B and these offsets of C).
+    const ChunkCache *cc = env.cache;
+    const bool known_ranges = cc && cc->valid && cc->a_rp == A.row_ptr && cc->a_col == A.col_idx &&
+                              cc->a_nrows == A.nrows && cc->a_ncols == A.ncols && cc->a_nnz == A.nnz &&
+                              (int64_t)cc->brange.size() == (A.nrows + CHUNK_RB - 1) / CHUNK_RB;
+    const bool known_max = known_ranges && cc->b_rp == B.row_ptr && cc->b_col == B.col_idx &&
+                           cc->b_nrows == B.nrows && cc->b_ncols == B.ncols && cc->b_nnz == B.nnz &&
+                           cc->c_rp == C.row_ptr;
+    // the largest row of C decides whether the block kernel and its maps are
+    // needed (the kernels flag a longer row than planned for)
     int64_t cap_max = 0;
-    for (int64_t i = 0; i < C.nrows; i++) cap_max = std::max(cap_max, C.row_ptr[i + 1] - C.row_ptr[i]);
+    if (known_max)
+        cap_max = cc->max_row;
+    else
+        for (int64_t i = 0; i < C.nrows; i++) cap_max = std::max(cap_max, C.row_ptr[i + 1] - C.row_ptr[i]);
     const bool big_rows = cap_max > FMA_WARP_CAP;
     int64_t slots = 2;
     while (slots < 2 * cap_max) slots <<= 1;
@@ -928,48 +1010,59 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     const cudaStream_t si = env.s_in, so = env.s_out;
     cudaEvent_t *ev = env.ev;   // [0..1] copied-in, [2..3] compute done, [4..5] copied-out
     int *err = env.err;
-    // fresh: the C part holds no partial entries yet (first multiply-add of it)
+    // mode: FMA_* bits (first pass of the C part, one window of B)
     auto fma = [&](const PartBuf &Ap, int64_t rows, int64_t lo, int64_t hi, const PartBuf &Bp,
-                   const PartBuf &Cp, bool fresh) -> int {
+                   const PartBuf &Cp, int mode) -> int {
         return dtype == SPGEMM_F64
-                   ? launch_fma<double>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, fresh)
-                   : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, fresh);
+                   ? launch_fma<double>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, mode)
+                   : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, mode);
     };
     if (p.algorithm == 2) {
         // ev (by buffer slot): [0..1] rows of B in, [2..3] rows of B used,
-        // [4..5] C part out, [6..7] A part in (with its column range in
-        // pinned host memory), [8..9] C part ready, [10..11] A part used.
-        // An A buffer is reused once its products are done, a C buffer once
-        // its part has left the device, so neither waits for the other.
+        // [4..5] C part out, [6..7] A part in (and, without recorded ranges,
+        // its column range in pinned host memory), [8..9] offsets of the C
+        // part in, [10..11] A part used.  An A buffer is reused once its
+        // products are done, a C buffer once its part has left the device, so
+        // neither waits for the other.  The copy streams carry copies only:
+        // offsets are rebased, and C cleared, on the compute stream, so no
+        // copy waits behind a kernel that waits for the GPU to have room.
         const size_t nac = p.ac_cuts.size() - 1;
         int *hmm = env.host_mm;
         size_t bcount = 0;
+        // column range of part j: from the recorded row blocks (a superset,
+        // at block granularity), else measured on the device once the part
+        // is in and read back by the host
+        auto recorded_range = [&](size_t j, int &lo_c, int &hi_c) {
+            const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1];
+            lo_c = INT_MAX;
+            hi_c = -1;
+            if (r1 <= r0) return;
+            for (int64_t b = r0 >> CHUNK_RB_L; b <= (r1 - 1) >> CHUNK_RB_L; b++) {
+                lo_c = std::min(lo_c, cc->brange[(size_t)b].x);
+                hi_c = std::max(hi_c, cc->brange[(size_t)b].y);
+            }
+        };
         auto stage_ac = [&](size_t j) -> int {
             const int slot = (int)(j & 1);
             const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
-            const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
             if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[10 + slot], 0));
-            stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st);
+            stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st, false);
             SG_TRY(st);
-            // column range of the A part decides which rows of B it needs
-            const int64_t an = A.row_ptr[r1] - A.row_ptr[r0];
-            int *dmm = mm + 2 * slot;
-            k_init_range<<<1, 1, 0, si>>>(dmm);
-            if (an > 0)
-                k_col_range<<<(unsigned)std::min<int64_t>((an + 255) / 256, (int64_t)c.nsm * 8), 256, 0, si>>>(
-                    Ab[slot].col, an, dmm);
-            SG_CUDA(cudaMemcpyAsync(hmm + 2 * slot, dmm, 8, cudaMemcpyDeviceToHost, si));
+            if (!known_ranges) {
+                // column range of the A part decides which rows of B it needs
+                const int64_t an = A.row_ptr[r1] - A.row_ptr[r0];
+                int *dmm = mm + 2 * slot;
+                k_init_range<<<1, 1, 0, si>>>(dmm);
+                if (an > 0)
+                    k_col_range<<<(unsigned)std::min<int64_t>((an + 255) / 256, (int64_t)c.nsm * 8), 256, 0, si>>>(
+                        Ab[slot].col, an, dmm);
+                SG_CUDA(cudaMemcpyAsync(hmm + 2 * slot, dmm, 8, cudaMemcpyDeviceToHost, si));
+            }
             SG_CUDA(cudaEventRecord(ev[6 + slot], si));
             // C starts empty: only its offsets come in (behind the copy out of
             // the part that used this buffer, on the same stream)
             SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, so));
             stats.h2d += (rows + 1) * 8;
-            if (rows > 0)
-                k_rebase<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, so>>>(Cb[slot].rp, rows + 1, C.row_ptr[r0]);
-            if (cn > 0) {
-                SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, so));
-                SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, so));
-            }
             SG_CUDA(cudaEventRecord(ev[8 + slot], so));
             return SPGEMM_OK;
         };
@@ -978,35 +1071,57 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             const int slot = (int)(j & 1);
             const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
             const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
-            // the host waits for this part's column range only; the device
-            // still has the previous part's products queued
-            SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
-            const int lo_c = hmm[2 * slot], hi_c = hmm[2 * slot + 1];
+            int lo_c, hi_c;
+            if (known_ranges) {
+                recorded_range(j, lo_c, hi_c);
+            } else {
+                // the host waits for this part's column range only; the
+                // device still has the previous part's products queued
+                SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
+                lo_c = hmm[2 * slot];
+                hi_c = hmm[2 * slot + 1];
+            }
             // the rows of B this part reaches, as (r0, r1) copies: one window
             // when it fits a buffer, else the fixed parts it overlaps
             std::vector<std::pair<int64_t, int64_t>> need;
+            bool window = false;
             if (hi_c >= 0 && carve_bytes(hi_c + 1 - lo_c, B.row_ptr[hi_c + 1] - B.row_ptr[lo_c], vb) <= inner_cap) {
                 need.push_back({(int64_t)lo_c, (int64_t)hi_c + 1});
                 stats.b_windows++;
+                window = true;
             } else {
                 for (size_t t = 0; t + 1 < p.b_cuts.size(); t++)
                     if (hi_c >= 0 && p.b_cuts[t] <= hi_c && p.b_cuts[t + 1] > lo_c)
                         need.push_back({p.b_cuts[t], p.b_cuts[t + 1]});
                 stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
             }
+            // the A part and the offsets of its C part, rebased on the compute stream
             SG_CUDA(cudaStreamWaitEvent(s, ev[6 + slot], 0));
             SG_CUDA(cudaStreamWaitEvent(s, ev[8 + slot], 0));
+            SG_TRY(rebase_rows(Ab[slot].rp, rows, A.row_ptr[r0], s));
+            SG_TRY(rebase_rows(Cb[slot].rp, rows, C.row_ptr[r0], s));
+            // One window and no long rows: the single pass writes every entry
+            // of the part (its rows are complete and padded), so C is not
+            // cleared first.  Otherwise passes merge into a cleared part.
+            if (cn > 0 && (!window || fma_blocks > 0)) {
+                SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, s));
+                SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, s));
+            }
             // stream the needed rows of B, double buffered
             for (size_t u = 0; u < need.size(); u++, bcount++) {
                 const int bs = (int)(bcount & 1);
                 const int64_t b0 = need[u].first, b1 = need[u].second;
                 Bb[bs] = carve(binner[bs], b1 - b0, vb, B.row_ptr[b1] - B.row_ptr[b0]);
                 if (bcount >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[2 + bs], 0));
-                stats.h2d += copy_rows_in(B, b0, b1, vb, Bb[bs].rp, Bb[bs].col, Bb[bs].val, si, &st);
+                stats.h2d += copy_rows_in(B, b0, b1, vb, Bb[bs].rp, Bb[bs].col, Bb[bs].val, si, &st, false);
                 SG_TRY(st);
                 SG_CUDA(cudaEventRecord(ev[bs], si));
                 SG_CUDA(cudaStreamWaitEvent(s, ev[bs], 0));
-                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[bs], Cb[slot], u == 0));
+                SG_TRY(rebase_rows(Bb[bs].rp, b1 - b0, B.row_ptr[b0], s));
+                // a recorded range may be stale if A changed after the
+                // symbolic call: a window then checks every column of A
+                const int mode = (u == 0 ? FMA_FRESH : 0) | (window && known_ranges ? FMA_STRICT : 0);
+                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[bs], Cb[slot], mode));
                 SG_CUDA(cudaEventRecord(ev[2 + bs], s));
             }
             SG_CUDA(cudaEventRecord(ev[10 + slot], s));   // A part used, C part complete
@@ -1056,7 +1171,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 }
                 SG_CUDA(cudaEventRecord(ev[slot], si));
                 SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
-                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[0], Cb[slot], t == 0));
+                SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[0], Cb[slot], t == 0 ? FMA_FRESH : 0));
                 SG_CUDA(cudaEventRecord(ev[2 + slot], s));
                 SG_CUDA(cudaStreamWaitEvent(so, ev[2 + slot], 0));
                 if (cn > 0) {
@@ -1091,7 +1206,11 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     const size_t poff_bytes = r256((size_t)(B.nrows + 1) * 8);
     const size_t btmp_bytes = r256(scan_tmp_bytes(B.nrows));
     const size_t raw_b = r256((size_t)(B.nrows + 1) * 8) + r256((size_t)std::max<int64_t>(B.nnz, 1) * 4);
-    const size_t reserve = bitmap + poff_bytes + btmp_bytes + 8192;
+    // column ranges of A's row blocks and the longest row of C, recorded for
+    // the numeric call
+    const int64_t nblk = (A.nrows + CHUNK_RB - 1) / CHUNK_RB;
+    const size_t brange_bytes = r256((size_t)std::max<int64_t>(nblk, 1) * sizeof(int2));
+    const size_t reserve = bitmap + poff_bytes + btmp_bytes + brange_bytes + 8192;
     if (budget <= reserve) {
         set_error("chunked symbolic: budget %zu below the fixed working set %zu", budget, reserve);
         return SPGEMM_ERR_BUDGET;
@@ -1140,11 +1259,12 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     Arena ar{(char *)env.arena, budget, 0};
     unsigned *bits = (unsigned *)ar.take(bitmap);
     int *flags = (int *)ar.take(4 * sizeof(int));   // overflow per slot, unsorted rows of B
-    int64_t *carry = (int64_t *)ar.take(4 * sizeof(int64_t));   // running offsets, scan totals
+    int64_t *carry = (int64_t *)ar.take(5 * sizeof(int64_t));   // running offsets, scan totals, longest row
     int64_t *poff = (int64_t *)ar.take(poff_bytes);
     void *btmp = ar.take(btmp_bytes);
+    int2 *brange = (int2 *)ar.take(brange_bytes);
     const size_t top = (budget - raw_b) & ~(size_t)255;
-    if (!bits || !flags || !carry || !poff || !btmp || ar.used > top) {
+    if (!bits || !flags || !carry || !poff || !btmp || !brange || ar.used > top) {
         set_error("chunked symbolic: budget %zu too small", budget);
         return SPGEMM_ERR_BUDGET;
     }
@@ -1162,7 +1282,8 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     // compress the pattern of B into (block, mask) pairs (Section 2.1): count,
     // offsets, and the host learns the pair count (one synchronisation)
     SG_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
-    SG_CUDA(cudaMemsetAsync(carry, 0, 4 * sizeof(int64_t), s));
+    SG_CUDA(cudaMemsetAsync(carry, 0, 5 * sizeof(int64_t), s));
+    if (nblk > 0) k_init_ranges<<<(unsigned)((nblk + 255) / 256), 256, 0, s>>>(brange, nblk);
     SG_CUDA(cudaMemsetAsync(poff, 0, 8, s));
     if (B.nrows > 0) {
         k_pairs_count<<<(unsigned)((B.nrows + 255) / 256), 256, 0, s>>>(B.nrows, Bp.rp, Bp.col, poff, &flags[2]);
@@ -1216,10 +1337,11 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
         const int slot = (int)(j & 1);
         const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
         if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[4 + slot], 0));   // buffers free again
-        stats.h2d += copy_rows_in(A, r0, r1, 0, Ap[slot].rp, Ap[slot].col, nullptr, si, &st);
+        stats.h2d += copy_rows_in(A, r0, r1, 0, Ap[slot].rp, Ap[slot].col, nullptr, si, &st, false);
         SG_TRY(st);
         SG_CUDA(cudaEventRecord(ev[slot], si));
         SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
+        SG_TRY(rebase_rows(Ap[slot].rp, rows, A.row_ptr[r0], s));
         int64_t *x = cnt[slot];
         SG_CUDA(cudaMemsetAsync(x, 0, 8, s));
         if (rows > 0) {
@@ -1245,6 +1367,11 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
                     rows, Ap[slot].rp, Ap[slot].col, Bp.rp, Bp.col, x + 1, nwords, bits, &flags[slot], B.nrows);
                 SG_CUDA(cudaGetLastError());
             }
+            k_max_count<<<(unsigned)std::min<int64_t>((rows + 255) / 256, (int64_t)c.nsm * 4), 256, 0, s>>>(
+                x + 1, rows, (long long *)&carry[4]);
+            k_block_range<<<(unsigned)(((r1 - 1) >> CHUNK_RB_L) - (r0 >> CHUNK_RB_L) + 1), 256, 0, s>>>(
+                Ap[slot].rp, Ap[slot].col, r0, r1, brange);
+            SG_CUDA(cudaGetLastError());
             SG_TRY(launch_scan_counts(x, rows, (long long *)&carry[2], tmp[slot], c));
         }
         k_add_carry<<<(unsigned)((rows + 1 + 255) / 256), 256, 0, s>>>(x, rows, &carry[j & 1],
@@ -1260,6 +1387,13 @@ int chunked_symbolic(ChunkEnv &env, const spgemm_csr &A, const spgemm_csr &B, in
     SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
     SG_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
     SG_CUDA(cudaMemcpyAsync(nnz_C, &carry[nparts & 1], 8, cudaMemcpyDeviceToHost, s));
+    if (env.cache) {
+        ChunkCache &cc = *env.cache;
+        cc.brange.resize((size_t)nblk);
+        if (nblk > 0)
+            SG_CUDA(cudaMemcpyAsync(cc.brange.data(), brange, (size_t)nblk * sizeof(int2), cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaMemcpyAsync(&cc.max_row, &carry[4], 8, cudaMemcpyDeviceToHost, s));
+    }
     return SPGEMM_OK;
 }
 

@@ -31,6 +31,7 @@ enum : int {
     DERR_COL_RANGE = 1,   // a column index of A (>= nrows(B)) or B (>= ncols) out of range
     DERR_PROBE = 2,       // a hash probe sequence exceeded the table
     DERR_COUNT = 4,       // numeric found a different column count than symbolic
+    DERR_WINDOW = 8,      // chunked: a column of A outside the rows of B copied for its part
 };
 
 struct DevState {          // lives in device memory, one per handle
@@ -232,8 +233,22 @@ bool cut_rows(const int64_t *rp1, const int64_t *rp2, int64_t n, int vb, double 
               std::vector<int64_t> &cuts);
 
 // chunked.cu: Algorithms 2 and 3 with host operands.
+// What a chunked symbolic call learns about its operands and hands on to the
+// chunked numeric call of the same product: the column range of every block
+// of CHUNK_RB rows of A (the rows of B each part of A reaches, known before
+// the part is copied) and the longest row of C.  Valid only for the same
+// host arrays and sizes.
+constexpr int CHUNK_RB_L = 10, CHUNK_RB = 1 << CHUNK_RB_L;
+struct ChunkCache {
+    bool valid = false;
+    const void *a_rp = nullptr, *a_col = nullptr, *b_rp = nullptr, *b_col = nullptr, *c_rp = nullptr;
+    int64_t a_nrows = 0, a_ncols = 0, a_nnz = 0, b_nrows = 0, b_ncols = 0, b_nnz = 0;
+    std::vector<int2> brange;   // per block of CHUNK_RB rows of A: {min, max} column ({INT_MAX, INT_MIN} if none)
+    int64_t max_row = 0;        // largest row of C
+};
 struct ChunkEnv {
     Ctx *ctx = nullptr;
+    ChunkCache *cache = nullptr;
     void *arena = nullptr;        // exactly the budget, device
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev[12] = {};

@@ -165,6 +165,65 @@ def test_chunked_banded_skips_b_parts(h):
     assert st["h2d_bytes"] + st["d2h_bytes"] < sa + sc + sb * st["n_ac"]
 
 
+def test_chunked_numeric_recorded_and_measured_ranges(h):
+    """The numeric call takes the rows of B that each part of A reaches from
+    the row-block column ranges its symbolic call recorded; a handle without
+    them measures each part's range on the device.  Same product both ways,
+    and the recorded ranges (supersets) never copy fewer bytes of B."""
+    a = I.laplace3d_27pt(20)
+    ref = oracle.spgemm(a, a)
+    A = sg.HostCsr.from_numpy(a)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, a.row_ptr, 8, 2, 3, 2)
+    assert budget is not None
+    rp, nnz = h.chunked_symbolic(A, A, max(budget, 1 << 22))
+    c1 = h.chunked_numeric(A, A, rp, nnz, budget)
+    st1 = h.chunked_stats()
+    check(c1, ref, "f64")
+    h2 = sg.Handle()
+    c2 = h2.chunked_numeric(A, A, rp.clone().pin_memory(), nnz, budget)
+    st2 = h2.chunked_stats()
+    check(c2, ref, "f64")
+    assert st1["n_ac"] == st2["n_ac"] >= 3
+    assert st1["h2d_bytes"] >= st2["h2d_bytes"]
+
+
+def test_chunked_numeric_flags_a_changed_after_symbolic(h):
+    """Columns of A moved outside the ranges its symbolic call recorded (same
+    host arrays) are caught by the window check: SPGEMM_ERR_NOT_SYMBOLIC."""
+    a = I.laplace3d_27pt(20)
+    ref = oracle.spgemm(a, a)
+    A, B = sg.HostCsr.from_numpy(a), sg.HostCsr.from_numpy(a)
+    rp, nnz = h.chunked_symbolic(A, B, 1 << 26)
+    tot = sum(CH.range_bytes(x, 0, len(x) - 1, 8) for x in (a.row_ptr, ref.row_ptr, a.row_ptr))
+    budget, seen = None, []
+    for frac in np.geomspace(1.5, 0.1, 40):
+        f = int(tot * frac)
+        try:
+            c = h.chunked_numeric(A, B, rp, nnz, f)
+        except sg.SpgemmError as e:
+            assert e.status == 5
+            continue
+        st = h.chunked_stats()
+        seen.append((round(frac, 3), st["algorithm"], st["n_ac"], st["n_b"], st["b_windows"]))
+        if st["algorithm"] == 2 and st["n_ac"] >= 2 and st["b_windows"] >= 1:
+            check(c, ref, "f64")
+            budget = f
+            break
+    assert budget is not None, seen
+    # every 50th row reaches a column no part of its half reaches: the last
+    # column of B (first half of the rows) or column 0 (second half); the
+    # rows stay ascending
+    col = A.col.numpy()
+    for r in range(0, a.nrows, 50):
+        if r < a.nrows // 2:
+            col[int(a.row_ptr[r + 1]) - 1] = a.ncols - 1
+        else:
+            col[int(a.row_ptr[r])] = 0
+    with pytest.raises(sg.SpgemmError) as ei:
+        h.chunked_numeric(A, B, rp, nnz, budget)
+    assert ei.value.status == 8
+
+
 def test_chunked_budget_errors(h):
     a = I.random_csr(50, 40, 0.2, 95)
     A = sg.HostCsr.from_numpy(a)
