@@ -1019,13 +1019,16 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     };
     if (p.algorithm == 2) {
         // ev (by buffer slot): [0..1] rows of B in, [2..3] rows of B used,
-        // [4..5] C part out, [6..7] A part in (and, without recorded ranges,
-        // its column range in pinned host memory), [8..9] offsets of the C
-        // part in, [10..11] A part used.  An A buffer is reused once its
-        // products are done, a C buffer once its part has left the device, so
-        // neither waits for the other.  The copy streams carry copies only:
-        // offsets are rebased, and C cleared, on the compute stream, so no
-        // copy waits behind a kernel that waits for the GPU to have room.
+        // [4..5] C part out, [6..7] A part and the offsets of its C part in
+        // (and, without recorded ranges, the part's column range in pinned
+        // host memory), [10..11] A part used.  The A buffer and the offsets
+        // of a C buffer are reused once the part's products are done, the
+        // entries of a C buffer once they have left the device, so neither
+        // waits for the other.  The copy-in stream carries copies only and
+        // the copy-out stream only the copies of C out: offsets are rebased,
+        // and C cleared, on the compute stream, so no copy waits behind a
+        // kernel that waits for the GPU to have room, nor a copy out behind
+        // a copy in.
         const size_t nac = p.ac_cuts.size() - 1;
         int *hmm = env.host_mm;
         size_t bcount = 0;
@@ -1048,6 +1051,9 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[10 + slot], 0));
             stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st, false);
             SG_TRY(st);
+            // C starts empty: only its offsets come in
+            SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
+            stats.h2d += (rows + 1) * 8;
             if (!known_ranges) {
                 // column range of the A part decides which rows of B it needs
                 const int64_t an = A.row_ptr[r1] - A.row_ptr[r0];
@@ -1059,11 +1065,6 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 SG_CUDA(cudaMemcpyAsync(hmm + 2 * slot, dmm, 8, cudaMemcpyDeviceToHost, si));
             }
             SG_CUDA(cudaEventRecord(ev[6 + slot], si));
-            // C starts empty: only its offsets come in (behind the copy out of
-            // the part that used this buffer, on the same stream)
-            SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, so));
-            stats.h2d += (rows + 1) * 8;
-            SG_CUDA(cudaEventRecord(ev[8 + slot], so));
             return SPGEMM_OK;
         };
         if (nac > 0) SG_TRY(stage_ac(0));
@@ -1095,9 +1096,10 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                         need.push_back({p.b_cuts[t], p.b_cuts[t + 1]});
                 stats.skipped_b += (int64_t)(p.b_cuts.size() - 1 - need.size());
             }
-            // the A part and the offsets of its C part, rebased on the compute stream
+            // the A part and the offsets of its C part, rebased on the compute
+            // stream once the C part that used the buffer has left
             SG_CUDA(cudaStreamWaitEvent(s, ev[6 + slot], 0));
-            SG_CUDA(cudaStreamWaitEvent(s, ev[8 + slot], 0));
+            if (j >= 2) SG_CUDA(cudaStreamWaitEvent(s, ev[4 + slot], 0));
             SG_TRY(rebase_rows(Ab[slot].rp, rows, A.row_ptr[r0], s));
             SG_TRY(rebase_rows(Cb[slot].rp, rows, C.row_ptr[r0], s));
             // One window and no long rows: the single pass writes every entry
