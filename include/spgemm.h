@@ -183,9 +183,14 @@ SPGEMM_API int spgemm_plan_chunks(const int64_t *A_row_ptr, int64_t nrows_A, con
  * buffer, that window of rows is copied once instead of the fixed parts and
  * the part is multiplied in one pass (same result, fewer bytes and passes).
  * The streamed operand is double buffered on side streams.  Values of C are
- * accumulated natively (FP64 or FP32).  The call returns once all copies and
- * kernels are enqueued (it waits once per part of A for its column range);
- * synchronise `stream` before reading C.
+ * accumulated natively (FP64 or FP32).  The rows of B each part of A reaches
+ * come from the row-block column ranges that spgemm_chunked_symbolic recorded
+ * on this handle for the same host arrays of A (those of B and C_row_ptr too
+ * for the longest row); a window pass checks every column of A against them
+ * (SPGEMM_ERR_NOT_SYMBOLIC from spgemm_check if A changed).  Without them the
+ * range of each part is measured on the device and the host waits for it
+ * once per part.  The call returns once all copies and kernels are enqueued;
+ * synchronise `stream` before reading C, then spgemm_check.
  * Errors: SPGEMM_ERR_BUDGET (a row or the double-buffered parts do not fit),
  * SPGEMM_ERR_NOMEM (the budget cannot be allocated), SPGEMM_ERR_DIM,
  * SPGEMM_ERR_INDEX (symbolic: a column out of range), SPGEMM_ERR_ARG.
@@ -210,6 +215,24 @@ SPGEMM_API int spgemm_chunked_numeric(spgemm_handle handle, int dtype, const spg
                                       const spgemm_csr *B, spgemm_csr *C, size_t fast_mem_budget,
                                       void *stream);
 SPGEMM_API int spgemm_chunked_stats(spgemm_handle handle, spgemm_chunk_stats *out);
+
+/* Allocator of the one-call chunked product: given nnz(C), points *col_idx
+ * and *values at host arrays of nnz elements (int32 columns; values of the
+ * call's dtype) that the call fills; pinned memory gives full-speed copies.
+ * Returns 0 on success. */
+typedef int (*spgemm_alloc_fn)(void *user, int64_t nnz, int32_t **col_idx, void **values);
+
+/* Both chunked phases in one call (kkmem(A, B, C, FastSize) of Section 3.3.1):
+ * the symbolic phase fills C->row_ptr (host, nrows(A)+1 int64, caller-
+ * allocated), `alloc(user, nnz(C), ...)` is called once for the entries, the
+ * numeric phase fills them; C->nrows, ncols, nnz, col_idx and values are set.
+ * The numeric phase takes the column ranges the symbolic phase recorded.
+ * Synchronises `stream` (C is complete on return).
+ * Errors: those of the two phases; SPGEMM_ERR_NOMEM if alloc fails or returns
+ * NULL arrays for nnz(C) > 0. */
+SPGEMM_API int spgemm_chunked(spgemm_handle handle, int dtype, const spgemm_csr *A, const spgemm_csr *B,
+                              spgemm_csr *C, spgemm_alloc_fn alloc, void *user, size_t fast_mem_budget,
+                              void *stream);
 
 /* Backward of C = A*B for a scalar loss L with dC = dL/dC given on the
  * pattern of C: the product is bilinear, so

@@ -61,6 +61,9 @@ class CsrDesc(C.Structure):
 
 _lib = None
 
+# int alloc(void *user, int64_t nnz, int32_t **col_idx, void **values)
+ALLOC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p))
+
 
 def load(path: str = LIB_PATH):
     """Load the CUDA library (raises if it was not built)."""
@@ -93,6 +96,7 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked_symbolic": ([p, p, p, p, C.POINTER(i64), C.c_size_t, p], i32),
         "spgemm_chunked_numeric": ([p, i32, p, p, p, C.c_size_t, p], i32),
         "spgemm_chunked_stats": ([p, p], i32),
+        "spgemm_chunked": ([p, i32, p, p, p, ALLOC_FN, p, C.c_size_t, p], i32),
         "spgemm_backward": ([p, i32, p, p, p, p, p, p], i32),
         "spgemm_batched_symbolic": ([p, i32, p, p, p, C.POINTER(i64), p, p], i32),
         "spgemm_batched_numeric": ([p, i32, i32, p, p, p, p], i32),
@@ -315,8 +319,28 @@ class Handle:
         self.check(stream)
 
     def chunked(self, A: "HostCsr", B: "HostCsr", budget: int, stream=None) -> "HostCsr":
-        rp, nnz = self.chunked_symbolic(A, B, budget, stream)
-        return self.chunked_numeric(A, B, rp, nnz, budget, stream)
+        """Both chunked phases in one call (spgemm_chunked): the entries of C
+        are allocated (pinned) by a callback once nnz(C) is known."""
+        torch = _torch()
+        rp = torch.empty(A.nrows + 1, dtype=torch.int64).pin_memory()
+        held = {}
+
+        def alloc(user, nnz, col_p, val_p):
+            try:
+                held["col"] = torch.empty(nnz, dtype=torch.int32).pin_memory()
+                held["val"] = torch.empty(nnz, dtype=A.val.dtype).pin_memory()
+            except Exception:
+                return 1
+            col_p[0] = held["col"].data_ptr()
+            val_p[0] = held["val"].data_ptr()
+            return 0
+
+        cb = ALLOC_FN(alloc)
+        dc = CsrDesc(A.nrows, B.ncols, 0, rp.data_ptr(), None, None)
+        da, db = A.desc(), B.desc()
+        _check(_lib.spgemm_chunked(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc), cb, None,
+                                   budget, _stream(stream)))
+        return HostCsr(A.nrows, B.ncols, rp, held["col"], held["val"])
 
     def chunked_stats(self) -> dict:
         r = ChunkStatsRec()

@@ -492,6 +492,28 @@ int spgemm_chunked_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, cons
     return chunked_numeric(env, dtype, *A, *B, *C, fast_mem_budget, h->cstats);
 }
 
+int spgemm_chunked(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_csr *B, spgemm_csr *C,
+                   spgemm_alloc_fn alloc, void *user, size_t fast_mem_budget, void *stream) {
+    if (!h || !C || !alloc || !A || !B) { set_error("NULL handle, operand, C or allocator"); return SPGEMM_ERR_ARG; }
+    if (!C->row_ptr) { set_error("C.row_ptr is NULL"); return SPGEMM_ERR_ARG; }
+    int64_t nnz = 0;
+    SG_TRY(spgemm_chunked_symbolic(h, A, B, C->row_ptr, &nnz, fast_mem_budget, stream));
+    int32_t *col = nullptr;
+    void *val = nullptr;
+    if (alloc(user, nnz, &col, &val) != 0 || (nnz > 0 && (!col || !val))) {
+        set_error("chunked: the allocator failed for %lld entries of C", (long long)nnz);
+        return SPGEMM_ERR_NOMEM;
+    }
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->nnz = nnz;
+    C->col_idx = col;
+    C->values = val;
+    SG_TRY(spgemm_chunked_numeric(h, dtype, A, B, C, fast_mem_budget, stream));
+    SG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return spgemm_check(h, stream);
+}
+
 int spgemm_chunked_stats(spgemm_handle h, spgemm_chunk_stats *out) {
     if (!h || !out) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
     const ChunkStats &x = h->cstats;

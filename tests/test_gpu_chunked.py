@@ -224,6 +224,27 @@ def test_chunked_numeric_flags_a_changed_after_symbolic(h):
     assert ei.value.status == 8
 
 
+def test_chunked_one_call_with_allocator(h):
+    """spgemm_chunked runs both phases with the caller's allocator for the
+    entries of C; an allocator that fails gives SPGEMM_ERR_NOMEM."""
+    import ctypes
+    import torch
+    a = I.laplace3d_27pt(10)
+    ref = oracle.spgemm(a, a)
+    A = sg.HostCsr.from_numpy(a)
+    c = h.chunked(A, A, 1 << 22)
+    check(c, ref, "f64")
+    lib = sg.load()
+    fail = sg.ALLOC_FN(lambda user, nnz, col_p, val_p: 1)
+    rp = torch.empty(a.nrows + 1, dtype=torch.int64).pin_memory()
+    dc = sg.CsrDesc(a.nrows, a.ncols, 0, rp.data_ptr(), None, None)
+    da = A.desc()
+    st = lib.spgemm_chunked(h._h, sg.F64, ctypes.byref(da), ctypes.byref(da), ctypes.byref(dc), fail, None,
+                            1 << 22, torch.cuda.current_stream().cuda_stream)
+    assert st == 4
+    assert np.array_equal(rp.numpy(), ref.row_ptr)   # the symbolic phase ran
+
+
 def test_chunked_budget_errors(h):
     a = I.random_csr(50, 40, 0.2, 95)
     A = sg.HostCsr.from_numpy(a)
