@@ -98,38 +98,44 @@ __global__ void k_analyze(int64_t nrows, int64_t nrows_b, int64_t nwords,
     __syncthreads();
     const int lane = threadIdx.x % AN_G;
     const unsigned gmask = ((1u << AN_G) - 1) << ((threadIdx.x & 31) & ~(AN_G - 1));
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / AN_G;
-    bool live = i < nrows;
-    long long f = 0, cp = 0;
+    // a fixed grid strides over the rows, so the block's totals reach the
+    // global counters once per block, not once per 32 rows
+    const int64_t rstride = (int64_t)gridDim.x * (blockDim.x / AN_G);
+    long long wf = 0, wl = 0;   // this lane's share of the products and the longest row
     bool bad = false;
-    if (live) {
-        for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += AN_G) {
-            int k = acol[p];
-            if (k < 0 || (int64_t)k >= nrows_b) { bad = true; continue; }
-            const int2 d = ana[k];
-            f += d.x;
-            cp += d.y;
+    for (int64_t i0 = (int64_t)blockIdx.x * (blockDim.x / AN_G); i0 < nrows; i0 += rstride) {
+        const int64_t i = i0 + threadIdx.x / AN_G;
+        const bool live = i < nrows;
+        long long f = 0, cp = 0;
+        if (live) {
+            for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += AN_G) {
+                int k = acol[p];
+                if (k < 0 || (int64_t)k >= nrows_b) { bad = true; continue; }
+                const int2 d = ana[k];
+                f += d.x;
+                cp += d.y;
+            }
         }
-    }
-    for (int d = AN_G / 2; d > 0; d >>= 1) {
-        f += __shfl_xor_sync(gmask, f, d, AN_G);
-        cp += __shfl_xor_sync(gmask, cp, d, AN_G);
+        for (int d = AN_G / 2; d > 0; d >>= 1) {
+            f += __shfl_xor_sync(gmask, f, d, AN_G);
+            cp += __shfl_xor_sync(gmask, cp, d, AN_G);
+        }
+        int b = BIN_EMPTY;
+        const bool lead = live && lane == 0;
+        if (lead) {
+            const long long keys = min(cp, (long long)nwords);
+            b = sym_bin(keys, cp);
+            flops[i] = f;
+            bins[i] = (uint8_t)b;
+            if (b == BIN_EMPTY) crp[i + 1] = 0;
+            if (b == BIN_HUGE) crp[i + 1] = -1;
+            wf += f;
+            wl = max(wl, (long long)(arp[i + 1] - arp[i]));
+        }
+        warp_hist(hist, lead, b);
     }
     if (bad) atomicOr(&st->err, DERR_COL_RANGE);
-    int b = BIN_EMPTY;
-    const bool lead = live && lane == 0;
-    if (lead) {
-        const long long keys = min(cp, (long long)nwords);
-        b = sym_bin(keys, cp);
-        flops[i] = f;
-        bins[i] = (uint8_t)b;
-        if (b == BIN_EMPTY) crp[i + 1] = 0;
-        if (b == BIN_HUGE) crp[i + 1] = -1;
-    }
-    warp_hist(hist, lead, b);
-    // products of the warp's rows (lane 0 of each group holds its row's count)
-    long long wf = lead ? f : 0;
-    long long wl = lead ? (long long)(arp[i + 1] - arp[i]) : 0;   // longest row of A
+    // products of the warp's rows and its longest row of A
     for (int d = 16; d > 0; d >>= 1) {
         wf += __shfl_xor_sync(0xffffffffu, wf, d);
         wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, d));
@@ -152,6 +158,7 @@ int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int2 *ana, in
     if (A.nrows == 0) return SPGEMM_OK;
     int64_t threads = A.nrows * AN_G;
     int64_t blocks = (threads + 255) / 256;
+    blocks = std::min<int64_t>(blocks, (int64_t)c.nsm * 16);
     int64_t nwords = (B.ncols + 31) / 32;
     c.begin("analyze", A.nrows);
     k_analyze<<<(unsigned)blocks, 256, 0, c.s>>>(A.nrows, B.nrows, nwords, A.row_ptr, A.col_idx,
