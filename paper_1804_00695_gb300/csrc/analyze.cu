@@ -168,6 +168,39 @@ int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int2 *ana, in
     return SPGEMM_OK;
 }
 
+__global__ void k_list_spans(const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                             const int2 *__restrict__ bmm, const int32_t *__restrict__ rows, int64_t count,
+                             int2 *__restrict__ spans) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < count; t += warps) {
+        const int i = rows[t];
+        int lo = INT_MAX, hi = -1;
+        for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += 32) {
+            const int2 m = bmm[acol[p]];
+            lo = min(lo, m.x);
+            hi = max(hi, m.y);
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+        }
+        if (lane == 0) spans[t] = make_int2(lo, hi >= lo ? hi - lo + 1 : 0);
+    }
+}
+
+int launch_list_spans(const spgemm_csr &A, const int2 *bmm, const int32_t *rows, int64_t count, int2 *spans,
+                      Ctx &c) {
+    if (count <= 0) return SPGEMM_OK;
+    int64_t blocks = (count + 7) / 8;
+    blocks = std::min<int64_t>(blocks, (int64_t)c.nsm * 16);
+    c.begin("list_spans", count);
+    k_list_spans<<<(unsigned)blocks, 256, 0, c.s>>>(A.row_ptr, A.col_idx, bmm, rows, count, spans);
+    c.end();
+    SG_CUDA(cudaGetLastError());
+    return SPGEMM_OK;
+}
+
 // Products per row only (inspection entry point).
 __global__ void k_row_flops(int64_t nrows, int64_t nrows_b, const int64_t *__restrict__ arp,
                             const int32_t *__restrict__ acol, const int64_t *__restrict__ brp,

@@ -246,12 +246,13 @@ static int lanes_for(double x, int lo = 8) {
     return g;
 }
 
-// Workspace: [bins | rows | B descriptors] persist from symbolic to numeric;
-// after them the symbolic scratch, or (later) the numeric scratch, which may
-// overlap it.
-static size_t ws_persist(int64_t n, int64_t nb) {
+// Workspace: [bins | rows | B descriptors | B block ranges | spans of the
+// listed rows] persist from symbolic to numeric; after them the symbolic
+// scratch, or (later) the numeric scratch, which may overlap it.
+static size_t ws_spans(int64_t n, int64_t nb) {
     return align_up((size_t)n) + align_up((size_t)n * 4) + align_up((size_t)nb * 16) + align_up((size_t)nb * 8);
 }
+static size_t ws_persist(int64_t n, int64_t nb) { return ws_spans(n, nb) + align_up((size_t)n * 8); }
 
 int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *C_row_ptr,
                     int64_t *nnz_C, void *stream) {
@@ -315,8 +316,13 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         for (int b = 2; b < NBINS; b++) h->sym_counts[b] = h->hstate->bin_count[0][b];
         if (second > 0) {
             SG_TRY(launch_scatter_bins(n, bins, C_row_ptr, rows, h->dstate, 0, c));
+            // spans of the rows of bins 2..5 (the lists come in bin order)
+            int2 *spans = (int2 *)(w + ws_spans(n, B->nrows));
+            long long spanned = 0;
+            for (int b = 2; b < BIN_HUGE; b++) spanned += h->hstate->bin_count[0][b];
+            SG_TRY(launch_list_spans(*A, minmax, rows, spanned, spans, c));
             SG_TRY(launch_symbolic(*A, *B, pairs, ccnt, rows, h->hstate->bin_count[0], C_row_ptr,
-                                   &h->dstate->err, w + o_gws, gws_bytes, minmax, c));
+                                   &h->dstate->err, w + o_gws, gws_bytes, spans, c));
         }
         SG_TRY(launch_scan_counts(C_row_ptr, n, &h->dstate->nnz, w + o_tmp, c));
         SG_TRY(launch_numeric_binning(n, C_row_ptr, flops, bins, h->dstate, c));
@@ -370,6 +376,7 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     const int4 *bdesc = (const int4 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4));
     const int2 *bmm = (const int2 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4) +
                                      align_up((size_t)B->nrows * 16));
+    int2 *spans = (int2 *)(h->ws + ws_spans(n, B->nrows));
     float2 *bsplit = (float2 *)(h->ws + ws_persist(n, B->nrows));
     char *gws = h->ws + ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
@@ -387,9 +394,13 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     for (int b = first_list; b <= BIN_HUGE; b++) listed += h->num_counts[b];
     if (listed > 0 && h->num_lists != first_list) {
         SG_TRY(launch_scatter_bins(n, bins, C->row_ptr, rows, h->dstate, 1, c, first_list));
+        // spans of the listed rows up to bin 4 (the kernels that choose by span)
+        long long spanned = 0;
+        for (int b = first_list; b <= 4; b++) spanned += h->num_counts[b];
+        SG_TRY(launch_list_spans(*A, bmm, rows, spanned, spans, c));
         h->num_lists = first_list;
     }
-    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, bmm, rows, h->num_counts,
+    return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, spans, rows, h->num_counts,
                           h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, tune, h->b_sorted,
                           h->max_alen, c);
 }

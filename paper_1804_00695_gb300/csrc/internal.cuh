@@ -168,22 +168,30 @@ int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, 
 int launch_scatter_bins(int64_t n, const uint8_t *bins, const int64_t *crp, int32_t *rows,
                         DevState *st, int phase, Ctx &c, int first_bin = 3);
 int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, int *err, Ctx &c);
+// Column-block span of each listed row of C, once for all the kernels that
+// choose by it: spans[t] = {first block, number of blocks} of the blocks the
+// rows of B reached by row rows[t] of A cover (bmm[k] = {first block, last
+// block} of B_k); {INT_MAX, 0} when they cover none.
+int launch_list_spans(const spgemm_csr &A, const int2 *bmm, const int32_t *rows, int64_t count, int2 *spans,
+                      Ctx &c);
 
 // symbolic.cu
 // First pass over all rows with a 32-slot map and G lanes per row.
 int launch_symbolic_first(const spgemm_csr &A, const uint8_t *bins, const int4 *desc,
                           const int2 *pairs, int64_t *crp, DevState *st, int G, Ctx &c);
 // Second pass: kernels of bins 2..6; counts[b] = rows in bin b (host),
-// rows = concatenated bin lists.  Writes nnz(C_i) to crp[i+1].
+// rows = concatenated bin lists, spans[t] = span of rows[t] (bins 2..5).
+// Writes nnz(C_i) to crp[i+1].
 int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
                     const int32_t *ccnt, const int32_t *rows, const long long *counts,
-                    int64_t *crp, int *err, void *gws, size_t gws_bytes, const int2 *bmm, Ctx &c);
+                    int64_t *crp, int *err, void *gws, size_t gws_bytes, const int2 *spans, Ctx &c);
 size_t symbolic_global_ws(int64_t ncols_b, int nsm);
 
 // numeric.cu
 // Runs the numeric kernels: bins 1-2 over all rows in order (bins[i]), bins
-// 3..6 from the row lists (counts[b] rows in bin b, host).  FP64 uses
-// double-word accumulation unless f64_native; bsplit: room for nnz(B) float2.
+// 3..6 from the row lists (counts[b] rows in bin b, host; spans[t] = span of
+// rows[t] for the lists of bins up to 4).  FP64 uses double-word
+// accumulation unless f64_native; bsplit: room for nnz(B) float2.
 // Tunables of the numeric phase: lanes per row of the small-row kernel,
 // largest output row it takes (16 or 32; bin 2 rows go to the warp kernel
 // when 16), and map slots per output entry (2 or 4).
@@ -193,7 +201,7 @@ struct NumTune {
     int slot_factor = 2;
 };
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B,
-                   spgemm_csr &C, const uint8_t *bins, const int4 *bdesc, const int2 *bmm,
+                   spgemm_csr &C, const uint8_t *bins, const int4 *bdesc, const int2 *spans,
                    const int32_t *rows,
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
                    size_t gws_bytes, int64_t max_row_nnz, const NumTune &tune, bool b_sorted,

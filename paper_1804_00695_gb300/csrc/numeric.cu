@@ -474,31 +474,6 @@ __device__ __forceinline__ void bitonic(int *k, V *v, int P, int tid, int NT, Sy
     }
 }
 
-// Column span of row i in 32-column blocks, from the blocks B_k reaches
-// (bmm[k] = {first block, last block}); a warp computes it, all lanes return it.
-__device__ __forceinline__ int row_span_blocks(const NumP &a, const int2 *__restrict__ bmm, int64_t i,
-                                               int &bmin) {
-    const int lane = threadIdx.x & 31;
-    const int64_t p0 = a.arp[i], p1 = a.arp[i + 1];
-    int lo = INT_MAX, hi = -1;
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-        const int2 m = bmm[a.acol[p]];
-        lo = min(lo, m.x);
-        hi = max(hi, m.y);
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
-    }
-    bmin = lo;
-    return hi >= lo ? hi - lo + 1 : 0;
-}
-
-__device__ __forceinline__ int row_span_words(const NumP &a, const int2 *__restrict__ bmm, int64_t i) {
-    int bmin;
-    return row_span_blocks(a, bmm, i, bmin);
-}
-
 // Which dense rank accumulator takes a row of bins 3-4 (0: none, the hash
 // maps of k_num_wide do): the smallest whose bitmap covers the row's span
 // of 32-column blocks and whose value array holds its outputs.  Smaller
@@ -542,7 +517,7 @@ struct RankLayout {
 // leaves its bitmap words and summary zero for the next.
 template <int BW, int NMAX, int WPB, int MODE>
 __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__restrict__ bdesc,
-                                                       const int2 *__restrict__ bmm,
+                                                       const int2 *__restrict__ spans,
                                                        const int32_t *__restrict__ rows, int64_t count,
                                                        int tier, const DevState *st, int *err) {
     using Lay = RankLayout<BW, NMAX, WPB, MODE>;
@@ -572,8 +547,8 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__
         const int64_t out = a.crp[i];
         const int nn = (int)(a.crp[i + 1] - out);
         if (nn > NMAX) continue;
-        int bmin;
-        const int nw = row_span_blocks(a, bmm, i, bmin);
+        const int2 sp = spans[t];
+        const int bmin = sp.x, nw = sp.y;
         if (nw > BW || nw == 0 || rank_tier(nw, nn) != tier) continue;
         const int64_t p0 = a.arp[i];
         const int plen = (int)(a.arp[i + 1] - p0);
@@ -774,7 +749,7 @@ struct WideLayout {
 
 template <int SMAX, int BW, int WPB, int MODE>
 __global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__restrict__ bdesc,
-                                                       const int2 *__restrict__ bmm,
+                                                       const int2 *__restrict__ spans,
                                                        const int32_t *__restrict__ rows, int64_t count,
                                                        int min_nnz, int min_span_words, const DevState *st,
                                                        int *err) {
@@ -804,7 +779,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__
         const int64_t out = a.crp[i];
         const int nn = (int)(a.crp[i + 1] - out);
         if (nn < min_nnz || nn > SMAX / 2) continue;
-        if (min_span_words > 0 && rank_tier(row_span_words(a, bmm, i), nn) != 0) continue;
+        if (min_span_words > 0 && rank_tier(spans[t].y, nn) != 0) continue;
         int S = next_pow2(2 * nn);
         S = S < 32 ? 32 : (S > SMAX ? SMAX : S);
         const int L = __ffs(S) - 1;
@@ -1412,14 +1387,14 @@ static int run_small_g(const NumTune &t, const NumP &a, const int4 *bdesc, int64
 }
 
 template <int BW, int NMAX, int WPB, int MODE>
-static int run_rank(const NumP &a, const int4 *bdesc, const int2 *bmm, const int32_t *rows, int64_t count,
+static int run_rank(const NumP &a, const int4 *bdesc, const int2 *spans, const int32_t *rows, int64_t count,
                     int tier, DevState *st, int *err, const char *label, Ctx &c) {
     const size_t smem = RankLayout<BW, NMAX, WPB, MODE>::bytes;
     SG_TRY(prep(k_num_rank<BW, NMAX, WPB, MODE>, smem));
     int64_t blocks = (count + WPB - 1) / WPB;
     blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
     c.begin(label, count);
-    k_num_rank<BW, NMAX, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, bmm, rows, count,
+    k_num_rank<BW, NMAX, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, spans, rows, count,
                                                                                 tier, st, err);
     c.end();
     SG_CUDA(cudaGetLastError());
@@ -1427,14 +1402,14 @@ static int run_rank(const NumP &a, const int4 *bdesc, const int2 *bmm, const int
 }
 
 template <int SMAX, int BW, int WPB, int MODE>
-static int run_wide(const NumP &a, const int4 *bdesc, const int2 *bmm, const int32_t *rows, int64_t count,
+static int run_wide(const NumP &a, const int4 *bdesc, const int2 *spans, const int32_t *rows, int64_t count,
                     int min_nnz, int min_span, DevState *st, int *err, const char *label, Ctx &c) {
     const size_t smem = WideLayout<SMAX, BW, WPB, MODE>::bytes;
     SG_TRY(prep(k_num_wide<SMAX, BW, WPB, MODE>, smem));
     int64_t blocks = (count + WPB - 1) / WPB;
     blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
     c.begin(label, count);
-    k_num_wide<SMAX, BW, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, bmm, rows, count, min_nnz,
+    k_num_wide<SMAX, BW, WPB, MODE><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(a, bdesc, spans, rows, count, min_nnz,
                                                                                 min_span, st, err);
     c.end();
     SG_CUDA(cudaGetLastError());
@@ -1513,7 +1488,7 @@ static int run_window(const NumP &a, const int32_t *rows, int64_t cnt, int *err,
 
 template <int MODE>
 static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, const uint8_t *bins,
-                   const int4 *bdesc, const int2 *bmm, const int32_t *rows, const long long *counts, DevState *st,
+                   const int4 *bdesc, const int2 *spans, const int32_t *rows, const long long *counts, DevState *st,
                    void *gws, size_t gws_bytes, int64_t max_row_nnz, const NumTune &t, bool b_sorted,
                    int64_t max_alen, Ctx &c) {
     using V = typename std::conditional<MODE == MODE_F32, float, double>::type;
@@ -1525,6 +1500,7 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
     for (int b = first_list; b <= BIN_HUGE; b++) {
         const int64_t cnt = counts[b];
         const int32_t *r = rows + off;
+        const int2 *sp = spans + off;
         off += cnt;
         if (cnt == 0) continue;
         switch (b) {
@@ -1533,17 +1509,17 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
             case 4:
                 // dense rank accumulators for the rows rank_takes accepts (two span
                 // limits), hash maps for the others (two map sizes)
-                SG_TRY((run_rank<RANK_BW1, RANK_NMAX1, 8, MODE>(a, bdesc, bmm, r, cnt, 1, st, err,
+                SG_TRY((run_rank<RANK_BW1, RANK_NMAX1, 8, MODE>(a, bdesc, sp, r, cnt, 1, st, err,
                                                                  "numeric.rank512", c)));
-                SG_TRY((run_rank<RANK_BW2, RANK_NMAX2, 8, MODE>(a, bdesc, bmm, r, cnt, 2, st, err,
+                SG_TRY((run_rank<RANK_BW2, RANK_NMAX2, 8, MODE>(a, bdesc, sp, r, cnt, 2, st, err,
                                                                  "numeric.rank1024", c)));
-                SG_TRY((run_rank<RANK_BW3, RANK_NMAX3, 4, MODE>(a, bdesc, bmm, r, cnt, 3, st, err,
+                SG_TRY((run_rank<RANK_BW3, RANK_NMAX3, 4, MODE>(a, bdesc, sp, r, cnt, 3, st, err,
                                                                  "numeric.rank2048", c)));
                 if (b <= 3) {
-                    SG_TRY((run_wide<256, 1024, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 1, st, err, "numeric.wide3", c)));
+                    SG_TRY((run_wide<256, 1024, 8, MODE>(a, bdesc, sp, r, cnt, 0, 1, st, err, "numeric.wide3", c)));
                 } else {
-                    SG_TRY((run_wide<512, 2048, 8, MODE>(a, bdesc, bmm, r, cnt, 0, 1, st, err, "numeric.wide4a", c)));
-                    SG_TRY((run_wide<2048, 2048, 4, MODE>(a, bdesc, bmm, r, cnt, 257, 1, st, err, "numeric.wide4b", c)));
+                    SG_TRY((run_wide<512, 2048, 8, MODE>(a, bdesc, sp, r, cnt, 0, 1, st, err, "numeric.wide4a", c)));
+                    SG_TRY((run_wide<2048, 2048, 4, MODE>(a, bdesc, sp, r, cnt, 257, 1, st, err, "numeric.wide4b", c)));
                 }
                 break;
             case 5: SG_TRY((run_block<256, 8192, V>(a, r, cnt, err, b, c))); break;
@@ -1556,16 +1532,16 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
 }
 
 int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C,
-                   const uint8_t *bins, const int4 *bdesc, const int2 *bmm, const int32_t *rows,
+                   const uint8_t *bins, const int4 *bdesc, const int2 *spans, const int32_t *rows,
                    const long long *counts, DevState *st, float2 *bsplit, void *gws,
                    size_t gws_bytes, int64_t max_row_nnz, const NumTune &G, bool b_sorted,
                    int64_t max_alen, Ctx &c) {
     NumP a{A.row_ptr, A.col_idx, A.values, B.row_ptr, B.col_idx, B.values, bsplit,
            C.row_ptr, C.col_idx, C.values};
     if (dtype == SPGEMM_F32)
-        return run_all<MODE_F32>(a, A, B, bins, bdesc, bmm, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
+        return run_all<MODE_F32>(a, A, B, bins, bdesc, spans, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
     if (f64_native)
-        return run_all<MODE_F64>(a, A, B, bins, bdesc, bmm, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
+        return run_all<MODE_F64>(a, A, B, bins, bdesc, spans, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
     SG_CUDA(cudaMemsetAsync(&st->b_out_of_range, 0, sizeof(int), c.s));
     if (B.nnz > 0) {
         int64_t blocks = (B.nnz + 255) / 256;
@@ -1575,7 +1551,7 @@ int launch_numeric(int dtype, bool f64_native, const spgemm_csr &A, const spgemm
         c.end();
         SG_CUDA(cudaGetLastError());
     }
-    return run_all<MODE_DW>(a, A, B, bins, bdesc, bmm, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
+    return run_all<MODE_DW>(a, A, B, bins, bdesc, spans, rows, counts, st, gws, gws_bytes, max_row_nnz, G, b_sorted, max_alen, c);
 }
 
 }  // namespace sg

@@ -247,25 +247,6 @@ __global__ void __launch_bounds__(256) k_sym_first_strided(
     }
 }
 
-// Column-block span of row i of C from the block ranges of the rows of B it
-// reaches (bmm[k] = {first block, last block}); all lanes of the warp get it.
-__device__ __forceinline__ int sym_row_span(const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
-                                            const int2 *__restrict__ bmm, int64_t i, int &bmin) {
-    const int lane = threadIdx.x & 31;
-    int lo = INT_MAX, hi = -1;
-    for (int64_t p = arp[i] + lane; p < arp[i + 1]; p += 32) {
-        const int2 m = bmm[acol[p]];
-        lo = min(lo, m.x);
-        hi = max(hi, m.y);
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
-    }
-    bmin = lo;
-    return hi >= lo ? hi - lo + 1 : 0;
-}
-
 // Second pass for rows whose column blocks span at most BW blocks: a warp
 // per row ORs the compressed pairs into a bitmap over the span (one word
 // per block) and counts its bits; a summary bitmap (one bit per word) lists
@@ -283,7 +264,7 @@ template <int BW, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_sym_span(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
-    const int2 *__restrict__ pairs, const int2 *__restrict__ bmm, const int32_t *__restrict__ rows,
+    const int2 *__restrict__ pairs, const int2 *__restrict__ spans, const int32_t *__restrict__ rows,
     int64_t count, int64_t *__restrict__ crp) {
     using Lay = SpanLayout<BW, WPB>;
     constexpr int NS = Lay::NS, E = Lay::E;
@@ -298,8 +279,8 @@ __global__ void __launch_bounds__(WPB * 32) k_sym_span(
     __syncwarp();
     for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
-        int bmin;
-        const int nw = sym_row_span(arp, acol, bmm, i, bmin);
+        const int2 sp = spans[t];
+        const int bmin = sp.x, nw = sp.y;
         if (nw > BW) continue;
         const int64_t p0 = arp[i];
         const int plen = (int)(arp[i + 1] - p0);
@@ -355,7 +336,7 @@ __global__ void __launch_bounds__(256) k_sym_warp(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
-    int64_t *__restrict__ crp, int *err, const int2 *__restrict__ bmm, int skip_span) {
+    int64_t *__restrict__ crp, int *err, const int2 *__restrict__ spans, int skip_span) {
     constexpr int L = __builtin_ctz(S), WPB = 8;
     extern __shared__ int smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -364,10 +345,7 @@ __global__ void __launch_bounds__(256) k_sym_warp(
     bool fail = false;
     for (int64_t t = (int64_t)blockIdx.x * WPB + w; t < count; t += (int64_t)gridDim.x * WPB) {
         const int i = rows[t];
-        if (skip_span > 0) {
-            int bmin;
-            if (sym_row_span(arp, acol, bmm, i, bmin) <= skip_span) continue;
-        }
+        if (skip_span > 0 && spans[t].y <= skip_span) continue;
         for (int s = lane; s < S; s += 32) {
             keys[s] = -1;
             masks[s] = 0;
@@ -400,28 +378,17 @@ __global__ void __launch_bounds__(BS) k_sym_block(
     const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
     const int64_t *__restrict__ brp, const int32_t *__restrict__ ccnt,
     const int2 *__restrict__ pairs, const int32_t *__restrict__ rows, int64_t count,
-    int64_t *__restrict__ crp, int *err, const int2 *__restrict__ bmm, int skip_span) {
+    int64_t *__restrict__ crp, int *err, const int2 *__restrict__ spans, int skip_span) {
     constexpr int L = __builtin_ctz(S);
     extern __shared__ int smem[];
     __shared__ int red[BS / 32];
-    __shared__ int span_s;
     int *keys = smem;
     unsigned *masks = (unsigned *)(smem + S);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     bool fail = false;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
         const int i = rows[t];
-        if (skip_span > 0) {
-            if (w == 0) {
-                int bmin;
-                const int sp = sym_row_span(arp, acol, bmm, i, bmin);
-                if (lane == 0) span_s = sp;
-            }
-            __syncthreads();
-            const int sp = span_s;
-            __syncthreads();
-            if (sp <= skip_span) continue;
-        }
+        if (skip_span > 0 && spans[t].y <= skip_span) continue;   // uniform over the block
         for (int s = threadIdx.x; s < S; s += BS) {
             keys[s] = -1;
             masks[s] = 0;
@@ -547,14 +514,14 @@ static const char *SYM_LABEL[NBINS] = {"", "", "symbolic.bin2", "symbolic.bin3",
 template <int S>
 static int run_warp(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt, const int2 *pairs,
                     const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c,
-                    const int2 *bmm, int skip_span) {
+                    const int2 *spans, int skip_span) {
     size_t smem = (size_t)8 * S * 8;
     SG_TRY(prep(k_sym_warp<S>, smem));
     int64_t blocks = (count + 7) / 8;
     blocks = blocks < (int64_t)c.nsm * 32 ? blocks : (int64_t)c.nsm * 32;
     c.begin(SYM_LABEL[b], count);
     k_sym_warp<S><<<(unsigned)blocks, 256, smem, c.s>>>(A.row_ptr, A.col_idx, brp, ccnt, pairs, rows,
-                                                         count, crp, err, bmm, skip_span);
+                                                         count, crp, err, spans, skip_span);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -563,13 +530,13 @@ static int run_warp(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt
 template <int BS, int S>
 static int run_block(const spgemm_csr &A, const int64_t *brp, const int32_t *ccnt, const int2 *pairs,
                      const int32_t *rows, int64_t count, int64_t *crp, int *err, int b, Ctx &c,
-                     const int2 *bmm, int skip_span) {
+                     const int2 *spans, int skip_span) {
     size_t smem = (size_t)S * 8;
     SG_TRY(prep(k_sym_block<BS, S>, smem));
     int64_t blocks = count < (int64_t)c.nsm * 16 ? count : (int64_t)c.nsm * 16;
     c.begin(SYM_LABEL[b], count);
     k_sym_block<BS, S><<<(unsigned)blocks, BS, smem, c.s>>>(A.row_ptr, A.col_idx, brp, ccnt, pairs,
-                                                            rows, count, crp, err, bmm, skip_span);
+                                                            rows, count, crp, err, spans, skip_span);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -581,13 +548,14 @@ constexpr int SPAN_BW = 2048;
 
 int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
                     const int32_t *ccnt, const int32_t *rows, const long long *counts,
-                    int64_t *crp, int *err, void *gws, size_t gws_bytes, const int2 *bmm, Ctx &c) {
+                    int64_t *crp, int *err, void *gws, size_t gws_bytes, const int2 *spans, Ctx &c) {
     const int nsm = c.nsm;
     int64_t off = 0;
     const int64_t *brp = B.row_ptr;
     for (int b = 2; b <= BIN_HUGE; b++) {
         int64_t cnt = counts[b];
         const int32_t *r = rows + off;
+        const int2 *sp = spans + off;
         off += cnt;
         if (cnt == 0) continue;
         if (b <= 5) {
@@ -599,15 +567,15 @@ int launch_symbolic(const spgemm_csr &A, const spgemm_csr &B, const int2 *pairs,
             blocks = blocks < (int64_t)nsm * 32 ? blocks : (int64_t)nsm * 32;
             c.begin(SPAN_LABEL[b], cnt);
             k_sym_span<SPAN_BW, WPB><<<(unsigned)blocks, WPB * 32, smem, c.s>>>(
-                A.row_ptr, A.col_idx, brp, ccnt, pairs, bmm, r, cnt, crp);
+                A.row_ptr, A.col_idx, brp, ccnt, pairs, sp, r, cnt, crp);
             c.end();
             SG_CUDA(cudaGetLastError());
         }
         switch (b) {
-            case 2: SG_TRY((run_warp<128>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
-            case 3: SG_TRY((run_warp<512>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
-            case 4: SG_TRY((run_block<128, 2048>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
-            case 5: SG_TRY((run_block<256, 8192>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, bmm, SPAN_BW))); break;
+            case 2: SG_TRY((run_warp<128>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, sp, SPAN_BW))); break;
+            case 3: SG_TRY((run_warp<512>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, sp, SPAN_BW))); break;
+            case 4: SG_TRY((run_block<128, 2048>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, sp, SPAN_BW))); break;
+            case 5: SG_TRY((run_block<256, 8192>(A, brp, ccnt, pairs, r, cnt, crp, err, b, c, sp, SPAN_BW))); break;
             default: {
                 int64_t nwords = (B.ncols + 31) / 32;
                 bool shared = nwords <= SMEM_BITMAP_WORDS;
