@@ -503,6 +503,8 @@ struct RankVal {
     static constexpr int bytes = MODE == MODE_F32 ? 4 : (MODE == MODE_DW ? 12 : 8);
 };
 
+constexpr int RANK_U = 4;   // products per lane per step in the rank kernels
+
 template <int BW, int NMAX, int WPB, int MODE>
 struct RankLayout {
     static constexpr size_t per_warp =
@@ -567,14 +569,20 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__
         const int sper = (ns + 31) / 32;               // per lane, contiguous
         const int s0 = min(ns, lane * sper), s1 = min(ns, s0 + sper);
         __syncwarp();
+        // a row whose stored a_ik fit one batch is staged once, for both passes
+        bool staged = false;
+        int total1 = 0;
         for (int pass = 0; pass < 2; pass++) {
             for (int pb = 0; pb < plen; pb += E) {
-                int len = 0;
-                if (pb + lane < plen) {
-                    const int4 d = bdesc[a.acol[p0 + pb + lane]];
-                    len = d.z;
-                    eq0[lane] = desc_start(d);
-                    if (pass == 1) {
+                int total;
+                if (pass == 1 && staged) {
+                    total = total1;
+                } else {
+                    int len = 0;
+                    if (pb + lane < plen) {
+                        const int4 d = bdesc[a.acol[p0 + pb + lane]];
+                        len = d.z;
+                        eq0[lane] = desc_start(d);
                         const V av = ((const V *)a.aval)[p0 + pb + lane];
                         if (MODE == MODE_DW && !nat) {
                             bool dummy = true;
@@ -585,81 +593,87 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__
                             ea[lane] = (double)av;
                         }
                     }
+                    int incl = len;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d) incl += y;
+                    }
+                    pre[lane] = incl - len;
+                    if (lane == 31) pre[E] = incl;
+                    total = __shfl_sync(0xffffffffu, incl, 31);
+                    if (pass == 0 && plen <= E) {
+                        staged = true;
+                        total1 = total;
+                    }
+                    __syncwarp();
                 }
-                int incl = len;
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl += y;
-                }
-                pre[lane] = incl - len;
-                if (lane == 31) pre[E] = incl;
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                __syncwarp();
-                // two products per lane per step (t and t + 32), loads issued together
+                // RANK_U products per lane per step (t, t + 32, ...): their
+                // loads of B are issued together, so a row waits for the
+                // memory once per step, not once per product
                 int e = 0;
-                for (int t0 = 0; t0 < total; t0 += 64) {
-                    const int ta = t0 + lane, tb = ta + 32;
-                    int ex = -1, ey = -1;
-                    int64_t qx = 0, qy = 0;
-                    if (ta < total) {
-                        while (pre[e + 1] <= ta) e++;
-                        ex = e;
-                        qx = eq0[e] + (ta - pre[e]);
+                for (int t0 = 0; t0 < total; t0 += 32 * RANK_U) {
+                    int ee[RANK_U], cc[RANK_U];
+                    int64_t qq[RANK_U];
+#pragma unroll
+                    for (int u = 0; u < RANK_U; u++) {
+                        const int tt = t0 + u * 32 + lane;
+                        ee[u] = -1;
+                        qq[u] = 0;
+                        if (tt < total) {
+                            while (pre[e + 1] <= tt) e++;
+                            ee[u] = e;
+                            qq[u] = eq0[e] + (tt - pre[e]);
+                        }
                     }
-                    if (tb < total) {
-                        while (pre[e + 1] <= tb) e++;
-                        ey = e;
-                        qy = eq0[e] + (tb - pre[e]);
-                    }
-                    const int colx = ex >= 0 ? a.bcol[qx] : 0;
-                    const int coly = ey >= 0 ? a.bcol[qy] : 0;
+#pragma unroll
+                    for (int u = 0; u < RANK_U; u++) cc[u] = ee[u] >= 0 ? a.bcol[qq[u]] : 0;
                     if (pass == 0) {
 #pragma unroll
-                        for (int h2 = 0; h2 < 2; h2++) {
-                            if ((h2 ? ey : ex) < 0) continue;
-                            const int col = h2 ? coly : colx;
+                        for (int u = 0; u < RANK_U; u++) {
+                            if (ee[u] < 0) continue;
+                            const int col = cc[u];
                             const int wd = (col >> 5) - bmin;
                             if (atomicOr(&bits[wd], 1u << (col & 31)) == 0)
                                 atomicOr(&summ[wd >> 5], 1u << (wd & 31));
                         }
                     } else if (MODE == MODE_F32) {
-                        const float bx = ex >= 0 ? ((const float *)a.bval)[qx] : 0.f;
-                        const float by = ey >= 0 ? ((const float *)a.bval)[qy] : 0.f;
+                        float bv[RANK_U];
 #pragma unroll
-                        for (int h2 = 0; h2 < 2; h2++) {
-                            const int ee = h2 ? ey : ex;
-                            if (ee < 0) continue;
-                            const int col = h2 ? coly : colx;
+                        for (int u = 0; u < RANK_U; u++) bv[u] = ee[u] >= 0 ? ((const float *)a.bval)[qq[u]] : 0.f;
+#pragma unroll
+                        for (int u = 0; u < RANK_U; u++) {
+                            if (ee[u] < 0) continue;
+                            const int col = cc[u];
                             const int wd = (col >> 5) - bmin;
                             const int r = (int)pref[wd] + __popc(bits[wd] & ((1u << (col & 31)) - 1));
-                            atomicAdd(&vf[r], (float)ea[ee] * (h2 ? by : bx));
+                            atomicAdd(&vf[r], (float)ea[ee[u]] * bv[u]);
                         }
                     } else if (MODE == MODE_DW && !nat) {
-                        const float2 bx = ex >= 0 ? a.bsplit[qx] : make_float2(0.f, 0.f);
-                        const float2 by = ey >= 0 ? a.bsplit[qy] : make_float2(0.f, 0.f);
+                        float2 bv[RANK_U];
 #pragma unroll
-                        for (int h2 = 0; h2 < 2; h2++) {
-                            const int ee = h2 ? ey : ex;
-                            if (ee < 0) continue;
-                            const int col = h2 ? coly : colx;
+                        for (int u = 0; u < RANK_U; u++) bv[u] = ee[u] >= 0 ? a.bsplit[qq[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < RANK_U; u++) {
+                            if (ee[u] < 0) continue;
+                            const int col = cc[u];
                             const int wd = (col >> 5) - bmin;
                             const int r = (int)pref[wd] + __popc(bits[wd] & ((1u << (col & 31)) - 1));
-                            const unsigned long long bb = (unsigned long long)__double_as_longlong(ea[ee]);
+                            const unsigned long long bb = (unsigned long long)__double_as_longlong(ea[ee[u]]);
                             const float2 a2 = make_float2(__uint_as_float((unsigned)bb),
                                                           __uint_as_float((unsigned)(bb >> 32)));
-                            dw_atomic_acc(v2, v3, r, dw_mul(a2, h2 ? by : bx));
+                            dw_atomic_acc(v2, v3, r, dw_mul(a2, bv[u]));
                         }
                     } else {
-                        const double bx = ex >= 0 ? ((const double *)a.bval)[qx] : 0.0;
-                        const double by = ey >= 0 ? ((const double *)a.bval)[qy] : 0.0;
+                        double bv[RANK_U];
 #pragma unroll
-                        for (int h2 = 0; h2 < 2; h2++) {
-                            const int ee = h2 ? ey : ex;
-                            if (ee < 0) continue;
-                            const int col = h2 ? coly : colx;
+                        for (int u = 0; u < RANK_U; u++) bv[u] = ee[u] >= 0 ? ((const double *)a.bval)[qq[u]] : 0.0;
+#pragma unroll
+                        for (int u = 0; u < RANK_U; u++) {
+                            if (ee[u] < 0) continue;
+                            const int col = cc[u];
                             const int wd = (col >> 5) - bmin;
                             const int r = (int)pref[wd] + __popc(bits[wd] & ((1u << (col & 31)) - 1));
-                            atomicAdd(&v8[r], ea[ee] * (h2 ? by : bx));
+                            atomicAdd(&v8[r], ea[ee[u]] * bv[u]);
                         }
                     }
                 }
