@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(256) k_sym_first_strided(
 // The pairs of the row are dealt out over the lanes through prefix sums of
 // pairs(B_k), as in the first pass.  A union of compressed sets by bitwise
 // OR, with no hash map (Section 2.1).
+constexpr int SPAN_U = 4;   // pairs per lane per step in k_sym_span
+
 template <int BW, int WPB>
 struct SpanLayout {
     static constexpr int NS = BW / 32, E = 32;
@@ -300,14 +302,27 @@ __global__ void __launch_bounds__(WPB * 32) k_sym_span(
             if (lane == 31) pre[E] = incl;
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             __syncwarp();
+            // SPAN_U pairs per lane per step, their loads issued together
             int e = 0;
-            for (int t0 = 0; t0 < total; t0 += 32) {
-                const int tt = t0 + lane;
-                if (tt < total) {
-                    while (pre[e + 1] <= tt) e++;
-                    const int2 pr = pairs[eq0[e] + (tt - pre[e])];
-                    const int wd = pr.x - bmin;
-                    if (atomicOr(&bits[wd], (unsigned)pr.y) == 0) atomicOr(&summ[wd >> 5], 1u << (wd & 31));
+            for (int t0 = 0; t0 < total; t0 += 32 * SPAN_U) {
+                int64_t qq[SPAN_U];
+                int2 pr[SPAN_U];
+#pragma unroll
+                for (int u = 0; u < SPAN_U; u++) {
+                    const int tt = t0 + u * 32 + lane;
+                    qq[u] = -1;
+                    if (tt < total) {
+                        while (pre[e + 1] <= tt) e++;
+                        qq[u] = eq0[e] + (tt - pre[e]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < SPAN_U; u++) pr[u] = qq[u] >= 0 ? pairs[qq[u]] : make_int2(0, 0);
+#pragma unroll
+                for (int u = 0; u < SPAN_U; u++) {
+                    if (qq[u] < 0) continue;
+                    const int wd = pr[u].x - bmin;
+                    if (atomicOr(&bits[wd], (unsigned)pr[u].y) == 0) atomicOr(&summ[wd >> 5], 1u << (wd & 31));
                 }
             }
             __syncwarp();
