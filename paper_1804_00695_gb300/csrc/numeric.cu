@@ -324,28 +324,41 @@ __global__ void __launch_bounds__(256, G <= 4 ? 2 : 4) k_num_small(NumP a, const
             const int total = __shfl_sync(0xffffffffu, incl, gbase + G - 1);
             const int maxtot = __reduce_max_sync(0xffffffffu, total);
             __syncwarp();
-            int e = 0;
+            // the lane's current stored entry: its first product (pe), the
+            // next entry's (pn), its start in B and its value, in registers;
+            // reloaded only when the cursor moves on
+            int e = 0, pe = 0, pn = pre[1];
+            long long q0 = eq0[0];
+            double ae = ea[0];
             for (int t0 = 0; t0 < maxtot; t0 += G) {
                 const int t = t0 + gl;
                 const bool valid = t < total;
                 int slot = -1;
                 float px = 0.f, py = 0.f;   // product payload (see acc below)
                 if (valid) {
-                    while (pre[e + 1] <= t) e++;
-                    const int64_t q = eq0[e] + (t - pre[e]);
+                    if (pn <= t) {
+                        do {
+                            e++;
+                            pe = pn;
+                            pn = pre[e + 1];
+                        } while (pn <= t);
+                        q0 = eq0[e];
+                        ae = ea[e];
+                    }
+                    const int64_t q = q0 + (t - pe);
                     slot = map_slot(keys, L, a.bcol[q]);
                     if (slot < 0) flag |= DERR_PROBE;
                     if (MODE == MODE_F32) {
-                        px = (float)ea[e] * ((const float *)a.bval)[q];
+                        px = (float)ae * ((const float *)a.bval)[q];
                     } else if (MODE == MODE_DW && !nat) {
-                        const unsigned long long bits = (unsigned long long)__double_as_longlong(ea[e]);
+                        const unsigned long long bits = (unsigned long long)__double_as_longlong(ae);
                         const float2 a2 = make_float2(__uint_as_float((unsigned)bits),
                                                       __uint_as_float((unsigned)(bits >> 32)));
                         const float2 pr = dw_mul(a2, a.bsplit[q]);
                         px = pr.x;
                         py = pr.y;
                     } else {
-                        const double pd = ea[e] * ((const double *)a.bval)[q];
+                        const double pd = ae * ((const double *)a.bval)[q];
                         px = __int_as_float(__double2loint(pd));
                         py = __int_as_float(__double2hiint(pd));
                     }
