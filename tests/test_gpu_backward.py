@@ -65,10 +65,28 @@ def _wide_case():
     return a, b
 
 
+def _long_rows_case():
+    """Rows of C with more than 1024 entries (searched in global memory) next
+    to short rows (searched in a shared-memory copy of their columns)."""
+    a = I.random_csr(120, 2000, 0.05, 31)
+    b = I.random_csr(2000, 5000, 0.02, 32)
+    keep = np.ones(a.nnz, dtype=bool)
+    rows = np.repeat(np.arange(a.nrows), np.diff(a.row_ptr))
+    for i in range(60):                       # rows 0..59 keep two entries each
+        keep[a.row_ptr[i] + 2:a.row_ptr[i + 1]] = False
+    rp = np.zeros(a.nrows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows[keep], minlength=a.nrows), out=rp[1:])
+    return I.Csr(a.nrows, a.ncols, rp, a.col[keep], a.val[keep]), b
+
+
 @pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 1e-5)])
-@pytest.mark.parametrize("case", ["random", "batch_like", "galerkin", "wide"])
+@pytest.mark.parametrize("case", ["random", "batch_like", "galerkin", "wide", "long_rows"])
 def test_backward_matches_oracle(h, dtype, tol, case):
-    if case == "wide":
+    if case == "long_rows":
+        a, b = _long_rows_case()
+        lens = np.diff(oracle.spgemm(a, b).row_ptr)
+        assert lens.max() > 1024 and lens.min() <= 1024
+    elif case == "wide":
         a, b = _wide_case()
     elif case == "random":
         a = I.random_csr(300, 200, 0.04, 11, shuffle_cols=True)
