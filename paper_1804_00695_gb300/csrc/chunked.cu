@@ -1081,6 +1081,16 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
                 lo_c = hmm[2 * slot];
                 hi_c = hmm[2 * slot + 1];
+                if (hi_c >= 0 && (lo_c < 0 || (int64_t)hi_c >= B.nrows)) {
+                    // a column of A outside the rows of B: stop once the
+                    // copies already issued are done with the arena
+                    cudaStreamSynchronize(si);
+                    cudaStreamSynchronize(so);
+                    cudaStreamSynchronize(s);
+                    set_error("chunked numeric: a column of A lies outside the %lld rows of B",
+                              (long long)B.nrows);
+                    return SPGEMM_ERR_INDEX;
+                }
             }
             // the rows of B this part reaches, as (r0, r1) copies: one window
             // when it fits a buffer, else the fixed parts it overlaps
