@@ -171,7 +171,9 @@ SPGEMM_API int spgemm_plan_chunks(const int64_t *A_row_ptr, int64_t nrows_A, con
  * spgemm_chunked_symbolic fills C_row_ptr (host, nrows(A)+1) and *nnz_C.
  * The pattern of B stays resident while the rows of A stream through, so
  * Algorithm 4 must be able to place the pattern of B (offsets and columns)
- * in the large (75%) portion; otherwise SPGEMM_ERR_BUDGET.  Synchronises.
+ * in the large (75%) portion; otherwise SPGEMM_ERR_BUDGET.  It also records
+ * in the handle the column range of every 1024-row block of A and the
+ * longest row of C, for the numeric call of the same arrays.  Synchronises.
  *
  * spgemm_chunked_numeric fills C->col_idx and C->values (host, C->nnz each,
  * C->row_ptr from spgemm_chunked_symbolic).  Algorithm 4 chooses the row
