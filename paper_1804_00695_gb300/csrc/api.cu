@@ -428,6 +428,12 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
         }
         h->arena_cap = budget;
     }
+    // work a previous call left on the side streams (one that returned an
+    // error part-way) finishes before this call reuses the arena
+    SG_CUDA(cudaEventRecord(h->ev[8], h->s_in));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[8], 0));
+    SG_CUDA(cudaEventRecord(h->ev[9], h->s_out));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[9], 0));
     // work issued before this call on the caller's stream comes first
     SG_CUDA(cudaEventRecord(h->ev[7], s));
     SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[7], 0));
