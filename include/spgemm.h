@@ -282,9 +282,10 @@ SPGEMM_API int spgemm_autotune(spgemm_handle handle, int reps, int64_t *choice, 
 
 /* Row offsets from per-row counts, allocating nothing (this entry point
  * has no counterpart in the paper; it exposes the symbolic phase's scan step
- * for callers that may not allocate device memory: code inside CUDA stream
- * capture, callers whose device memory belongs to another allocator, and
- * paths that cannot afford cudaMalloc's implicit synchronisation).
+ * for callers that may not allocate device memory: programs whose device
+ * memory is wholly owned by another allocator, such as a framework's caching
+ * pool or an arena reserved up front, and latency-critical paths that cannot
+ * afford the implicit device-wide synchronisation of cudaMalloc/cudaFree).
  * row_ptr: device, nrows+1 int64, the count of row i in row_ptr[i+1]
  * (row_ptr[0] is ignored); on completion row_ptr holds the exclusive prefix
  * (row_ptr[0] = 0, row_ptr[nrows] = total).  No handle is needed.  The

@@ -413,8 +413,16 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
         for (auto &e : h->ev) SG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         SG_CUDA(cudaMallocHost(&h->host_mm, 4 * sizeof(int)));
     }
+    // work a previous call left on the side streams (one that returned an
+    // error part-way) finishes before this call reuses or frees the arena
+    SG_CUDA(cudaEventRecord(h->ev[8], h->s_in));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[8], 0));
+    SG_CUDA(cudaEventRecord(h->ev[9], h->s_out));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[9], 0));
     if (h->arena_cap != budget) {
         if (h->arena) {
+            // s now waits for both side streams: nothing queued touches the
+            // arena once it is done
             SG_CUDA(cudaStreamSynchronize(s));
             SG_CUDA(cudaFree(h->arena));
             h->arena = nullptr;
@@ -428,12 +436,6 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
         }
         h->arena_cap = budget;
     }
-    // work a previous call left on the side streams (one that returned an
-    // error part-way) finishes before this call reuses the arena
-    SG_CUDA(cudaEventRecord(h->ev[8], h->s_in));
-    SG_CUDA(cudaStreamWaitEvent(s, h->ev[8], 0));
-    SG_CUDA(cudaEventRecord(h->ev[9], h->s_out));
-    SG_CUDA(cudaStreamWaitEvent(s, h->ev[9], 0));
     // work issued before this call on the caller's stream comes first
     SG_CUDA(cudaEventRecord(h->ev[7], s));
     SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[7], 0));

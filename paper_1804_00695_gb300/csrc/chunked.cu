@@ -1081,7 +1081,10 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
                 lo_c = hmm[2 * slot];
                 hi_c = hmm[2 * slot + 1];
-                if (hi_c >= 0 && (lo_c < 0 || (int64_t)hi_c >= B.nrows)) {
+                // lo_c == INT_MAX only for a part with no entries (hi_c
+                // alone cannot tell: a part whose columns are all negative
+                // leaves it at -1)
+                if (lo_c != INT_MAX && (lo_c < 0 || (int64_t)hi_c >= B.nrows)) {
                     // a column of A outside the rows of B: stop once the
                     // copies already issued are done with the arena
                     cudaStreamSynchronize(si);

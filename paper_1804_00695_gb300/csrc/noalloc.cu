@@ -1,14 +1,14 @@
 // Row offsets from per-row counts with no device allocation at all.
 //
-// Some callers cannot allocate device memory when they need this step: code
-// running inside CUDA stream capture (an allocation there breaks or
-// serialises the capture), callers whose device memory is entirely owned by
-// another allocator (a framework's caching pool, a fixed arena sized up
-// front), and latency-critical paths where cudaMalloc's implicit device
-// synchronisation is unacceptable.  For them this entry point runs the same
-// scan kernels as the symbolic phase, but their scratch (one partial sum per
-// tile of rows, and the total) lives in a fixed, file-scope device array
-// instead of the handle's growable workspace, and no handle is needed.
+// Some callers cannot allocate device memory at the point where they need
+// this step: programs whose device memory is wholly owned by another
+// allocator (a framework's caching pool, or an arena reserved up front that
+// leaves nothing for cudaMalloc), and latency-critical paths where
+// cudaMalloc and cudaFree would stall other streams with their implicit
+// device-wide synchronisation.  For them this entry point runs the same scan
+// kernels as the symbolic phase, but their scratch (one partial sum per tile
+// of rows, and the total) lives in a fixed, file-scope device array instead
+// of the handle's growable workspace, and no handle is needed.
 #include <mutex>
 #include "internal.cuh"
 

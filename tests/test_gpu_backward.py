@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_1804_00695_gb300 as sg
 from paper_1804_00695_gb300 import inputs as I
-from gpu_helpers import to_dev
+from gpu_helpers import assert_grads_match, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -122,6 +122,5 @@ def test_autograd_function(h):
     w = torch.linspace(-1, 1, C.nnz, dtype=torch.float64, device="cuda")
     loss = (C.val * w).sum()
     loss.backward()
-    ra, rb = oracle.backward(a, b, C.row_ptr.cpu().numpy(), C.col.cpu().numpy(), w.cpu().numpy())
-    assert np.allclose(A.val.grad.cpu().numpy(), ra, rtol=1e-10, atol=1e-12)
-    assert np.allclose(B.val.grad.cpu().numpy(), rb, rtol=1e-10, atol=1e-12)
+    assert_grads_match(a, b, C.row_ptr.cpu().numpy(), C.col.cpu().numpy(), w.cpu().numpy(),
+                       A.val.grad.cpu().numpy(), B.val.grad.cpu().numpy(), 1e-12)

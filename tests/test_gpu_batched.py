@@ -6,7 +6,7 @@ import pytest
 import oracle
 import paper_1804_00695_gb300 as sg
 from paper_1804_00695_gb300 import inputs as I
-from gpu_helpers import assert_matches, oracle_product, to_dev
+from gpu_helpers import assert_grads_match, assert_matches, oracle_product, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +85,5 @@ def test_batched_backward(h):
     for (a, b), c, x, y in zip(pairs, bt.split(Cm), ga, gb):
         d = dc[p0:p0 + c.nnz].cpu().numpy()
         p0 += c.nnz
-        ra, rb = oracle.backward(a, b, c.row_ptr.cpu().numpy(), c.col.cpu().numpy(), d)
-        assert np.allclose(x.cpu().numpy(), ra, rtol=1e-11, atol=1e-12)
-        assert np.allclose(y.cpu().numpy(), rb, rtol=1e-11, atol=1e-12)
+        assert_grads_match(a, b, c.row_ptr.cpu().numpy(), c.col.cpu().numpy(), d,
+                           x.cpu().numpy(), y.cpu().numpy(), 1e-12)

@@ -297,3 +297,44 @@ def test_chunked_symbolic_tight_budget_recuts_a(h):
         assert st["device_bytes"] <= budget
         hit = hit or st["n_ac"] >= 3
     assert hit
+
+
+def _with_bad_column(a, part_rows, col_value):
+    """Copy of A whose rows in `part_rows` (a slice) all take column
+    `col_value` in their first entry (rows keep their other entries)."""
+    col = a.col.copy()
+    for r in range(part_rows.start, part_rows.stop):
+        if a.row_ptr[r + 1] > a.row_ptr[r]:
+            col[int(a.row_ptr[r])] = col_value
+    return I.Csr(a.nrows, a.ncols, a.row_ptr, col, a.val)
+
+
+def test_chunked_numeric_bad_columns_without_recorded_ranges():
+    """A fresh handle (no symbolic call, so no recorded ranges) measures each
+    part's column range on the device: a column beyond the rows of B in a
+    middle part, and a part whose every column is negative, both give
+    SPGEMM_ERR_INDEX.  The same handle then multiplies correct operands, with
+    the same budget and with another one (the arena freed and taken again
+    after the error return), against the oracle."""
+    a = I.laplace3d_27pt(20)
+    ref = oracle.spgemm(a, a)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, a.row_ptr, 8, 2, 3, 2)
+    assert budget is not None
+    part = slice(*plan["p_ac"][len(plan["p_ac"]) // 2])
+    import torch
+    rp_host = torch.from_numpy(ref.row_ptr.copy()).pin_memory()
+    B = sg.HostCsr.from_numpy(a)
+    beyond = _with_bad_column(a, part, a.nrows + 5)
+    col = a.col.copy()
+    for r in range(part.start, part.stop):
+        s0, s1 = int(a.row_ptr[r]), int(a.row_ptr[r + 1])
+        col[s0:s1] = -1 - np.arange(s1 - s0)
+    negative = I.Csr(a.nrows, a.ncols, a.row_ptr, col, a.val)
+    for bad in (beyond, negative):
+        h = sg.Handle()
+        with pytest.raises(sg.SpgemmError) as ei:
+            h.chunked_numeric(sg.HostCsr.from_numpy(bad), B, rp_host, ref.nnz, budget)
+        assert ei.value.status == 3
+        for bud in (budget, budget + (1 << 20)):
+            c = h.chunked_numeric(sg.HostCsr.from_numpy(a), B, rp_host, ref.nnz, bud)
+            check(c, ref, "f64")

@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_1804_00695_gb300 as sg
 from paper_1804_00695_gb300 import inputs as I
-from gpu_helpers import assert_matches, oracle_product, to_dev
+from gpu_helpers import assert_matches, host_csr, oracle_product, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -40,16 +40,12 @@ def test_galerkin_small(h, n):
     ap = run(h, a, p)
     ref_ap = oracle.spgemm(a, p)
     assert_matches(ap, ref_ap, "f64")
-    apm = I.Csr(a.nrows, p.ncols, ref_ap.row_ptr, ref_ap.col, ref_ap.val)
-    rap_ref = oracle.spgemm(r, apm)
     R = to_dev(r)
     rap = h.spgemm(R, ap)
     h.check()
-    # second product uses the device AP; compare against the oracle on the oracle AP
-    assert np.array_equal(rap.row_ptr.cpu().numpy(), rap_ref.row_ptr)
-    assert np.array_equal(rap.col.cpu().numpy(), rap_ref.col)
-    err = np.abs(rap.val.cpu().numpy() - rap_ref.val)
-    assert np.all(err <= 1e-12 * rap_ref.bound + 1e-13 * np.abs(rap_ref.val))
+    # the second product consumes the device AP: the oracle takes the same
+    # values as its input, so the stated bound holds with nothing added
+    assert_matches(rap, oracle.spgemm(r, host_csr(ap)), "f64")
 
 
 def test_galerkin_128_full(h):
@@ -63,12 +59,8 @@ def test_galerkin_128_full(h):
     assert_matches(ap, ref_ap, "f64")
     rap = h.spgemm(R, ap)
     h.check()
-    apm = I.Csr(a.nrows, p.ncols, ref_ap.row_ptr, ref_ap.col, ref_ap.val)
-    rap_ref = oracle.spgemm(r, apm)
     assert rap.nnz == 2048383
-    assert np.array_equal(rap.col.cpu().numpy(), rap_ref.col)
-    err = np.abs(rap.val.cpu().numpy() - rap_ref.val)
-    assert np.all(err <= 1e-12 * rap_ref.bound + 1e-13 * np.abs(rap_ref.val))
+    assert_matches(rap, oracle.spgemm(r, host_csr(ap)), "f64")
 
 
 @pytest.mark.parametrize("scale", [8, 11])

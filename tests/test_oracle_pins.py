@@ -285,3 +285,52 @@ def test_validate_errors():
     assert oracle.validate(bad) == 3
     oor = I.Csr(2, 5, np.array([0, 1, 2]), np.array([1, 5], dtype=np.int32), np.ones(2))
     assert oracle.validate(oor) == 2
+
+
+def _row_flops_loops(a, b):
+    """Multiplications of each row of A*B counted with explicit loops: for
+    every stored a_ik, one per stored entry of row k of B (Section 3.1)."""
+    out = []
+    for i in range(a.nrows):
+        f = 0
+        for p in range(int(a.row_ptr[i]), int(a.row_ptr[i + 1])):
+            k = int(a.col[p])
+            f += int(b.row_ptr[k + 1]) - int(b.row_ptr[k])
+        out.append(f)
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("seed,shape,dens", [(81, (40, 60, 30), 0.1), (82, (200, 150, 90), 0.05),
+                                             (83, (1, 50, 20), 0.8), (84, (64, 1, 5), 0.5)])
+def test_row_flops_per_row(seed, shape, dens):
+    """oracle.row_flops row by row against the loop count and against the
+    multiplications the C oracle's symbolic pass counts, on unsorted rows
+    (rows of A with no entries and rows of B with none included)."""
+    m, k, n = shape
+    a = I.random_csr(m, k, dens, seed, shuffle_cols=True)
+    b = I.random_csr(k, n, dens, seed + 7, shuffle_cols=True)
+    got = oracle.row_flops(a, b)
+    assert np.array_equal(got, _row_flops_loops(a, b))
+    _, mults = oracle.symbolic(a, b)
+    assert np.array_equal(got, mults)
+
+
+@pytest.mark.parametrize("n", [6, 11])
+def test_row_flops_galerkin_closed_form(n):
+    """Per-row multiplications of A*P and R*(AP) from 1D factors: the patterns
+    are Kronecker cubes, so row x + n*y + n^2*z of A*P does f(x) f(y) f(z)
+    multiplications with f = T times the row lengths of Tp, and row J of
+    R*(AP) does g(j1) g(j2) g(j3) with g = pattern(Tp)^T times the row
+    lengths of T^2 p (at n = 128 the totals are 634^3 and 464^3, the sizes
+    test_galerkin_128_sizes checks)."""
+    a, p, r = I.galerkin_problem(n)
+    t = _t1(n)
+    p1 = _agg1d(n)
+    tp, t2p = t @ p1, t @ t @ p1
+    f1 = (t != 0).astype(np.int64) @ (tp != 0).sum(1).astype(np.int64)
+    np.testing.assert_array_equal(oracle.row_flops(a, p), np.kron(np.kron(f1, f1), f1))
+    ap = oracle.spgemm(a, p)
+    apm = I.Csr(a.nrows, p.ncols, ap.row_ptr, ap.col, ap.val)
+    g1 = (tp != 0).T.astype(np.int64) @ (t2p != 0).sum(1).astype(np.int64)
+    np.testing.assert_array_equal(oracle.row_flops(r, apm), np.kron(np.kron(g1, g1), g1))
+    assert int(f1.sum()) ** 3 == int(oracle.row_flops(a, p).sum())

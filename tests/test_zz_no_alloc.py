@@ -1,8 +1,10 @@
 """The allocation-free row-offset entry point, for callers that may not
-allocate device memory (inside stream capture, under another allocator, or
-where cudaMalloc's synchronisation is too costly).  Called through the C ABI
-and checked against the offsets spgemm_symbolic produces for the same
-products, on two calls in a row.  Kept in a file of its own, collected last."""
+allocate device memory (their device memory belongs to another allocator, or
+cudaMalloc's device-wide synchronisation would stall their other streams).
+Called through the C ABI and checked, on two calls in a row, against the
+prefix sum of the counts computed on the host and against the offsets
+spgemm_symbolic produces for the same products.  Kept in a file of its own,
+collected last."""
 import ctypes
 
 import numpy as np
@@ -34,12 +36,15 @@ def test_row_offsets_noalloc_matches_symbolic(cuda_lib):
         counts = torch.zeros_like(rp)
         counts[1:] = rp[1:] - rp[:-1]
         counts[0] = 12345                      # ignored by the call
+        host_counts = counts[1:].cpu().numpy()
+        expect = np.concatenate([[0], np.cumsum(host_counts)]).astype(np.int64)
         for _ in range(2):                     # two calls in a row share the scratch
             x = counts.clone()
             rc = lib.spgemm_row_offsets_noalloc(ctypes.c_void_p(x.data_ptr()), a.nrows,
                                                 ctypes.c_void_p(stream))
             assert rc == 0, lib.spgemm_last_error()
             torch.cuda.synchronize()
+            assert np.array_equal(x.cpu().numpy(), expect)
             assert torch.equal(x, rp)
             assert int(x[-1]) == nnz
 
