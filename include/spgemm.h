@@ -128,13 +128,26 @@ SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr 
  *    small-row numeric kernel takes; larger rows go to a warp each.
  *  SPGEMM_OPT_SLOT_FACTOR (2 or 4, default 2): hash-map slots per output
  *    entry in the small-row numeric kernel.
- * spgemm_autotune picks the last three by timing. */
+ *  SPGEMM_OPT_NARROW (0/1, default 1): 1 = rows whose columns all fall
+ *    within 128 consecutive blocks of 32 columns are counted and (with at
+ *    most 32 outputs and 8192 products) multiplied over a dense window of
+ *    the compressed column sets (Section 2.1) instead of hash maps; the
+ *    window gives every column its rank, so those rows need no probe and no
+ *    sort.  They accumulate in native precision whatever
+ *    SPGEMM_OPT_F64_NATIVE says.  Takes effect at the next spgemm_symbolic.
+ *  SPGEMM_OPT_LANES_NARROW_SYMBOLIC (0, 4, 8, 16, 32) and
+ *    SPGEMM_OPT_LANES_NARROW_NUMERIC (0, 4, 8, 16): lanes per row of the
+ *    narrow-row kernels (0 = from the mean length of the rows of A).
+ * spgemm_autotune picks lanes, small-row cap and slot factor by timing. */
 typedef enum spgemm_option {
     SPGEMM_OPT_F64_NATIVE = 1,
     SPGEMM_OPT_LANES_NUMERIC = 2,
     SPGEMM_OPT_LANES_SYMBOLIC = 3,
     SPGEMM_OPT_SMALL_CAP = 4,
-    SPGEMM_OPT_SLOT_FACTOR = 5
+    SPGEMM_OPT_SLOT_FACTOR = 5,
+    SPGEMM_OPT_NARROW = 6,
+    SPGEMM_OPT_LANES_NARROW_SYMBOLIC = 7,
+    SPGEMM_OPT_LANES_NARROW_NUMERIC = 8
 } spgemm_option;
 SPGEMM_API int spgemm_set_option(spgemm_handle handle, int option, int64_t value);
 
@@ -323,7 +336,10 @@ SPGEMM_API int spgemm_compress(spgemm_handle handle, const spgemm_csr *M, int32_
                     uint32_t *pairs, void *stream);
 
 /* Per-bin row counts of the last symbolic and numeric phases on this handle
- * (host array of at least SPGEMM_NBINS int64 each), for tests and tuning. */
+ * (host array of at least SPGEMM_NBINS int64 each), for tests and tuning.
+ * Index 7 counts the narrow rows (SPGEMM_OPT_NARROW): in the symbolic
+ * array the rows counted over a window, in the numeric array the rows
+ * multiplied over one. */
 #define SPGEMM_NBINS 8
 SPGEMM_API int spgemm_bin_counts(spgemm_handle handle, int64_t *symbolic_bins, int64_t *numeric_bins);
 

@@ -68,17 +68,6 @@ int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minma
 }
 
 // ---------------------------------------------------------------- analysis
-// Adds this warp's per-bin row counts (bins held by the lanes where `has`)
-// to a shared histogram with one ballot per bin.
-__device__ __forceinline__ void warp_hist(unsigned long long *hist, bool has, int bin) {
-    const unsigned have = __ballot_sync(0xffffffffu, has);
-    if (!have) return;
-    for (int b = 0; b < NBINS; b++) {
-        unsigned m = __ballot_sync(0xffffffffu, has && bin == b);
-        if (m && (threadIdx.x & 31) == 0) atomicAdd(&hist[b], (unsigned long long)__popc(m));
-    }
-}
-
 // Eight lanes per row of A.  For row i: flops_i = sum_k nnz(B_k) (the number
 // of accumulator insertions, Section 3.1) and cpairs_i = sum_k pairs(B_k).
 // The symbolic accumulator needs at most min(cpairs_i, ceil(ncols/32)) keys
@@ -237,7 +226,7 @@ int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, i
 // ---------------------------------------------------------------- numeric bins
 __global__ void k_numeric_binning(int64_t n, const int64_t *__restrict__ crp,
                                   const int64_t *__restrict__ flops, uint8_t *__restrict__ bins,
-                                  DevState *st) {
+                                  DevState *st, const int32_t *__restrict__ nlo) {
     __shared__ unsigned long long hist[NBINS];
     if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
     __syncthreads();
@@ -245,7 +234,9 @@ __global__ void k_numeric_binning(int64_t n, const int64_t *__restrict__ crp,
     int b = BIN_EMPTY;
     if (i < n) {
         long long c = crp[i + 1] - crp[i];
-        b = c > 0 ? num_bin(c, flops[i]) : BIN_EMPTY;
+        const long long f = flops[i];
+        b = c > 0 ? num_bin(c, f) : BIN_EMPTY;
+        if (b != BIN_EMPTY && nlo && nlo[i] >= 0 && c <= NARROW_NMAX && f <= NARROW_FLOPS) b = BIN_NARROW;
         bins[i] = (uint8_t)b;
         if (b == BIN_HUGE) atomicMax((unsigned long long *)&st->max_row_nnz, (unsigned long long)c);
     }
@@ -256,10 +247,10 @@ __global__ void k_numeric_binning(int64_t n, const int64_t *__restrict__ crp,
 }
 
 int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, uint8_t *bins,
-                           DevState *st, Ctx &c) {
+                           DevState *st, Ctx &c, const int32_t *nlo) {
     if (n == 0) return SPGEMM_OK;
     c.begin("numeric_binning", n);
-    k_numeric_binning<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, crp, flops, bins, st);
+    k_numeric_binning<<<(unsigned)((n + 255) / 256), 256, 0, c.s>>>(n, crp, flops, bins, st, nlo);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;
@@ -289,7 +280,7 @@ __global__ void k_scatter_bins(int64_t n, const uint8_t *__restrict__ bins,
             if (crp[i + 1] < 0) b = max((int)bins[i], 2);
         } else {
             int x = bins[i];
-            if (x >= first_bin) b = x;
+            if (x >= first_bin && x <= BIN_HUGE) b = x;
         }
     }
     unsigned act = __ballot_sync(0xffffffffu, b != BIN_EMPTY);

@@ -74,6 +74,9 @@ struct spgemm_handle_s {
     int small_cap = 32, slot_factor = 2;
     // options
     bool f64_native = true;
+    bool narrow = true;                  // window-table kernels for narrow rows
+    int g_narrow_sym = 0, g_narrow_num = 0;   // their lanes per row (0 = automatic)
+    bool sym_narrow_used = false;        // the last symbolic call ran them
     int g_numeric = 0, g_symbolic = 0;   // lanes per row (0 = from the mean products per row)
     double mean_flops = 0;
     // chunked calls: budget arena, side streams, events, last statistics
@@ -246,13 +249,31 @@ static int lanes_for(double x, int lo = 8) {
     return g;
 }
 
-// Workspace: [bins | rows | B descriptors | B block ranges | spans of the
-// listed rows] persist from symbolic to numeric; after them the symbolic
-// scratch, or (later) the numeric scratch, which may overlap it.
-static size_t ws_spans(int64_t n, int64_t nb) {
-    return align_up((size_t)n) + align_up((size_t)n * 4) + align_up((size_t)nb * 16) + align_up((size_t)nb * 8);
+// Workspace offsets.  [bins | rows | B descriptors | B block ranges | spans
+// of the listed rows | first window block of every row | B's compressed
+// pairs] persist from symbolic to numeric; after them the symbolic scratch,
+// or (later) the numeric scratch, which may overlap it.
+struct WsLayout {
+    size_t bins, rows, desc, mm, spans, nlo, pairs, persist;   // persistent
+    size_t ana, flops, ccnt, tmp, gws;                          // symbolic scratch
+};
+static WsLayout ws_layout(int64_t n, int64_t nb, int64_t nnzb) {
+    WsLayout L;
+    L.bins = 0;
+    L.rows = L.bins + align_up((size_t)n);
+    L.desc = L.rows + align_up((size_t)n * 4);
+    L.mm = L.desc + align_up((size_t)nb * 16);
+    L.spans = L.mm + align_up((size_t)nb * 8);
+    L.nlo = L.spans + align_up((size_t)n * 8);
+    L.pairs = L.nlo + align_up((size_t)n * 4);
+    L.persist = L.pairs + align_up((size_t)nnzb * 8);
+    L.ana = L.persist;
+    L.flops = L.ana + align_up((size_t)nb * 8);
+    L.ccnt = L.flops + align_up((size_t)n * 8);
+    L.tmp = L.ccnt + align_up((size_t)nb * 4);
+    L.gws = L.tmp + align_up(scan_tmp_bytes(n));
+    return L;
 }
-static size_t ws_persist(int64_t n, int64_t nb) { return ws_spans(n, nb) + align_up((size_t)n * 8); }
 
 int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, int64_t *C_row_ptr,
                     int64_t *nnz_C, void *stream) {
@@ -275,35 +296,35 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         memset(h->sym_counts, 0, sizeof(h->sym_counts));
         memset(h->num_counts, 0, sizeof(h->num_counts));
     } else {
-        const size_t o_bins = 0;
-        const size_t o_rows = align_up((size_t)n);
-        const size_t o_desc = o_rows + align_up((size_t)n * 4);
-        const size_t o_ana = ws_persist(n, B->nrows);
-        const size_t o_flops = o_ana + align_up((size_t)B->nrows * 8);
-        const size_t o_pairs = o_flops + align_up((size_t)n * 8);
-        const size_t o_ccnt = o_pairs + align_up((size_t)B->nnz * 8);
-        const size_t o_mm = o_desc + align_up((size_t)B->nrows * 16);   // persistent, after desc
-        const size_t o_tmp = o_ccnt + align_up((size_t)B->nrows * 4);
-        const size_t o_gws = o_tmp + align_up(scan_tmp_bytes(n));
+        const WsLayout L = ws_layout(n, B->nrows, B->nnz);
         const size_t gws_bytes = symbolic_global_ws(B->ncols, h->nsm);
-        SG_TRY(ws_reserve(h, o_gws + gws_bytes, s));
+        SG_TRY(ws_reserve(h, L.gws + gws_bytes, s));
         char *w = h->ws;
-        uint8_t *bins = (uint8_t *)(w + o_bins);
-        int32_t *rows = (int32_t *)(w + o_rows);
-        int64_t *flops = (int64_t *)(w + o_flops);
-        int2 *pairs = (int2 *)(w + o_pairs);
-        int32_t *ccnt = (int32_t *)(w + o_ccnt);
-        int2 *minmax = (int2 *)(w + o_mm);
-        int4 *desc = (int4 *)(w + o_desc);
-        int2 *ana = (int2 *)(w + o_ana);
+        uint8_t *bins = (uint8_t *)(w + L.bins);
+        int32_t *rows = (int32_t *)(w + L.rows);
+        int64_t *flops = (int64_t *)(w + L.flops);
+        int2 *pairs = (int2 *)(w + L.pairs);
+        int32_t *ccnt = (int32_t *)(w + L.ccnt);
+        int2 *minmax = (int2 *)(w + L.mm);
+        int4 *desc = (int4 *)(w + L.desc);
+        int2 *ana = (int2 *)(w + L.ana);
+        int32_t *nlo = (int32_t *)(w + L.nlo);
         Ctx c = h->ctx(s);
         // lanes per row from the mean number of compressed pairs a row visits
-        const double mean_pairs = (double)A->nnz / (double)n *
-                                  ((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1)) * 0.6;
+        const double mean_alen = (double)A->nnz / (double)n;
+        const double mean_pairs = mean_alen * ((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1)) * 0.6;
         const int gs = h->g_symbolic ? h->g_symbolic : lanes_for(mean_pairs / 64.0);
         SG_TRY(launch_compress(*B, pairs, ccnt, minmax, desc, ana, &h->dstate->err, c,
                                &h->dstate->b_unsorted));
-        SG_TRY(launch_analyze(*A, *B, ana, flops, bins, C_row_ptr, h->dstate, c));
+        h->sym_narrow_used = h->narrow;
+        if (h->narrow) {
+            // analysis and the narrow rows' counts in one pass; the first
+            // pass below takes the other rows
+            const int gn = h->g_narrow_sym ? h->g_narrow_sym : lanes_for(mean_alen / 4.0, 4);
+            SG_TRY(launch_sym_narrow(*A, *B, desc, minmax, pairs, flops, bins, C_row_ptr, nlo, h->dstate, gn, c));
+        } else {
+            SG_TRY(launch_analyze(*A, *B, ana, flops, bins, C_row_ptr, h->dstate, c));
+        }
         SG_TRY(launch_symbolic_first(*A, bins, desc, pairs, C_row_ptr, h->dstate, gs, c));
         SG_TRY(fetch_state(h, s));
         SG_TRY(device_errors(h->hstate->err));
@@ -314,18 +335,19 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         h->sym_counts[0] = h->hstate->sym_hist[0];
         h->sym_counts[1] = first - (second - h->hstate->bin_count[0][BIN_HUGE]);
         for (int b = 2; b < NBINS; b++) h->sym_counts[b] = h->hstate->bin_count[0][b];
+        h->sym_counts[BIN_NARROW] = h->hstate->sym_hist[BIN_NARROW];
         if (second > 0) {
             SG_TRY(launch_scatter_bins(n, bins, C_row_ptr, rows, h->dstate, 0, c));
             // spans of the rows of bins 2..5 (the lists come in bin order)
-            int2 *spans = (int2 *)(w + ws_spans(n, B->nrows));
+            int2 *spans = (int2 *)(w + L.spans);
             long long spanned = 0;
             for (int b = 2; b < BIN_HUGE; b++) spanned += h->hstate->bin_count[0][b];
             SG_TRY(launch_list_spans(*A, minmax, rows, spanned, spans, c));
             SG_TRY(launch_symbolic(*A, *B, pairs, ccnt, rows, h->hstate->bin_count[0], C_row_ptr,
-                                   &h->dstate->err, w + o_gws, gws_bytes, spans, c));
+                                   &h->dstate->err, w + L.gws, gws_bytes, spans, c));
         }
-        SG_TRY(launch_scan_counts(C_row_ptr, n, &h->dstate->nnz, w + o_tmp, c));
-        SG_TRY(launch_numeric_binning(n, C_row_ptr, flops, bins, h->dstate, c));
+        SG_TRY(launch_scan_counts(C_row_ptr, n, &h->dstate->nnz, w + L.tmp, c));
+        SG_TRY(launch_numeric_binning(n, C_row_ptr, flops, bins, h->dstate, c, h->narrow ? nlo : nullptr));
         SG_TRY(fetch_state(h, s));
         SG_TRY(device_errors(h->hstate->err));
         *nnz_C = h->hstate->nnz;
@@ -340,8 +362,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
                          : 0;
         h->num_lists = 0;
         // numeric scratch: B split into double-words, then the second-level maps
-        SG_TRY(ws_reserve(h, ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8) + h->num_gws, s,
-                          ws_persist(n, B->nrows)));
+        SG_TRY(ws_reserve(h, L.persist + align_up((size_t)B->nnz * 8) + h->num_gws, s, L.persist));
     }
     h->a_rp = A->row_ptr; h->a_col = A->col_idx; h->a_n = A->nrows; h->a_m = A->ncols;
     h->a_nnz = A->nnz;
@@ -371,14 +392,16 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     cudaStream_t s = (cudaStream_t)stream;
     SG_CUDA(cudaSetDevice(h->device));
     const int64_t n = A->nrows;
-    uint8_t *bins = (uint8_t *)h->ws;
-    int32_t *rows = (int32_t *)(h->ws + align_up((size_t)n));
-    const int4 *bdesc = (const int4 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4));
-    const int2 *bmm = (const int2 *)(h->ws + align_up((size_t)n) + align_up((size_t)n * 4) +
-                                     align_up((size_t)B->nrows * 16));
-    int2 *spans = (int2 *)(h->ws + ws_spans(n, B->nrows));
-    float2 *bsplit = (float2 *)(h->ws + ws_persist(n, B->nrows));
-    char *gws = h->ws + ws_persist(n, B->nrows) + align_up((size_t)B->nnz * 8);
+    const WsLayout L = ws_layout(n, B->nrows, B->nnz);
+    uint8_t *bins = (uint8_t *)(h->ws + L.bins);
+    int32_t *rows = (int32_t *)(h->ws + L.rows);
+    const int4 *bdesc = (const int4 *)(h->ws + L.desc);
+    const int2 *bmm = (const int2 *)(h->ws + L.mm);
+    int2 *spans = (int2 *)(h->ws + L.spans);
+    const int32_t *nlo = (const int32_t *)(h->ws + L.nlo);
+    const int2 *pairs = (const int2 *)(h->ws + L.pairs);
+    float2 *bsplit = (float2 *)(h->ws + L.persist);
+    char *gws = h->ws + L.persist + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
     h->have_last = true;
     h->last_dtype = dtype;
@@ -399,6 +422,11 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
         for (int b = first_list; b <= 4; b++) spanned += h->num_counts[b];
         SG_TRY(launch_list_spans(*A, bmm, rows, spanned, spans, c));
         h->num_lists = first_list;
+    }
+    if (h->num_counts[BIN_NARROW] > 0) {
+        const double mean_alen = (double)A->nnz / (double)n;
+        const int gn = h->g_narrow_num ? h->g_narrow_num : (mean_alen >= 64.0 ? 8 : 4);
+        SG_TRY(launch_num_narrow(dtype, *A, *B, *C, bdesc, pairs, nlo, bins, &h->dstate->err, gn, c));
     }
     return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, spans, rows, h->num_counts,
                           h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, tune, h->b_sorted,
@@ -786,6 +814,21 @@ int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
         case SPGEMM_OPT_SLOT_FACTOR:
             if (value != 2 && value != 4) { set_error("slot factor must be 2 or 4"); return SPGEMM_ERR_ARG; }
             h->slot_factor = (int)value;
+            return SPGEMM_OK;
+        case SPGEMM_OPT_NARROW: h->narrow = value != 0; return SPGEMM_OK;
+        case SPGEMM_OPT_LANES_NARROW_SYMBOLIC:
+            if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32) {
+                set_error("narrow symbolic lanes per row must be 0 (automatic), 4, 8, 16 or 32");
+                return SPGEMM_ERR_ARG;
+            }
+            h->g_narrow_sym = (int)value;
+            return SPGEMM_OK;
+        case SPGEMM_OPT_LANES_NARROW_NUMERIC:
+            if (value != 0 && value != 4 && value != 8 && value != 16) {
+                set_error("narrow numeric lanes per row must be 0 (automatic), 4, 8 or 16");
+                return SPGEMM_ERR_ARG;
+            }
+            h->g_narrow_num = (int)value;
             return SPGEMM_OK;
         default: set_error("unknown option %d", option); return SPGEMM_ERR_ARG;
     }

@@ -89,6 +89,34 @@ __host__ __device__ inline int sym_bin(long long keys, long long cpairs) {
     return b;
 }
 
+// Narrow rows (narrow.cu): rows of C whose columns all fall within
+// NARROW_W consecutive blocks of 32 columns.  The symbolic phase marks them
+// BIN_NARROW (their count done by the window table, nlo[i] = the window's
+// first block); the numeric phase gives BIN_NARROW to those of them with at
+// most NARROW_NMAX outputs and NARROW_FLOPS products.  Bin 7 is otherwise
+// unused in both phases.
+constexpr int BIN_NARROW = 7;
+constexpr int NARROW_W = 128;
+constexpr int NARROW_NMAX = 32;
+constexpr long long NARROW_FLOPS = 8192;
+constexpr long long NARROW_PAIRS = 4096;
+// Row-slot strides of the narrow kernels' shared tables, padded so that the
+// row slots of a warp start on different banks (words, bytes, values).
+constexpr int NARROW_TAB_STRIDE = NARROW_W + 4;
+constexpr int NARROW_BASE_STRIDE = NARROW_W + 4;
+constexpr int NARROW_ACC_STRIDE = NARROW_NMAX + 1;
+
+// Adds this warp's per-bin row counts (bins held by the lanes where `has`)
+// to a shared histogram with one ballot per bin.
+__device__ __forceinline__ void warp_hist(unsigned long long *hist, bool has, int bin) {
+    const unsigned have = __ballot_sync(0xffffffffu, has);
+    if (!have) return;
+    for (int b = 0; b < NBINS; b++) {
+        unsigned m = __ballot_sync(0xffffffffu, has && bin == b);
+        if (m && (threadIdx.x & 31) == 0) atomicAdd(&hist[b], (unsigned long long)__popc(m));
+    }
+}
+
 // Multiplicative hash (Fibonacci) of a non-negative key into [0, 2^log2S).
 __device__ __forceinline__ unsigned hash_slot(int key, int log2S) {
     return ((unsigned)key * 0x9E3779B1u) >> (32 - log2S);
@@ -160,9 +188,11 @@ int launch_scan_counts(int64_t *x, int64_t n, long long *total, void *tmp, Ctx &
 // Per row i of A: flops, symbolic bin; empty rows get crp[i+1] = 0.
 int launch_analyze(const spgemm_csr &A, const spgemm_csr &B, const int2 *ana, int64_t *flops,
                    uint8_t *bins, int64_t *crp, DevState *st, Ctx &c);
-// Numeric bin of every row from its output count crp[i+1]-crp[i] and flops.
+// Numeric bin of every row from its output count crp[i+1]-crp[i] and flops;
+// rows the symbolic phase found narrow (nlo[i] >= 0; nlo may be null) that
+// fit the narrow numeric kernel get BIN_NARROW.
 int launch_numeric_binning(int64_t n, const int64_t *crp, const int64_t *flops, uint8_t *bins,
-                           DevState *st, Ctx &c);
+                           DevState *st, Ctx &c, const int32_t *nlo = nullptr);
 // Row lists per bin: rows[offset(b) + t]; offsets from st->bin_count[phase]
 // (phase 0: symbolic second pass, phase 1: numeric bins 3..6).
 int launch_scatter_bins(int64_t n, const uint8_t *bins, const int64_t *crp, int32_t *rows,
@@ -175,8 +205,22 @@ int launch_row_flops(const spgemm_csr &A, const spgemm_csr &B, int64_t *flops, i
 int launch_list_spans(const spgemm_csr &A, const int2 *bmm, const int32_t *rows, int64_t count, int2 *spans,
                       Ctx &c);
 
+// narrow.cu
+// Analysis of every row of A (flops, symbolic bin, as launch_analyze) with
+// the count of every narrow row done in the same pass (bins[i] =
+// BIN_NARROW, nlo[i] = first block of its window; nlo[i] = -1 otherwise).
+// bmm[k] = {first block, last block} of B_k; G lanes per row (4..32).
+int launch_sym_narrow(const spgemm_csr &A, const spgemm_csr &B, const int4 *desc, const int2 *bmm,
+                      const int2 *pairs, int64_t *flops, uint8_t *bins, int64_t *crp, int32_t *nlo,
+                      DevState *st, int G, Ctx &c);
+// Numeric phase of the rows with bins[i] == BIN_NARROW (F32 or native F64),
+// G lanes per row (4, 8 or 16).
+int launch_num_narrow(int dtype, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C, const int4 *bdesc,
+                      const int2 *pairs, const int32_t *nlo, const uint8_t *bins, int *err, int G, Ctx &c);
+
 // symbolic.cu
-// First pass over all rows with a 32-slot map and G lanes per row.
+// First pass over all rows with a 32-slot map and G lanes per row (rows of
+// bins EMPTY, HUGE and NARROW are skipped).
 int launch_symbolic_first(const spgemm_csr &A, const uint8_t *bins, const int4 *desc,
                           const int2 *pairs, int64_t *crp, DevState *st, int G, Ctx &c);
 // Second pass: kernels of bins 2..6; counts[b] = rows in bin b (host),

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_sym_first(
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
         const int64_t i = base + g;
         const int b = i < n ? bins[i] : 0;
-        const bool active = b != BIN_EMPTY && b != BIN_HUGE;
+        const bool active = b != BIN_EMPTY && b != BIN_HUGE && b != BIN_NARROW;
         const int64_t p0 = active ? arp[i] : 0;
         const int plen = active ? (int)(arp[i + 1] - p0) : 0;
 #pragma unroll
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_sym_first_strided(
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
         const int64_t i = base + g;
         const int b = i < n ? bins[i] : 0;
-        const bool active = b != BIN_EMPTY && b != BIN_HUGE;
+        const bool active = b != BIN_EMPTY && b != BIN_HUGE && b != BIN_NARROW;
         const int64_t p0 = active ? arp[i] : 0;
         const int plen = active ? (int)(arp[i + 1] - p0) : 0;
 #pragma unroll
