@@ -250,12 +250,13 @@ static int lanes_for(double x, int lo = 8) {
 }
 
 // Workspace offsets.  [bins | rows | B descriptors | B block ranges | spans
-// of the listed rows | first window block of every row | B's compressed
-// pairs] persist from symbolic to numeric; after them the symbolic scratch,
-// or (later) the numeric scratch, which may overlap it.
+// of the listed rows | first window block of every row | window words of
+// the narrow rows (count, list)] persist from symbolic to numeric; after
+// them the symbolic scratch, or (later) the numeric scratch, which may
+// overlap it.
 struct WsLayout {
-    size_t bins, rows, desc, mm, spans, nlo, pairs, persist;   // persistent
-    size_t ana, flops, ccnt, tmp, gws;                          // symbolic scratch
+    size_t bins, rows, desc, mm, spans, nlo, nwords, ulist, persist;   // persistent
+    size_t ana, flops, pairs, ccnt, tmp, gws;                          // symbolic scratch
 };
 static WsLayout ws_layout(int64_t n, int64_t nb, int64_t nnzb) {
     WsLayout L;
@@ -265,10 +266,12 @@ static WsLayout ws_layout(int64_t n, int64_t nb, int64_t nnzb) {
     L.mm = L.desc + align_up((size_t)nb * 16);
     L.spans = L.mm + align_up((size_t)nb * 8);
     L.nlo = L.spans + align_up((size_t)n * 8);
-    L.pairs = L.nlo + align_up((size_t)n * 4);
-    L.persist = L.pairs + align_up((size_t)nnzb * 8);
+    L.nwords = L.nlo + align_up((size_t)n * 4);
+    L.ulist = L.nwords + align_up((size_t)n);
+    L.persist = L.ulist + align_up((size_t)n * NARROW_NMAX * 8);
     L.ana = L.persist;
-    L.flops = L.ana + align_up((size_t)nb * 8);
+    L.pairs = L.ana + align_up((size_t)nb * 8);
+    L.flops = L.pairs + align_up((size_t)nnzb * 8);
     L.ccnt = L.flops + align_up((size_t)n * 8);
     L.tmp = L.ccnt + align_up((size_t)nb * 4);
     L.gws = L.tmp + align_up(scan_tmp_bytes(n));
@@ -309,6 +312,8 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         int4 *desc = (int4 *)(w + L.desc);
         int2 *ana = (int2 *)(w + L.ana);
         int32_t *nlo = (int32_t *)(w + L.nlo);
+        uint8_t *nwords = (uint8_t *)(w + L.nwords);
+        uint2 *ulist = (uint2 *)(w + L.ulist);
         Ctx c = h->ctx(s);
         // lanes per row from the mean number of compressed pairs a row visits
         const double mean_alen = (double)A->nnz / (double)n;
@@ -320,8 +325,10 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         if (h->narrow) {
             // analysis and the narrow rows' counts in one pass; the first
             // pass below takes the other rows
-            const int gn = h->g_narrow_sym ? h->g_narrow_sym : lanes_for(mean_alen / 4.0, 4);
-            SG_TRY(launch_sym_narrow(*A, *B, desc, minmax, pairs, flops, bins, C_row_ptr, nlo, h->dstate, gn, c));
+            // lanes per row: rows of A longer than 32 entries take 8
+            const int gn = h->g_narrow_sym ? h->g_narrow_sym : (mean_alen <= 32.0 ? 4 : 8);
+            SG_TRY(launch_sym_narrow(*A, *B, desc, minmax, pairs, flops, bins, C_row_ptr, nlo, nwords, ulist,
+                                     h->dstate, gn, c));
         } else {
             SG_TRY(launch_analyze(*A, *B, ana, flops, bins, C_row_ptr, h->dstate, c));
         }
@@ -399,7 +406,8 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     const int2 *bmm = (const int2 *)(h->ws + L.mm);
     int2 *spans = (int2 *)(h->ws + L.spans);
     const int32_t *nlo = (const int32_t *)(h->ws + L.nlo);
-    const int2 *pairs = (const int2 *)(h->ws + L.pairs);
+    const uint8_t *nwords = (const uint8_t *)(h->ws + L.nwords);
+    const uint2 *ulist = (const uint2 *)(h->ws + L.ulist);
     float2 *bsplit = (float2 *)(h->ws + L.persist);
     char *gws = h->ws + L.persist + align_up((size_t)B->nnz * 8);
     Ctx c = h->ctx(s);
@@ -424,9 +432,11 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
         h->num_lists = first_list;
     }
     if (h->num_counts[BIN_NARROW] > 0) {
-        const double mean_alen = (double)A->nnz / (double)n;
-        const int gn = h->g_narrow_num ? h->g_narrow_num : (mean_alen >= 64.0 ? 8 : 4);
-        SG_TRY(launch_num_narrow(dtype, *A, *B, *C, bdesc, pairs, nlo, bins, &h->dstate->err, gn, c));
+        // lanes per row: a chunk of G consecutive entries of a row of B per
+        // step, so G follows the mean length of the rows of B
+        const double mean_blen = (double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1);
+        const int gn = h->g_narrow_num ? h->g_narrow_num : (mean_blen <= 8.0 ? 4 : 8);
+        SG_TRY(launch_num_narrow(dtype, *A, *B, *C, bdesc, nlo, nwords, ulist, bins, &h->dstate->err, gn, c));
     }
     return launch_numeric(dtype, h->f64_native, *A, *B, *C, bins, bdesc, spans, rows, h->num_counts,
                           h->dstate, bsplit, gws, h->num_gws, h->max_row_nnz, tune, h->b_sorted,

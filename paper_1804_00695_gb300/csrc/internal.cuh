@@ -210,13 +210,17 @@ int launch_list_spans(const spgemm_csr &A, const int2 *bmm, const int32_t *rows,
 // the count of every narrow row done in the same pass (bins[i] =
 // BIN_NARROW, nlo[i] = first block of its window; nlo[i] = -1 otherwise).
 // bmm[k] = {first block, last block} of B_k; G lanes per row (4..32).
+// A narrow row also leaves its non-empty window words, in order, at
+// ulist[i*NARROW_NMAX ...] (first NARROW_NMAX of them; {word | rank of its
+// first column << 8, mask}) and their number in nwords[i].
 int launch_sym_narrow(const spgemm_csr &A, const spgemm_csr &B, const int4 *desc, const int2 *bmm,
                       const int2 *pairs, int64_t *flops, uint8_t *bins, int64_t *crp, int32_t *nlo,
-                      DevState *st, int G, Ctx &c);
+                      uint8_t *nwords, uint2 *ulist, DevState *st, int G, Ctx &c);
 // Numeric phase of the rows with bins[i] == BIN_NARROW (F32 or native F64),
-// G lanes per row (4, 8 or 16).
+// from the word lists of the symbolic phase; G lanes per row (4, 8 or 16).
 int launch_num_narrow(int dtype, const spgemm_csr &A, const spgemm_csr &B, spgemm_csr &C, const int4 *bdesc,
-                      const int2 *pairs, const int32_t *nlo, const uint8_t *bins, int *err, int G, Ctx &c);
+                      const int32_t *nlo, const uint8_t *nwords, const uint2 *ulist, const uint8_t *bins, int *err,
+                      int G, Ctx &c);
 
 // symbolic.cu
 // First pass over all rows with a 32-slot map and G lanes per row (rows of
