@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--batch-max", type=int, default=65536, help="largest instance order of the batched workload")
     ap.add_argument("--workload", default="galerkin128",
                     choices=["galerkin128", "rmat20", "chunked256", "batched256"])
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default line without the R-MAT, chunked and batched workloads")
     return ap.parse_args()
 
 
@@ -70,28 +72,38 @@ def bins_of(keys, flops):
 NARROW_W, NARROW_NMAX, NARROW_FLOPS, NARROW_PAIRS = 128, 32, 8192, 4096
 
 
+def _seg_reduce(ufunc, vals, rp, empty):
+    """ufunc.reduceat over the rows of a CSR (empty rows get `empty`)."""
+    n = len(rp) - 1
+    out = np.full(n, empty, dtype=np.int64)
+    lens = np.diff(rp)
+    nz = np.nonzero(lens > 0)[0]
+    if len(nz):
+        out[nz] = ufunc.reduceat(vals, rp[nz])
+    return out
+
+
 def narrow_numeric_rows(a, b, c_rp, flops):
     """Rows the narrow numeric kernel takes (the library's rule): columns of
     the rows of B they reach within NARROW_W blocks of 32, at most
     NARROW_PAIRS compressed pairs, at most NARROW_NMAX outputs and
     NARROW_FLOPS products."""
-    blk = b.col.astype(np.int64) >> 5
-    brow = np.repeat(np.arange(b.nrows), np.diff(b.row_ptr))
     big = np.iinfo(np.int64).max
-    bmin = np.full(b.nrows, big, dtype=np.int64)
-    bmax = np.full(b.nrows, -1, dtype=np.int64)
-    np.minimum.at(bmin, brow, blk)
-    np.maximum.at(bmax, brow, blk)
-    pk = np.unique(brow * (1 << 26) + blk)
-    bpairs = np.bincount(pk // (1 << 26), minlength=b.nrows)
+    blk = b.col.astype(np.int64) >> 5
+    brp = np.asarray(b.row_ptr, dtype=np.int64)
+    bmin = _seg_reduce(np.minimum, blk, brp, big)
+    bmax = _seg_reduce(np.maximum, blk, brp, -1)
+    # pairs of a row: runs of consecutive entries in one block
+    starts = np.ones(len(blk), dtype=np.int64)
+    if len(blk):
+        starts[1:] = blk[1:] != blk[:-1]
+        starts[brp[:-1][np.diff(brp) > 0]] = 1
+    bpairs = _seg_reduce(np.add, starts, brp, 0)
     k = a.col.astype(np.int64)
-    arow = np.repeat(np.arange(a.nrows), np.diff(a.row_ptr))
-    lo = np.full(a.nrows, big, dtype=np.int64)
-    hi = np.full(a.nrows, -1, dtype=np.int64)
-    np.minimum.at(lo, arow, bmin[k])
-    np.maximum.at(hi, arow, bmax[k])
-    cp = np.zeros(a.nrows, dtype=np.int64)
-    np.add.at(cp, arow, bpairs[k])
+    arp = np.asarray(a.row_ptr, dtype=np.int64)
+    lo = _seg_reduce(np.minimum, bmin[k], arp, big)
+    hi = _seg_reduce(np.maximum, bmax[k], arp, -1)
+    cp = _seg_reduce(np.add, bpairs[k], arp, 0)
     nn = np.diff(c_rp)
     return ((hi >= lo) & (hi - lo < NARROW_W) & (cp <= NARROW_PAIRS) & (nn > 0) & (nn <= NARROW_NMAX)
             & (flops <= NARROW_FLOPS))
@@ -241,6 +253,15 @@ def main():
         import bench_workloads
         return bench_workloads.run(args, rank, world, local)
 
+    # inputs of the secondary workloads (one GPU only), generated in worker
+    # processes before any CUDA call and before anything is timed
+    gen = None
+    if world == 1 and not args.no_secondary:
+        import bench_workloads
+        gen = bench_workloads.Inputs(args)
+        gen.rmat_graph()
+        gen.batch_pairs()
+
     import torch
     import paper_1804_00695_gb300 as sg
     from paper_1804_00695_gb300 import inputs as I
@@ -369,42 +390,18 @@ def main():
                   kernel_bytes(r, ap_rp, rap_rp, np.ones(r.nrows, dtype=bool), 8))
     step_frac = step_bytes / (ms / 1e3) / 1e9 / hbm
 
-    # end to end: host (pinned) inputs -> device, both products, result -> host
-    hosts = {}
-    for nm, m in (("a", a), ("p", p), ("r", r)):
-        hosts[nm] = [torch.from_numpy(x).pin_memory() for x in (m.row_ptr, m.col, m.val)]
-    devs = {nm: [torch.empty_like(x, device=dev) for x in hosts[nm]] for nm in hosts}
-    h2d = sum(x.numel() * x.element_size() for v in hosts.values() for x in v)
-
-    side = torch.cuda.Stream(device=dev)
-    r_in = torch.cuda.Event()
+    # end to end through the library's host-operand call (spgemm_host): A, P
+    # and R in pinned host memory are copied in by the library, A*P stays on
+    # the device, R*(AP) comes back to pinned host memory
+    Ah, Ph, Rh = (sg.HostCsr.from_numpy(m) for m in (a, p, r))
+    h2d = sum(x.numel() * x.element_size() for m in (Ah, Ph, Rh) for x in (m.row_ptr, m.col, m.val))
 
     def e2e_step():
-        # A and P come in on the compute stream; R, needed only by the second
-        # product, comes in on a side stream while A*P runs
-        for nm in ("a", "p"):
-            for hx, dx in zip(hosts[nm], devs[nm]):
-                dx.copy_(hx, non_blocking=True)
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            for hx, dx in zip(hosts["r"], devs["r"]):
-                dx.copy_(hx, non_blocking=True)
-            r_in.record(side)
-        Ad = sg.Csr(a.nrows, a.ncols, *devs["a"])
-        Pd = sg.Csr(p.nrows, p.ncols, *devs["p"])
-        Rd = sg.Csr(r.nrows, r.ncols, *devs["r"])
-        rp1, n1 = h1.symbolic(Ad, Pd)
-        APd = h1.numeric(Ad, Pd, rp1, n1)
-        stream.wait_event(r_in)
-        rp2, n2 = h2.symbolic(Rd, APd)
-        RAPd = h2.numeric(Rd, APd, rp2, n2)
-        out = [RAPd.row_ptr.to("cpu", non_blocking=True), RAPd.col.to("cpu", non_blocking=True),
-               RAPd.val.to("cpu", non_blocking=True)]
-        return out
+        APd = h1.host_product(Ah, Ph, keep_on_device=True)
+        return h2.host_product(Rh, APd)
 
     o = e2e_step()
-    torch.cuda.synchronize()
-    d2h = sum(x.numel() * x.element_size() for x in o)
+    d2h = sum(x.numel() * x.element_size() for x in (o.row_ptr, o.col, o.val))
     ke = max(1, min(args.steps, 5))
     barrier()
     e0.record(stream)
@@ -416,6 +413,25 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     a_bytes = 8 * (a.nrows + 1) + 12 * a.nnz
+    secondary = None
+    if gen is not None:
+        # the other BASELINE workloads, measured on this GPU after the default one
+        del A, P, R, AP, RAP, h1, h2, Ah, Ph, Rh, o
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        secondary = {}
+        for name, fn in (("rmat20", lambda: bench_workloads.measure_rmat(args, gen.rmat_graph(), local)),
+                         ("chunked256", lambda: bench_workloads.measure_chunked(args, local)),
+                         ("batched256", lambda: bench_workloads.measure_batched(args, gen.batch_pairs(), local))):
+            t0 = time.perf_counter()
+            try:
+                secondary[name] = fn()
+            except Exception as exc:   # one workload failing does not lose the others
+                secondary[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            secondary[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        gen.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -433,8 +449,11 @@ def main():
                 "gpu_launches": launches,
                 "clocks": clk,
                 "e2e": {"value": world * 2 * mults / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                        "entry_point": "spgemm_host (A, P host -> AP device; R host * AP -> RAP host)"},
                 "cpu_baseline": cpu}
+        if secondary is not None:
+            line["secondary"] = secondary
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

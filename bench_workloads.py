@@ -1,6 +1,7 @@
-"""Benchmark workloads besides the default Galerkin product (run with
-``python bench.py --workload rmat20|chunked256|batched256``); each prints one
-JSON line in the same format as bench.py.
+"""Benchmark workloads besides the default Galerkin product; each measure_*
+function returns a dict that bench.py puts under "secondary" in its default
+line, and ``python bench.py --workload rmat20|chunked256|batched256`` prints
+one of them as a full line.
 
 * rmat20     - C = A*A, A symmetrised R-MAT scale 20, edge factor 16, FP32.
 * chunked256 - C = A*A, A the 27-point Laplacian on 256^3, FP64, operands and
@@ -8,10 +9,19 @@ JSON line in the same format as bench.py.
 * batched256 - 256 products A_i*B_i, rows log-uniform in [1024, 65536], 4-32
                random columns per row, FP32: batched forward and backward
                against a per-instance loop on the same GPU.
+
+Every entry carries a CPU baseline: the oracle timed on a bounded sample of
+the same workload (rows of C, or instances), on all host cores; the same
+oracle output is compared with the device result for that sample (pattern
+exact, values within the stated tolerance), reported as "parity".
+The large inputs are generated in a process pool (spawn) that bench.py starts
+before its first CUDA call.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import json
+import multiprocessing as mp
 import os
 import statistics
 import sys
@@ -24,48 +34,129 @@ sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402  (shared helpers: clocks, peaks, bytes)
 
-
-def _line(args, world, metric_value, ms, dtype, config, extra):
-    line = {"metric": bench.METRIC, "value": metric_value, "unit": "GFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-            "data": "synthetic (seeded generators)", "config": config}
-    line.update(extra)
-    print(json.dumps(line), flush=True)
+TOL = {"f64": 1e-12, "f32": 1e-5}
+CPU_SAMPLE_S = 4.0   # target seconds of oracle work per CPU-baseline sample
 
 
+# ---------------------------------------------------------------- inputs
+def _gen_rmat(scale):
+    from paper_1804_00695_gb300 import inputs as I
+    return I.rmat_symmetric(scale, 16, seed=1)
+
+
+def _gen_pair(n, s):
+    from paper_1804_00695_gb300 import inputs as I
+    return I.random_square(n, 2 * s, dtype=np.float32), I.random_square(n, 2 * s + 1, dtype=np.float32)
+
+
+class Inputs:
+    """The secondary workloads' inputs, generated in worker processes (spawn)
+    while the caller measures: the R-MAT graph and the batch instances
+    (instance i: n_i from the log-uniform sizes, seeds 2(1+i), 2(1+i)+1, as
+    inputs.random_batch)."""
+
+    def __init__(self, args, workers=None):
+        from paper_1804_00695_gb300 import inputs as I
+        workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
+        self.pool = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+        self.rmat = self.pool.submit(_gen_rmat, args.rmat_scale)
+        sizes = I.batch_sizes(args.batch_count, 1024, args.batch_max, 1)
+        self.batch = [self.pool.submit(_gen_pair, n, 1 + i) for i, n in enumerate(sizes)]
+
+    def rmat_graph(self):
+        return self.rmat.result()
+
+    def batch_pairs(self):
+        return [f.result() for f in self.batch]
+
+    def close(self):
+        self.pool.shutdown(wait=False, cancel_futures=True)
+
+
+# ---------------------------------------------------------------- helpers
 def _mults(a, b_rp):
     return int(np.diff(b_rp)[a.col.astype(np.int64)].sum())
 
 
-def run(args, rank, world, local):
-    """The secondary workloads are measured on one GPU: under a multi-rank
-    launch rank 0 runs and reports them, the other ranks exit at once."""
-    import torch
-    if world > 1 and rank != 0:
-        return
-    world = 1
-    torch.cuda.set_device(local)
-    if args.workload == "rmat20":
-        return rmat20(args, world, local)
-    if args.workload == "chunked256":
-        return chunked256(args, world, local)
-    return batched256(args, world, local)
+def _row_flops(a, b):
+    """Multiplications per row of A*B (sum over stored a_ik of nnz(B_k))."""
+    rows = np.repeat(np.arange(a.nrows), np.diff(a.row_ptr))
+    per = np.diff(b.row_ptr)[a.col.astype(np.int64)].astype(np.float64)
+    return np.rint(np.bincount(rows, weights=per, minlength=a.nrows)).astype(np.int64)
 
 
-def rmat20(args, world, local):
+def _hbm_peak():
+    peaks = bench.measured_peaks()
+    return (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
+
+
+def _compare_rows(got_rp, got_col, got_val, ref, tol):
+    """Device rows (host copies) against an oracle Result of the same rows:
+    pattern exact, values within tol * sum|a||b| (exact where that is 0)."""
+    got_rp = got_rp - got_rp[0]
+    ok_pat = np.array_equal(got_rp, ref.row_ptr) and np.array_equal(got_col, ref.col)
+    err = np.abs(got_val.astype(np.float64) - ref.val) if ok_pat else None
+    ok_val = bool(ok_pat and np.all(err <= tol * ref.bound))
+    worst = float(np.max(err / np.maximum(ref.bound, 1e-300))) if ok_pat and len(err) else 0.0
+    return {"pattern_exact": bool(ok_pat), "values_in_tolerance": ok_val, "max_err_over_bound": worst}
+
+
+def _row_block(fl, target_mults, start):
+    """Rows [start, end) whose products add up to about target_mults."""
+    cum = np.cumsum(fl[start:])
+    end = start + int(np.searchsorted(cum, target_mults)) + 1
+    return start, min(end, len(fl))
+
+
+def _oracle_rows_sample(a, b, fl, start, tol_tag, device_rows, label):
+    """CPU baseline leg: the oracle on a block of rows of about CPU_SAMPLE_S
+    seconds (grown from a small probe), timed on all host cores; its output
+    is compared with the device rows (device_rows(r0, r1) -> rp, col, val)."""
+    import oracle
+    r0, r1 = _row_block(fl, 2e8, start)
+    t0 = time.perf_counter()
+    oracle.spgemm(a, b, r0, r1)
+    probe = max(time.perf_counter() - t0, 1e-3)
+    rate = max(int(fl[r0:r1].sum()), 1) / probe
+    r0, r1 = _row_block(fl, rate * CPU_SAMPLE_S, start)
+    t0 = time.perf_counter()
+    ref = oracle.spgemm(a, b, r0, r1)
+    dt = time.perf_counter() - t0
+    m = int(fl[r0:r1].sum())
+    par = _compare_rows(*device_rows(r0, r1), ref, TOL[tol_tag])
+    par["rows"] = [int(r0), int(r1)]
+    return ({"value": 2 * m / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+             "sample": f"{label}: rows [{r0}, {r1}) of C ({m} multiplications), {dt:.2f} s"}, par)
+
+
+# ---------------------------------------------------------------- R-MAT
+def measure_rmat(args, g, local):
+    """C = A*A on the R-MAT graph: GFLOP/s, % of the HBM-byte roofline, the
+    dominant kernel's roofline, a CPU baseline on a block of rows and the
+    parity of that block."""
     import torch
     import paper_1804_00695_gb300 as sg
-    from paper_1804_00695_gb300 import inputs as I
-    g = I.rmat_symmetric(args.rmat_scale, 16, seed=1)
     A = sg.Csr.from_host(g, "cuda", np.float32)
     h = sg.Handle(local)
     mults = _mults(g, g.row_ptr)
+    fl = _row_flops(g, g)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        c = h.spgemm(A, A)
-        del c
+    steps, warm = 2, 2
+    c = h.spgemm(A, A)
     h.check()
+    crp = c.row_ptr.cpu().numpy()
+    nnz = c.nnz
+
+    def rows(r0, r1):
+        p0, p1 = int(crp[r0]), int(crp[r1])
+        return crp[r0:r1 + 1].copy(), c.col[p0:p1].cpu().numpy(), c.val[p0:p1].cpu().numpy()
+
+    # sample rows where the degrees are mixed (away from the hub at row 0)
+    cpu, par = _oracle_rows_sample(g, g, fl, g.nrows // 3, "f32", rows, "R-MAT scale %d" % args.rmat_scale)
+    del c
+    for _ in range(warm - 1):
+        del_c = h.spgemm(A, A)
+        del del_c
     h.set_timing(True)
     h.reset_timings()
     clocks = bench.ClockSampler(local)
@@ -73,33 +164,53 @@ def rmat20(args, world, local):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         c = h.spgemm(A, A)
         del c
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     tim = h.timings()
-    c = h.spgemm(A, A)
-    nnz = c.nnz
-    crp = c.row_ptr.cpu().numpy()
-    del c
-    peaks = bench.measured_peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    h.set_timing(False)
+    hbm, src = _hbm_peak()
     step_bytes = bench.kernel_bytes(g, g.row_ptr, crp, np.ones(g.nrows, dtype=bool), 4)
-    dom = max(tim.items(), key=lambda kv: kv[1][2])
-    _line(args, world, 2 * mults / (ms / 1e3) / 1e9, ms, "f32",
-          {"workload": f"C = A*A, A symmetrised R-MAT scale {args.rmat_scale}, edge factor 16, "
-                       "(a,b,c,d) = (.57,.19,.19,.05), seed 1, FP32", "mults": mults, "nnz_C": nnz},
-          {"pct_hbm_byte_roofline": 100 * step_bytes / (ms / 1e3) / 1e9 / hbm,
-           "step_algorithmic_bytes": step_bytes,
-           "dominant_kernel": {"label": dom[0], "ms_per_step": dom[1][2] / args.steps},
-           "kernels_ms_per_step": {k: v[2] / args.steps for k, v in sorted(tim.items())},
-           "gpu_launches": sum(v[0] for v in tim.values()) // max(args.steps, 1) * args.steps,
-           "clocks": clk})
+    nar = bench.narrow_numeric_rows(g, g, crp, fl)
+    bb = np.where(nar, 7, bench.bins_of(np.diff(crp), fl))
+    kern = []
+    for key, (nl, nrows, tms) in tim.items():
+        parts = key.split(".")
+        if parts[0] != "numeric":
+            continue
+        lab = parts[1]
+        if lab == "narrow":
+            mask = nar
+        elif lab == "small":
+            mask = (bb == 1) | (bb == 2)
+        elif lab.startswith("bin"):
+            mask = bb == int(lab[3:4])
+        else:
+            continue
+        kern.append((tms / nl, key, bench.kernel_bytes(g, g.row_ptr, crp, mask, 4, True), nl))
+    roof = None
+    if kern:
+        per_ms, key, byt, nl = max(kern, key=lambda x: x[0] * x[3])
+        ach = byt / (per_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": key, "bytes_per_launch": byt, "ms_per_launch": per_ms,
+                "peak_source": src}
+    return {"metric_value": 2 * mults / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "steps": steps,
+            "warmup": warm, "dtype": "f32",
+            "config": {"workload": f"C = A*A, A symmetrised R-MAT scale {args.rmat_scale}, edge factor 16, "
+                                   "(a,b,c,d) = (.57,.19,.19,.05), seed 1, FP32", "mults": mults, "nnz_C": nnz},
+            "pct_hbm_byte_roofline": 100 * step_bytes / (ms / 1e3) / 1e9 / hbm,
+            "step_algorithmic_bytes": step_bytes, "roofline": roof,
+            "kernels_ms_per_step": {k: v[2] / steps for k, v in sorted(tim.items())},
+            "gpu_launches": sum(v[0] for v in tim.values()), "clocks": clk, "cpu_baseline": cpu,
+            "parity": par}
 
 
+# ---------------------------------------------------------------- chunked
 def _link_bandwidth():
     import torch
     n = 1 << 30
@@ -134,24 +245,29 @@ def _link_bandwidth():
     return out
 
 
-def chunked256(args, world, local):
+def measure_chunked(args, local, a=None):
+    """Chunked C = A*A with operands and C in pinned host memory and a device
+    budget: algorithmic GFLOP/s including every copy (symbolic + numeric),
+    the fraction of the measured host link, bytes copied against the minimal
+    bytes, the plan, a CPU baseline on a block of rows and its parity."""
     import torch
     import paper_1804_00695_gb300 as sg
     from paper_1804_00695_gb300 import inputs as I
     n = args.chunk_grid
-    a = I.laplace3d_27pt(n)
+    if a is None:
+        a = I.laplace3d_27pt(n)
     A = sg.HostCsr.from_numpy(a)
     budget = int(args.budget)
     h = sg.Handle(local)
     mults = _mults(a, a.row_ptr)
     link = _link_bandwidth()
-    steps = max(1, min(args.steps, 3))
+    steps = 2
     rp, nnz = h.chunked_symbolic(A, A, budget)
     col = torch.empty(nnz, dtype=torch.int32).pin_memory()
     val = torch.empty(nnz, dtype=torch.float64).pin_memory()
     Cm = sg.HostCsr(a.nrows, a.ncols, rp, col, val)
     clocks = bench.ClockSampler(local)
-    times, sym_times, stats = [], [], None
+    times, sym_times, stats, sym = [], [], None, None
     clocks.start()
     for it in range(steps + 1):
         torch.cuda.synchronize()
@@ -168,37 +284,62 @@ def chunked256(args, world, local):
             sym_times.append(t1 - t0)
     clk = clocks.stop()
     ms = 1e3 * statistics.median(times)
-    # per-kernel device time of one more (untimed) step
-    h.set_timing(True)
-    h.reset_timings()
-    h.chunked_symbolic(A, A, budget, out=Cm.row_ptr)
-    h.chunked_numeric_into(A, A, Cm, budget)
-    torch.cuda.synchronize()
-    kern = {k: round(v[2], 3) for k, v in h.timings().items()}
-    h.set_timing(False)
     size_a = 8 * (a.nrows + 1) + 12 * a.nnz
     size_c = 8 * (a.nrows + 1) + 12 * nnz
     minimal = 2 * size_a + size_c            # A and B in, C out, each once
     moved = stats["h2d_bytes"] + stats["d2h_bytes"] + sym["h2d_bytes"] + sym["d2h_bytes"]
     peak = max(link["bidir"], link["h2d"], link["d2h"])
-    _line(args, world, 2 * mults / (ms / 1e3) / 1e9, ms, "f64",
-          {"workload": f"chunked C = A*A, 27-point 3D Laplacian on {n}^3, FP64, operands and C in "
-                       f"pinned host memory, {budget:.3g}-byte device budget", "mults": mults, "nnz_C": nnz,
-           "budget_bytes": budget},
-          {"roofline": {"bound": "host-link", "achieved": minimal / (ms / 1e3) / 1e9, "peak": peak,
-                        "unit": "GB/s", "frac": minimal / (ms / 1e3) / 1e9 / peak,
-                        "traffic": moved, "note": "achieved = minimal bytes (A, B in and C out "
-                        "once) over time; traffic = bytes actually copied (symbolic + numeric)"},
-           "link_gbs_measured": link, "numeric_plan": stats, "symbolic_plan": sym,
-           "symbolic_ms": 1e3 * statistics.median(sym_times), "kernels_ms": kern,
-           "clocks": clk})
+    fl = _row_flops(a, a)
+    crp = Cm.row_ptr.numpy()
+
+    def rows(r0, r1):
+        p0, p1 = int(crp[r0]), int(crp[r1])
+        return crp[r0:r1 + 1].copy(), Cm.col[p0:p1].numpy(), Cm.val[p0:p1].numpy()
+
+    cpu, par = _oracle_rows_sample(a, a, fl, a.nrows // 2, "f64", rows, f"27-point {n}^3 A*A")
+    return {"metric_value": 2 * mults / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "steps": steps,
+            "warmup": 1, "dtype": "f64",
+            "config": {"workload": f"chunked C = A*A, 27-point 3D Laplacian on {n}^3, FP64, operands and C in "
+                                   f"pinned host memory, {budget:.3g}-byte device budget", "mults": mults,
+                       "nnz_C": nnz, "budget_bytes": budget},
+            "roofline": {"bound": "host-link", "achieved": minimal / (ms / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": minimal / (ms / 1e3) / 1e9 / peak, "traffic": moved,
+                         "note": "achieved = minimal bytes (A, B in and C out once) over the step time; "
+                                 "peak = the best of the pinned H2D, D2H and both-ways copies measured in "
+                                 "the same run; traffic = bytes actually copied (symbolic + numeric)"},
+            "bytes_copied_over_minimal": moved / minimal, "link_gbs_measured": link, "numeric_plan": stats,
+            "symbolic_plan": sym, "symbolic_ms": 1e3 * statistics.median(sym_times), "clocks": clk,
+            "cpu_baseline": cpu, "parity": par}
 
 
-def batched256(args, world, local):
+# ---------------------------------------------------------------- batched
+def _grad_check(a, b, c_rp, c_col, dc, da, db, tol):
+    """Oracle gradients of <dC, A*B> for one instance, and the device ones
+    against them (each entry within tol * the sum of the absolute terms it
+    adds)."""
+    import oracle
+    from paper_1804_00695_gb300 import inputs as I
+    a64 = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, a.val.astype(np.float64))
+    b64 = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, b.val.astype(np.float64))
+    dc64 = dc.astype(np.float64)
+    ra, rb = oracle.backward(a64, b64, c_rp, c_col, dc64)
+    ones_a = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.ones(a.nnz))
+    ones_b = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, np.ones(b.nnz))
+    abs_a = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, np.abs(a64.val))
+    abs_b = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, np.abs(b64.val))
+    ba, _ = oracle.backward(ones_a, abs_b, c_rp, c_col, np.abs(dc64))
+    _, bb = oracle.backward(abs_a, ones_b, c_rp, c_col, np.abs(dc64))
+    return bool(np.all(np.abs(da - ra) <= tol * ba) and np.all(np.abs(db - rb) <= tol * bb))
+
+
+def measure_batched(args, pairs, local):
+    """Batched forward and backward against a per-instance loop on the same
+    GPU (speedups), a CPU baseline on a sample of instances and the parity of
+    that sample (forward and backward)."""
     import torch
+    import oracle
     import paper_1804_00695_gb300 as sg
     from paper_1804_00695_gb300 import inputs as I
-    pairs = I.random_batch(args.batch_count, 1024, args.batch_max, 1, dtype=np.float32)
     As = [sg.Csr.from_host(a, "cuda") for a, _ in pairs]
     Bs = [sg.Csr.from_host(b, "cuda") for _, b in pairs]
     mults = sum(_mults(a, b.row_ptr) for a, b in pairs)
@@ -206,9 +347,10 @@ def batched256(args, world, local):
     hl = sg.Handle(local)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    steps, warm = 5, 2
 
     def timed(fn, reps):
-        for _ in range(max(1, args.warmup)):
+        for _ in range(warm):
             fn()
         torch.cuda.synchronize()
         e0, e1 = ev(), ev()
@@ -219,16 +361,17 @@ def batched256(args, world, local):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    clocks = bench.ClockSampler(local)
+    clocks.start()
     bt = sg.Batch(h, As, Bs)
-    fwd_batched = timed(lambda: bt.run(), args.steps)
+    fwd_batched = timed(lambda: bt.run(), steps)
     loop_out = []
 
     def loop_fwd():
         loop_out.clear()
         for A, B in zip(As, Bs):
             loop_out.append(hl.spgemm(A, B))
-    fwd_loop = timed(loop_fwd, max(1, args.steps // 2))
-    # numeric only, replayed from a CUDA graph vs a loop of numeric calls
+    fwd_loop = timed(loop_fwd, 2)
     bt.symbolic()
     Cm = bt.alloc()
     bt.numeric_into(Cm)
@@ -238,41 +381,87 @@ def batched256(args, world, local):
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
             bt.numeric_into(Cm)
-    num_graph = timed(lambda: g.replay(), args.steps)
+    num_graph = timed(lambda: g.replay(), steps)
     singles = []
     for A, B in zip(As, Bs):
         hh = sg.Handle(local)
         rp, nz = hh.symbolic(A, B)
         singles.append((hh, A, B, hh.numeric(A, B, rp, nz)))
-    num_loop = timed(lambda: [hh.numeric_into(A, B, c) for hh, A, B, c in singles], args.steps)
-    # backward: batched vs loop
+    num_loop = timed(lambda: [hh.numeric_into(A, B, c) for hh, A, B, c in singles], steps)
     dc = torch.cos(torch.arange(Cm.nnz, device="cuda", dtype=torch.float32))
-    bwd_batched = timed(lambda: bt.backward(Cm, dc), args.steps)
+    bwd_batched = timed(lambda: bt.backward(Cm, dc), steps)
     parts = bt.split(Cm)
     dcs = []
     p0 = 0
     for c in parts:
         dcs.append(dc[p0:p0 + c.nnz])
         p0 += c.nnz
-    bwd_loop = timed(lambda: [hh.backward(A, B, c, d) for (hh, A, B, c), d in zip(singles, dcs)],
-                     max(1, args.steps // 2))
-    # per-kernel breakdown of one batched forward and backward (untimed pass)
-    h.set_timing(True)
-    h.reset_timings()
-    bt.run()
-    bt.backward(Cm, dc)
-    torch.cuda.synchronize()
-    kern = {k: round(v[2], 4) for k, v in h.timings().items()}
-    h.set_timing(False)
+    bwd_loop = timed(lambda: [hh.backward(A, B, c, d) for (hh, A, B, c), d in zip(singles, dcs)], 2)
+    clk = clocks.stop()
+    # CPU baseline leg: the oracle forward on instances in order until about
+    # CPU_SAMPLE_S seconds; the same outputs (and the oracle backward of the
+    # first sampled instance) against the device results
+    da, db = bt.backward(Cm, dc)
+    ga, gb = bt.split_grads(da, db)
+    t_cpu, m_cpu, done, par_ok = 0.0, 0, [], True
+    k = len(pairs) // 2
+    while k < len(pairs) and t_cpu < CPU_SAMPLE_S:
+        a, b = pairs[k]
+        a64 = I.Csr(a.nrows, a.ncols, a.row_ptr, a.col, a.val.astype(np.float64))
+        b64 = I.Csr(b.nrows, b.ncols, b.row_ptr, b.col, b.val.astype(np.float64))
+        t0 = time.perf_counter()
+        ref = oracle.spgemm(a64, b64)
+        t_cpu += time.perf_counter() - t0
+        m_cpu += int(ref.mults.sum())
+        c = parts[k]
+        r = _compare_rows(c.row_ptr.cpu().numpy(), c.col.cpu().numpy(), c.val.cpu().numpy(), ref, TOL["f32"])
+        par_ok = par_ok and r["pattern_exact"] and r["values_in_tolerance"]
+        done.append(k)
+        k += 1
+    i0 = done[0]
+    c0 = parts[i0]
+    bwd_ok = _grad_check(pairs[i0][0], pairs[i0][1], c0.row_ptr.cpu().numpy(), c0.col.cpu().numpy(),
+                         dcs[i0].cpu().numpy(), ga[i0].double().cpu().numpy(), gb[i0].double().cpu().numpy(),
+                         TOL["f32"])
     gf = lambda ms: 2 * mults / (ms / 1e3) / 1e9
-    _line(args, world, gf(fwd_batched), fwd_batched, "f32",
-          {"workload": f"{args.batch_count} products A_i*B_i, n_i log-uniform in [1024, {args.batch_max}], "
-                       "4-32 random columns per row, N(0,1) FP32", "mults": mults, "nnz_C": int(Cm.nnz),
-           "rows": int(sum(a.nrows for a, _ in pairs))},
-          {"batched_forward_ms": fwd_batched, "loop_forward_ms": fwd_loop,
-           "forward_speedup": fwd_loop / fwd_batched,
-           "batched_numeric_graph_ms": num_graph, "loop_numeric_ms": num_loop,
-           "numeric_speedup": num_loop / num_graph,
-           "batched_backward_ms": bwd_batched, "loop_backward_ms": bwd_loop,
-           "backward_speedup": bwd_loop / bwd_batched,
-           "loop_forward_gflops": gf(fwd_loop), "kernels_ms": kern})
+    return {"metric_value": gf(fwd_batched), "unit": "GFLOP/s", "ms_per_step": fwd_batched, "steps": steps,
+            "warmup": warm, "dtype": "f32",
+            "config": {"workload": f"{args.batch_count} products A_i*B_i, n_i log-uniform in [1024, "
+                                   f"{args.batch_max}], 4-32 random columns per row, N(0,1) FP32",
+                       "mults": mults, "nnz_C": int(Cm.nnz), "rows": int(sum(a.nrows for a, _ in pairs))},
+            "batched_forward_ms": fwd_batched, "loop_forward_ms": fwd_loop,
+            "forward_speedup": fwd_loop / fwd_batched,
+            "batched_numeric_graph_ms": num_graph, "loop_numeric_ms": num_loop,
+            "numeric_speedup": num_loop / num_graph,
+            "batched_backward_ms": bwd_batched, "loop_backward_ms": bwd_loop,
+            "backward_speedup": bwd_loop / bwd_batched, "loop_forward_gflops": gf(fwd_loop), "clocks": clk,
+            "cpu_baseline": {"value": 2 * m_cpu / t_cpu / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"forward of instances {done[0]}..{done[-1]} ({m_cpu} multiplications), "
+                                       f"{t_cpu:.2f} s"},
+            "parity": {"instances": [done[0], done[-1]], "forward_pattern_exact_and_in_tolerance": bool(par_ok),
+                       "backward_instance": i0, "backward_in_tolerance": bwd_ok}}
+
+
+# ---------------------------------------------------------------- one workload as a full line
+def run(args, rank, world, local):
+    """`--workload X`: one secondary workload as a full JSON line (measured on
+    one GPU: under a multi-rank launch rank 0 runs it, the others exit)."""
+    import torch
+    if world > 1 and rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1804_00695_gb300 import inputs as I
+    if args.workload == "rmat20":
+        r = measure_rmat(args, I.rmat_symmetric(args.rmat_scale, 16, seed=1), local)
+    elif args.workload == "chunked256":
+        r = measure_chunked(args, local)
+    else:
+        r = measure_batched(args, I.random_batch(args.batch_count, 1024, args.batch_max, 1, dtype=np.float32),
+                            local)
+    line = {"metric": bench.METRIC, "value": r.pop("metric_value"), "unit": r.pop("unit"), "n_gpus": 1,
+            "steps": r.pop("steps"), "warmup": r.pop("warmup"), "ms_per_step": r.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r.pop("dtype"),
+            "data": "synthetic (seeded generators)", "config": r.pop("config")}
+    line.update(r)
+    print(json.dumps(line), flush=True)

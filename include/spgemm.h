@@ -249,6 +249,28 @@ SPGEMM_API int spgemm_chunked(spgemm_handle handle, int dtype, const spgemm_csr 
                               spgemm_csr *C, spgemm_alloc_fn alloc, void *user, size_t fast_mem_budget,
                               void *stream);
 
+/* The two-phase product with operands in host memory (the paper's problem
+ * statement C = A*B with A, B and C where the caller keeps them): A (and B,
+ * unless flags has SPGEMM_HOST_B_ON_DEVICE) are host CSR arrays, pinned for
+ * full-speed copies.  The call copies them to the device (patterns first,
+ * values on a side stream while the symbolic phase runs), runs
+ * spgemm_symbolic and spgemm_numeric on the device copies (the same kernels
+ * as the device calls), and returns C: C->row_ptr (nrows(A)+1 int64,
+ * caller-allocated) filled; `alloc(user, nnz(C), ...)` called once for the
+ * entries; C->nrows, ncols, nnz, col_idx, values set.  C is on the host (its
+ * offsets copied out while the numeric phase runs, then its entries) unless
+ * flags has SPGEMM_HOST_C_ON_DEVICE, in which case C->row_ptr and the
+ * allocator's arrays are device memory and nothing is copied out.  The
+ * handle keeps the device copies (grown on demand, reused by later calls).
+ * Synchronises `stream` (C is complete on return).  Not in the paper as an
+ * entry point: its copies are what the chunked calls do when everything
+ * fits the fast memory.  Errors: those of the two phases; SPGEMM_ERR_NOMEM
+ * if a device copy cannot be allocated or alloc fails. */
+#define SPGEMM_HOST_B_ON_DEVICE 1
+#define SPGEMM_HOST_C_ON_DEVICE 2
+SPGEMM_API int spgemm_host(spgemm_handle handle, int dtype, const spgemm_csr *A, const spgemm_csr *B,
+                           spgemm_csr *C, spgemm_alloc_fn alloc, void *user, int flags, void *stream);
+
 /* Backward of C = A*B for a scalar loss L with dC = dL/dC given on the
  * pattern of C: the product is bilinear, so
  *   dA_ik = sum over stored b_kj of dC_ij b_kj   (dC B^T restricted to the pattern of A)

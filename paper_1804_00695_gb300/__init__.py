@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked_numeric": ([p, i32, p, p, p, C.c_size_t, p], i32),
         "spgemm_chunked_stats": ([p, p], i32),
         "spgemm_chunked": ([p, i32, p, p, p, ALLOC_FN, p, C.c_size_t, p], i32),
+        "spgemm_host": ([p, i32, p, p, p, ALLOC_FN, p, i32, p], i32),
         "spgemm_backward": ([p, i32, p, p, p, p, p, p], i32),
         "spgemm_batched_symbolic": ([p, i32, p, p, p, C.POINTER(i64), p, p], i32),
         "spgemm_batched_numeric": ([p, i32, i32, p, p, p, p], i32),
@@ -343,6 +344,43 @@ class Handle:
         _check(_lib.spgemm_chunked(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc), cb, None,
                                    budget, _stream(stream)))
         return HostCsr(A.nrows, B.ncols, rp, held["col"], held["val"])
+
+    def host_product(self, A: "HostCsr", B: "Csr", keep_on_device: bool = False, stream=None) -> "Csr":
+        """C = A*B with A in (pinned) host memory and B on the host or the
+        device (spgemm_host): the library copies the operands in, runs both
+        phases on the device and returns C on the host (pinned HostCsr), or
+        on the device (Csr) with keep_on_device."""
+        torch = _torch()
+        b_dev = B.row_ptr.device.type == "cuda"
+        dev = torch.device("cuda", self.device)
+        if keep_on_device:
+            rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+        else:
+            rp = torch.empty(A.nrows + 1, dtype=torch.int64).pin_memory()
+        held = {}
+
+        def alloc(user, nnz, col_p, val_p):
+            try:
+                if keep_on_device:
+                    held["col"] = torch.empty(nnz, dtype=torch.int32, device=dev)
+                    held["val"] = torch.empty(nnz, dtype=A.val.dtype, device=dev)
+                else:
+                    held["col"] = torch.empty(nnz, dtype=torch.int32).pin_memory()
+                    held["val"] = torch.empty(nnz, dtype=A.val.dtype).pin_memory()
+            except Exception:
+                return 1
+            col_p[0] = held["col"].data_ptr() if nnz else None
+            val_p[0] = held["val"].data_ptr() if nnz else None
+            return 0
+
+        cb = ALLOC_FN(alloc)
+        dc = CsrDesc(A.nrows, B.ncols, 0, rp.data_ptr(), None, None)
+        da, db = A.desc(), B.desc()
+        flags = (1 if b_dev else 0) | (2 if keep_on_device else 0)
+        _check(_lib.spgemm_host(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc), cb, None, flags,
+                                _stream(stream)))
+        cls = Csr if keep_on_device else HostCsr
+        return cls(A.nrows, B.ncols, rp, held["col"], held["val"])
 
     def chunked_stats(self) -> dict:
         r = ChunkStatsRec()

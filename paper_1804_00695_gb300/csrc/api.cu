@@ -83,7 +83,7 @@ struct spgemm_handle_s {
     void *arena = nullptr;
     size_t arena_cap = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev[12] = {};
+    cudaEvent_t ev[14] = {};   // [0..11] chunked calls, [12..13] spgemm_host
     std::vector<int64_t> zeros;   // offsets of an empty C (chunked symbolic plan)
     int *host_mm = nullptr;       // pinned, column ranges of A parts (chunked numeric)
     ChunkStats cstats;
@@ -97,6 +97,9 @@ struct spgemm_handle_s {
     spgemm_csr As{}, Bs{};
     int64_t *inst_out = nullptr;   // device, nbatch+1 offsets gathered from C
     int64_t max_ar = 0, max_an = 0, max_br = 0, max_bn = 0;
+    // spgemm_host: device copies of A, B (and C's entries), grown on demand
+    char *hbuf = nullptr, *hbufc = nullptr;
+    size_t hbuf_cap = 0, hbufc_cap = 0;
     // last numeric call (for the autotuner)
     bool have_last = false;
     int last_dtype = 0;
@@ -220,6 +223,8 @@ int spgemm_destroy(spgemm_handle h) {
     }
     if (h->arena) cudaFree(h->arena);
     if (h->bws) cudaFree(h->bws);
+    if (h->hbuf) cudaFree(h->hbuf);
+    if (h->hbufc) cudaFree(h->hbufc);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->s_in) cudaStreamDestroy(h->s_in);
@@ -443,14 +448,20 @@ int spgemm_numeric(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
                           h->max_alen, c);
 }
 
-// Side streams, events and the budget arena of the chunked calls.
-static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &env, Ctx &c) {
+// Side streams and events of the calls with host operands.
+static int side_streams(spgemm_handle h) {
     if (!h->s_in) {
         SG_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
         SG_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
         for (auto &e : h->ev) SG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         SG_CUDA(cudaMallocHost(&h->host_mm, 4 * sizeof(int)));
     }
+    return SPGEMM_OK;
+}
+
+// Side streams, events and the budget arena of the chunked calls.
+static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &env, Ctx &c) {
+    SG_TRY(side_streams(h));
     // work a previous call left on the side streams (one that returned an
     // error part-way) finishes before this call reuses or frees the arena
     SG_CUDA(cudaEventRecord(h->ev[8], h->s_in));
@@ -568,6 +579,117 @@ int spgemm_chunked(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm
     C->values = val;
     SG_TRY(spgemm_chunked_numeric(h, dtype, A, B, C, fast_mem_budget, stream));
     SG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return spgemm_check(h, stream);
+}
+
+// Grow-only device buffer of the host-operand calls (previous contents not kept).
+static int host_buf(char *&buf, size_t &cap, size_t bytes, cudaStream_t s) {
+    if (bytes <= cap) return SPGEMM_OK;
+    if (buf) SG_CUDA(cudaFreeAsync(buf, s));
+    buf = nullptr;
+    cap = 0;
+    const size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMallocAsync((void **)&buf, want, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        buf = nullptr;
+        set_error("spgemm_host: device copy of %zu bytes failed: %s", want, cudaGetErrorString(e));
+        return SPGEMM_ERR_NOMEM;
+    }
+    cap = want;
+    return SPGEMM_OK;
+}
+
+int spgemm_host(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_csr *B, spgemm_csr *C,
+                spgemm_alloc_fn alloc, void *user, int flags, void *stream) {
+    if (!h || !C || !alloc || !A || !B) { set_error("NULL handle, operand, C or allocator"); return SPGEMM_ERR_ARG; }
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) { set_error("bad dtype %d", dtype); return SPGEMM_ERR_ARG; }
+    if (!C->row_ptr) { set_error("C.row_ptr is NULL"); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", true));
+    SG_TRY(check_csr(B, "B", true));
+    if (A->ncols != B->nrows) { set_error("dimension mismatch"); return SPGEMM_ERR_DIM; }
+    const bool b_dev = (flags & SPGEMM_HOST_B_ON_DEVICE) != 0, c_dev = (flags & SPGEMM_HOST_C_ON_DEVICE) != 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    SG_TRY(side_streams(h));
+    const size_t vb = dtype == SPGEMM_F32 ? 4 : 8;
+    auto part = [](size_t x) { return align_up(x); };
+    // device copies: [A row_ptr | A col | A val | B row_ptr | B col | B val | C row_ptr]
+    const size_t oa_rp = 0, oa_col = oa_rp + part((size_t)(A->nrows + 1) * 8),
+                 oa_val = oa_col + part((size_t)A->nnz * 4), ob_rp = oa_val + part((size_t)A->nnz * vb);
+    const size_t ob_col = ob_rp + (b_dev ? 0 : part((size_t)(B->nrows + 1) * 8));
+    const size_t ob_val = ob_col + (b_dev ? 0 : part((size_t)B->nnz * 4));
+    const size_t oc_rp = ob_val + (b_dev ? 0 : part((size_t)B->nnz * vb));
+    const size_t total = oc_rp + part((size_t)(A->nrows + 1) * 8);
+    SG_TRY(host_buf(h->hbuf, h->hbuf_cap, total, s));
+    char *d = h->hbuf;
+    spgemm_csr Ad = *A, Bd = *B;
+    Ad.row_ptr = (int64_t *)(d + oa_rp);
+    Ad.col_idx = (int32_t *)(d + oa_col);
+    Ad.values = d + oa_val;
+    if (!b_dev) {
+        Bd.row_ptr = (int64_t *)(d + ob_rp);
+        Bd.col_idx = (int32_t *)(d + ob_col);
+        Bd.values = d + ob_val;
+    }
+    int64_t *crp = c_dev ? C->row_ptr : (int64_t *)(d + oc_rp);
+    // patterns on the caller's stream; values on the copy-in stream, after
+    // the work already queued on the caller's stream
+    SG_CUDA(cudaEventRecord(h->ev[12], s));
+    SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[12], 0));
+    SG_CUDA(cudaMemcpyAsync(Ad.row_ptr, A->row_ptr, (size_t)(A->nrows + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (A->nnz) SG_CUDA(cudaMemcpyAsync(Ad.col_idx, A->col_idx, (size_t)A->nnz * 4, cudaMemcpyHostToDevice, s));
+    if (!b_dev) {
+        SG_CUDA(cudaMemcpyAsync(Bd.row_ptr, B->row_ptr, (size_t)(B->nrows + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (B->nnz) SG_CUDA(cudaMemcpyAsync(Bd.col_idx, B->col_idx, (size_t)B->nnz * 4, cudaMemcpyHostToDevice, s));
+    }
+    if (A->nnz)
+        SG_CUDA(cudaMemcpyAsync(Ad.values, A->values, (size_t)A->nnz * vb, cudaMemcpyHostToDevice, h->s_in));
+    if (!b_dev && B->nnz)
+        SG_CUDA(cudaMemcpyAsync(Bd.values, B->values, (size_t)B->nnz * vb, cudaMemcpyHostToDevice, h->s_in));
+    SG_CUDA(cudaEventRecord(h->ev[13], h->s_in));
+    int64_t nnz = 0;
+    const int st_sym = spgemm_symbolic(h, &Ad, &Bd, crp, &nnz, stream);
+    if (st_sym != SPGEMM_OK) {
+        cudaStreamSynchronize(h->s_in);
+        return st_sym;
+    }
+    // C's offsets leave while the numeric phase runs
+    if (!c_dev) {
+        SG_CUDA(cudaEventRecord(h->ev[12], s));
+        SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[12], 0));
+        SG_CUDA(cudaMemcpyAsync(C->row_ptr, crp, (size_t)(A->nrows + 1) * 8, cudaMemcpyDeviceToHost, h->s_out));
+    }
+    int32_t *col = nullptr;
+    void *val = nullptr;
+    if (alloc(user, nnz, &col, &val) != 0 || (nnz > 0 && (!col || !val))) {
+        cudaStreamSynchronize(h->s_in);
+        cudaStreamSynchronize(h->s_out);
+        set_error("spgemm_host: the allocator failed for %lld entries of C", (long long)nnz);
+        return SPGEMM_ERR_NOMEM;
+    }
+    spgemm_csr Cd{A->nrows, B->ncols, nnz, crp, col, val};
+    if (!c_dev) {
+        SG_TRY(host_buf(h->hbufc, h->hbufc_cap, part((size_t)nnz * 4) + part((size_t)nnz * vb), s));
+        Cd.col_idx = (int32_t *)h->hbufc;
+        Cd.values = h->hbufc + part((size_t)nnz * 4);
+    }
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[13], 0));
+    SG_TRY(spgemm_numeric(h, dtype, &Ad, &Bd, &Cd, stream));
+    if (!c_dev && nnz) {
+        SG_CUDA(cudaMemcpyAsync(col, Cd.col_idx, (size_t)nnz * 4, cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaMemcpyAsync(val, Cd.values, (size_t)nnz * vb, cudaMemcpyDeviceToHost, s));
+    }
+    if (!c_dev) {
+        SG_CUDA(cudaEventRecord(h->ev[12], h->s_out));
+        SG_CUDA(cudaStreamWaitEvent(s, h->ev[12], 0));
+    }
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->nnz = nnz;
+    C->col_idx = col;
+    C->values = val;
+    SG_CUDA(cudaStreamSynchronize(s));
     return spgemm_check(h, stream);
 }
 

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) k_sym_first(
         const int64_t i = base + g;
         const int b = i < n ? bins[i] : 0;
         const bool active = b != BIN_EMPTY && b != BIN_HUGE && b != BIN_NARROW;
+        if (!__any_sync(0xffffffffu, active)) continue;   // rows done elsewhere
         const int64_t p0 = active ? arp[i] : 0;
         const int plen = active ? (int)(arp[i + 1] - p0) : 0;
 #pragma unroll
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) k_sym_first_strided(
         const int64_t i = base + g;
         const int b = i < n ? bins[i] : 0;
         const bool active = b != BIN_EMPTY && b != BIN_HUGE && b != BIN_NARROW;
+        if (!__any_sync(0xffffffffu, active)) continue;   // rows done elsewhere
         const int64_t p0 = active ? arp[i] : 0;
         const int plen = active ? (int)(arp[i + 1] - p0) : 0;
 #pragma unroll
