@@ -14,7 +14,10 @@ Multilevel Memory Architectures":
   * ``compress_rows``     - Section 2.1 column compression (block index, bit mask);
   * ``row_flops``         - Section 3.1: insertions per row = multiplications;
   * ``partition`` & co.   - Algorithm 4 and the copy costs of Algorithms 2 and 3
-                            (see ``oracle.chunking``).
+                            (see ``oracle.chunking``);
+  * ``triangles``         - triangle counting by the masked product L*L .* L
+                            of Section 4.1's triangle-counting experiment
+                            (degree-ordered lower triangle, sorted-row merges).
 """
 from __future__ import annotations
 
@@ -38,6 +41,9 @@ def lib():
         _lib.oracle_fma_range_rows.argtypes = [i64, i64, i64, i64, i64] + [p] * 13
         _lib.oracle_backward.argtypes = [i64, i64] + [p] * 11
         _lib.oracle_set_num_threads.argtypes = [C.c_int]
+        _lib.oracle_degree_order.argtypes = [i64, p, p]
+        _lib.oracle_triangles.argtypes = [i64, p, p, p, p]
+        _lib.oracle_triangles.restype = i64
     return _lib
 
 
@@ -201,3 +207,28 @@ def _cat_rows(parts):
         cols.append(col); vals.append(val)
     return (np.concatenate(rps), np.concatenate(cols) if cols else np.zeros(0, np.int32),
             np.concatenate(vals) if vals else np.zeros(0))
+
+
+def degree_order(g) -> np.ndarray:
+    """New label of every vertex: position of (degree, vertex) in ascending
+    order (ties by vertex index)."""
+    perm = np.zeros(g.nrows, dtype=np.int64)
+    if lib().oracle_degree_order(g.nrows, _p(_c64(g.row_ptr)), _p(perm)) != 0:
+        raise MemoryError("oracle degree order failed")
+    return perm
+
+
+def triangles(g, perm=None):
+    """(total, per-vertex counts) of triangles of the undirected graph with
+    the symmetric pattern g (no self loops), by the masked product L*L .* L:
+    L the strictly lower triangle after relabelling by `perm` (default: the
+    degree order); the count of vertex u is the number of triangles whose
+    highest-labelled vertex is u."""
+    rc = np.zeros(g.nrows, dtype=np.int64)
+    pp = None if perm is None else _c64(perm)
+    total = lib().oracle_triangles(g.nrows, _p(_c64(g.row_ptr)), _p(_c32(g.col)), _p(pp), _p(rc))
+    if total == -1:
+        raise MemoryError("oracle triangles failed")
+    if total == -2:
+        raise ValueError("perm is not a permutation")
+    return int(total), rc
