@@ -271,6 +271,24 @@ SPGEMM_API int spgemm_chunked(spgemm_handle handle, int dtype, const spgemm_csr 
 SPGEMM_API int spgemm_host(spgemm_handle handle, int dtype, const spgemm_csr *A, const spgemm_csr *B,
                            spgemm_csr *C, spgemm_alloc_fn alloc, void *user, int flags, void *stream);
 
+/* Triangles of an undirected graph by a masked sparse product (the
+ * triangle-counting experiment of Section 4.1, after Wolf et al.): the
+ * vertices are relabelled in order of non-decreasing degree, L is the
+ * strictly lower triangle of the relabelled pattern, and the number of
+ * triangles is the sum of (L*L) masked by L, computed as L x compressed(L)
+ * (Section 2.1's column compression of the right-hand operand).
+ * A: device CSR, the symmetric pattern of the graph without self loops
+ * (values unused; a self loop is ignored).  *total (host): the number of
+ * triangles.  perm (device, nrows int64, may be NULL): the label of every
+ * vertex (degrees non-decreasing along the labels; vertices of equal degree
+ * in an unspecified order).  vertex_counts (device, nrows int64, may be
+ * NULL): for every vertex u, the triangles whose highest-labelled vertex is
+ * u (they sum to *total).  The handle keeps the workspace (grown on demand).
+ * Synchronises `stream`.  Errors: SPGEMM_ERR_DIM (not square),
+ * SPGEMM_ERR_INDEX (a column out of range), SPGEMM_ERR_NOMEM. */
+SPGEMM_API int spgemm_triangles(spgemm_handle handle, const spgemm_csr *A, int64_t *total, int64_t *perm,
+                                int64_t *vertex_counts, void *stream);
+
 /* Backward of C = A*B for a scalar loss L with dC = dL/dC given on the
  * pattern of C: the product is bilinear, so
  *   dA_ik = sum over stored b_kj of dC_ij b_kj   (dC B^T restricted to the pattern of A)

@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked_stats": ([p, p], i32),
         "spgemm_chunked": ([p, i32, p, p, p, ALLOC_FN, p, C.c_size_t, p], i32),
         "spgemm_host": ([p, i32, p, p, p, ALLOC_FN, p, i32, p], i32),
+        "spgemm_triangles": ([p, p, C.POINTER(i64), p, p, p], i32),
         "spgemm_backward": ([p, i32, p, p, p, p, p, p], i32),
         "spgemm_batched_symbolic": ([p, i32, p, p, p, C.POINTER(i64), p, p], i32),
         "spgemm_batched_numeric": ([p, i32, i32, p, p, p, p], i32),
@@ -381,6 +382,22 @@ class Handle:
                                 _stream(stream)))
         cls = Csr if keep_on_device else HostCsr
         return cls(A.nrows, B.ncols, rp, held["col"], held["val"])
+
+    def triangles(self, G: "Csr", labels: bool = False, stream=None):
+        """Triangles of the undirected graph with the symmetric pattern G
+        (device) by the masked product L*L .* L (spgemm_triangles).  Returns
+        the count, or with labels=True (count, labels of the vertices,
+        per-vertex counts) as device int64 tensors."""
+        torch = _torch()
+        total = C.c_int64()
+        perm = vc = None
+        if labels:
+            perm = torch.empty(G.nrows, dtype=torch.int64, device=G.row_ptr.device)
+            vc = torch.empty(G.nrows, dtype=torch.int64, device=G.row_ptr.device)
+        d = G.desc()
+        _check(_lib.spgemm_triangles(self._h, C.byref(d), C.byref(total), perm.data_ptr() if labels else None,
+                                     vc.data_ptr() if labels else None, _stream(stream)))
+        return (int(total.value), perm, vc) if labels else int(total.value)
 
     def chunked_stats(self) -> dict:
         r = ChunkStatsRec()

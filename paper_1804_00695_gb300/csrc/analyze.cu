@@ -14,6 +14,8 @@ namespace sg {
 // alongside: desc = {first entry (int64), entries, pairs} for the product
 // kernels, ana = {entries, pairs} for the analysis, and the row's first and
 // last block (minmax) for the span tests.
+constexpr int64_t COMPRESS_LONG = 128;   // rows longer than this take a warp each
+
 __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
                            const int32_t *__restrict__ col, int2 *__restrict__ pairs,
                            int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
@@ -22,6 +24,7 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     const int64_t beg = rp[r], end = rp[r + 1];
+    if (end - beg > COMPRESS_LONG) return;   // k_compress_long
     int cur = -1;
     unsigned m = 0;
     int n = 0, bmin = INT_MAX, bmax = INT_MIN, prev = -1;
@@ -55,6 +58,95 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
     if (unsorted && unsorted_flag) atomicOr(unsorted_flag, 1);
 }
 
+// The same for the rows longer than COMPRESS_LONG, a warp per row, 32
+// consecutive entries at a time: a pair starts where an entry's block
+// differs from the previous entry's; the masks of a run are ORed by a
+// segmented scan over the lanes; a run that reaches the end of the 32 is
+// carried into the next 32 (its pair written once it ends).
+__global__ void k_compress_long(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
+                                const int32_t *__restrict__ col, int2 *__restrict__ pairs,
+                                int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
+                                int4 *__restrict__ desc, int2 *__restrict__ ana, int *err,
+                                int *unsorted_flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    bool bad = false, unsorted = false;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
+        const int64_t beg = rp[r], end = rp[r + 1];
+        if (end - beg <= COMPRESS_LONG) continue;
+        int cblk = -1;          // block of the run carried from the previous 32 (-1: none)
+        unsigned cmask = 0;
+        int npairs = 0;         // runs started so far (the carried one included)
+        int prevc = -1;         // last valid column of the previous 32
+        int bmin = INT_MAX, bmax = INT_MIN;
+        for (int64_t base = beg; base < end; base += 32) {
+            const int64_t p = base + lane;
+            int c = p < end ? col[p] : -1;
+            if (c >= 0 && (int64_t)c >= ncols) { bad = true; c = -1; }
+            if (p < end && c < 0) bad = true;
+            const bool valid = c >= 0;
+            // sortedness against the previous valid entry in storage order
+            int pc = __shfl_up_sync(0xffffffffu, c, 1);
+            if (lane == 0) pc = prevc;
+            unsorted |= valid && pc >= 0 && c <= pc;
+            const int b = valid ? c >> 5 : -2;
+            int pb = __shfl_up_sync(0xffffffffu, b, 1);
+            if (lane == 0) pb = cblk;
+            bool start = valid && b != pb;
+            unsigned m = valid ? 1u << (c & 31) : 0u;
+            if (lane == 0 && valid && !start) m |= cmask;   // continues the carried run
+            // invalid lanes (bad columns) break runs: they act as run starts with no bits
+            bool seg = start || !valid;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned ym = __shfl_up_sync(0xffffffffu, m, d);
+                const bool ys = __shfl_up_sync(0xffffffffu, seg, d);
+                if (lane >= d && !seg) m |= ym;
+                if (lane >= d) seg = seg || ys;
+            }
+            const unsigned starts = __ballot_sync(0xffffffffu, start);
+            const int idx = npairs + __popc(starts & ((2u << lane) - 1u)) - 1;
+            // the carried run, if it ends before this 32 continues it
+            if (lane == 0 && cblk >= 0 && !(valid && !start)) {
+                if (pairs) pairs[beg + npairs - 1] = make_int2(cblk, (int)cmask);
+            }
+            const bool nxt_start = __shfl_down_sync(0xffffffffu, start || !valid, 1);
+            const bool last_valid = valid && (lane == 31 || nxt_start);
+            const unsigned lastm = __ballot_sync(0xffffffffu, valid);
+            const int top = lastm ? 31 - __clz(lastm) : -1;   // last valid lane
+            // runs that end inside this 32 are written; the one at the last
+            // valid lane is carried unless the row ends here
+            const bool row_ends = base + 32 >= end;
+            if (last_valid && (lane != top || row_ends) && pairs && idx >= 0) pairs[beg + idx] = make_int2(b, (int)m);
+            npairs += __popc(starts);
+            if (top >= 0) {
+                const int tb = __shfl_sync(0xffffffffu, b, top);
+                const unsigned tm = __shfl_sync(0xffffffffu, m, top);
+                cblk = row_ends ? -1 : tb;
+                cmask = row_ends ? 0u : tm;
+                prevc = __shfl_sync(0xffffffffu, c, top);
+            }
+            if (valid) { bmin = min(bmin, b); bmax = max(bmax, b); }
+        }
+        if (cblk >= 0 && lane == 0 && pairs) pairs[beg + npairs - 1] = make_int2(cblk, (int)cmask);
+        for (int d = 16; d > 0; d >>= 1) {
+            bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, d));
+            bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, d));
+        }
+        if (lane == 0) {
+            const int len = (int)(end - beg);
+            if (ccnt) ccnt[r] = npairs;
+            if (minmax) minmax[r] = make_int2(bmin, bmax);
+            if (desc) desc[r] = make_int4((int)(unsigned)(uint64_t)beg, (int)((uint64_t)beg >> 32), len, npairs);
+            if (ana) ana[r] = make_int2(len, npairs);
+        }
+    }
+    unsorted = __any_sync(0xffffffffu, unsorted);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) atomicOr(err, DERR_COL_RANGE);
+    if (lane == 0 && unsorted && unsorted_flag) atomicOr(unsorted_flag, 1);
+}
+
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
                     int2 *ana, int *err, Ctx &c, int *unsorted) {
     if (M.nrows == 0) return SPGEMM_OK;
@@ -62,6 +154,11 @@ int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minma
     c.begin("compress", M.nrows);
     k_compress<<<(unsigned)blocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
                                                     ccnt, minmax, desc, ana, err, unsorted);
+    c.end();
+    const int64_t wblocks = std::min<int64_t>((M.nrows + 7) / 8, (int64_t)c.nsm * 16);
+    c.begin("compress_long", M.nrows);
+    k_compress_long<<<(unsigned)wblocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs, ccnt,
+                                                        minmax, desc, ana, err, unsorted);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;

@@ -97,6 +97,9 @@ struct spgemm_handle_s {
     spgemm_csr As{}, Bs{};
     int64_t *inst_out = nullptr;   // device, nbatch+1 offsets gathered from C
     int64_t max_ar = 0, max_an = 0, max_br = 0, max_bn = 0;
+    // spgemm_triangles: workspace, grown on demand
+    char *tws = nullptr;
+    size_t tws_cap = 0;
     // spgemm_host: device copies of A, B (and C's entries), grown on demand
     char *hbuf = nullptr, *hbufc = nullptr;
     size_t hbuf_cap = 0, hbufc_cap = 0;
@@ -224,6 +227,7 @@ int spgemm_destroy(spgemm_handle h) {
     if (h->arena) cudaFree(h->arena);
     if (h->bws) cudaFree(h->bws);
     if (h->hbuf) cudaFree(h->hbuf);
+    if (h->tws) cudaFree(h->tws);
     if (h->hbufc) cudaFree(h->hbufc);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -691,6 +695,25 @@ int spgemm_host(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_cs
     C->values = val;
     SG_CUDA(cudaStreamSynchronize(s));
     return spgemm_check(h, stream);
+}
+
+int spgemm_triangles(spgemm_handle h, const spgemm_csr *A, int64_t *total, int64_t *perm, int64_t *vertex_counts,
+                     void *stream) {
+    if (!h || !total) { set_error("NULL handle or total"); return SPGEMM_ERR_ARG; }
+    SG_TRY(check_csr(A, "A", false));
+    if (A->nrows != A->ncols) { set_error("the graph's pattern must be square"); return SPGEMM_ERR_DIM; }
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CUDA(cudaSetDevice(h->device));
+    *total = 0;
+    if (A->nrows == 0) return SPGEMM_OK;
+    SG_TRY(host_buf(h->tws, h->tws_cap, triangles_ws(A->nrows, A->nnz, h->nsm), s));
+    SG_CUDA(cudaMemsetAsync(&h->dstate->err, 0, sizeof(int), s));
+    Ctx c = h->ctx(s);
+    SG_TRY(launch_triangles(*A, h->tws, perm, vertex_counts, &h->dstate->triangles, &h->dstate->err, c));
+    SG_TRY(fetch_state(h, s));
+    SG_TRY(device_errors(h->hstate->err));
+    *total = (int64_t)h->hstate->triangles;
+    return SPGEMM_OK;
 }
 
 int spgemm_chunked_stats(spgemm_handle h, spgemm_chunk_stats *out) {

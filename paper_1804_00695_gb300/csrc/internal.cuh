@@ -46,6 +46,7 @@ struct DevState {          // lives in device memory, one per handle
     int b_unsorted;          // some row of B has columns out of ascending order
     int pad2;
     long long max_alen;      // longest row of A (analysis)
+    unsigned long long triangles;   // spgemm_triangles: the count
 };
 
 // ---------------------------------------------------------------- bins
@@ -271,6 +272,14 @@ struct BatchInst {
 int launch_stack(const BatchInst *dinst, int nb, int64_t max_rows, int64_t max_nnz, int which, bool pattern,
                  int vb, int64_t total_rows, int64_t total_nnz, int64_t *rp, int32_t *col, void *val,
                  Ctx &c);
+
+// triangles.cu: triangles of the undirected graph with the symmetric
+// pattern A by the masked product L*L .* L (degree-ordered lower triangle
+// L, compressed right-hand operand); the count lands in *total (device);
+// perm_out / vcount (device, optional): labels, per-vertex counts.
+size_t triangles_ws(int64_t n, int64_t nnz, int nsm);
+int launch_triangles(const spgemm_csr &A, void *ws, int64_t *perm_out, int64_t *vcount, unsigned long long *total,
+                     int *err, Ctx &c);
 
 // backward.cu: dA on pattern(A), dB on pattern(B) from dC on pattern(C).
 int launch_backward(int dtype, const spgemm_csr &A, const spgemm_csr &B, const spgemm_csr &C, void *da,

@@ -316,3 +316,46 @@ def test_row_flops_and_compression(h):
         for kb, mk in pairs2[a.row_ptr[i]:a.row_ptr[i] + cnt2[i]]:
             dec.update(32 * int(kb) + t for t in range(32) if (int(mk) >> t) & 1)
         assert dec == s
+
+
+def test_compression_long_rows(h):
+    """Rows longer than 128 entries (compressed by a warp each): sorted rows
+    with dense runs crossing the 32-entry steps (blocks full of columns) and
+    sparse stretches, against the canonical compression; unsorted long rows,
+    against the runs of equal blocks in storage order."""
+    rows, cols = [], []
+    for i in range(60):
+        w = 129 + 37 * i
+        dense = np.arange(w // 2) + 64 * (i % 5)                 # runs of 32 columns per block
+        sparse = 5000 + np.arange(w - w // 2) * (7 + i % 3)
+        c = np.unique(np.concatenate([dense, sparse]))
+        rows += [i] * len(c)
+        cols += c.tolist()
+    key = np.array(rows, dtype=np.int64) * 100000 + np.array(cols, dtype=np.int64)
+    b = I.Csr(60, 100000, np.concatenate([[0], np.cumsum(np.bincount(key // 100000, minlength=60))]).astype(np.int64),
+              (key % 100000).astype(np.int32), np.ones(len(key)))
+    cnt, pairs = h.compress(to_dev(b))
+    rp, blk, mask = oracle.compress_rows(b)
+    cnt = cnt.cpu().numpy()
+    pairs = pairs.cpu().numpy().view(np.uint32)
+    assert np.array_equal(cnt, np.diff(rp))
+    for k in range(b.nrows):
+        got = pairs[b.row_ptr[k]:b.row_ptr[k] + cnt[k]]
+        assert np.array_equal(got[:, 0], blk[rp[k]:rp[k + 1]].astype(np.uint32))
+        assert np.array_equal(got[:, 1], mask[rp[k]:rp[k + 1]])
+    # the same rows with their entries permuted: runs of equal blocks in
+    # storage order, each run one pair
+    order = np.lexsort((I.uniform01(np.arange(b.nnz, dtype=np.uint64), 19), np.repeat(np.arange(60), np.diff(b.row_ptr))))
+    bu = I.Csr(60, 100000, b.row_ptr, b.col[order], b.val)
+    cnt2, pairs2 = h.compress(to_dev(bu))
+    cnt2 = cnt2.cpu().numpy(); pairs2 = pairs2.cpu().numpy().view(np.uint32)
+    for k in range(bu.nrows):
+        c = bu.col[bu.row_ptr[k]:bu.row_ptr[k + 1]].astype(np.int64)
+        bl = c >> 5
+        runs = np.concatenate([[0], np.nonzero(bl[1:] != bl[:-1])[0] + 1])
+        assert cnt2[k] == len(runs)
+        got = pairs2[bu.row_ptr[k]:bu.row_ptr[k] + cnt2[k]]
+        for t, r0 in enumerate(runs):
+            r1 = runs[t + 1] if t + 1 < len(runs) else len(c)
+            assert got[t, 0] == bl[r0]
+            assert got[t, 1] == np.bitwise_or.reduce((np.uint64(1) << (c[r0:r1] % 32).astype(np.uint64))).astype(np.uint32)
