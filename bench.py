@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (profiling cases)")
     ap.add_argument("--batch-max", type=int, default=65536, help="largest instance order of the batched workload")
     ap.add_argument("--workload", default="galerkin128",
-                    choices=["galerkin128", "rmat20", "chunked256", "batched256"])
+                    choices=["galerkin128", "rmat20", "triangles20", "chunked256", "batched256"])
     ap.add_argument("--no-secondary", action="store_true",
                     help="default line without the R-MAT, chunked and batched workloads")
     return ap.parse_args()
@@ -421,6 +421,7 @@ def main():
         torch.cuda.empty_cache()
         secondary = {}
         for name, fn in (("rmat20", lambda: bench_workloads.measure_rmat(args, gen.rmat_graph(), local)),
+                         ("triangles20", lambda: bench_workloads.measure_triangles(args, gen.rmat_graph(), local)),
                          ("chunked256", lambda: bench_workloads.measure_chunked(args, local)),
                          ("batched256", lambda: bench_workloads.measure_batched(args, gen.batch_pairs(), local))):
             t0 = time.perf_counter()

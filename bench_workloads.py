@@ -1,9 +1,10 @@
 """Benchmark workloads besides the default Galerkin product; each measure_*
 function returns a dict that bench.py puts under "secondary" in its default
-line, and ``python bench.py --workload rmat20|chunked256|batched256`` prints
+line, and ``python bench.py --workload rmat20|triangles20|chunked256|batched256`` prints
 one of them as a full line.
 
 * rmat20     - C = A*A, A symmetrised R-MAT scale 20, edge factor 16, FP32.
+* triangles20 - triangles of the same graph by the masked product L*L .* L.
 * chunked256 - C = A*A, A the 27-point Laplacian on 256^3, FP64, operands and
                result in pinned host memory, 4 GB device budget (Section 3.3.1).
 * batched256 - 256 products A_i*B_i, rows log-uniform in [1024, 65536], 4-32
@@ -208,6 +209,60 @@ def measure_rmat(args, g, local):
             "kernels_ms_per_step": {k: v[2] / steps for k, v in sorted(tim.items())},
             "gpu_launches": sum(v[0] for v in tim.values()), "clocks": clk, "cpu_baseline": cpu,
             "parity": par}
+
+
+# ---------------------------------------------------------------- triangles
+def measure_triangles(args, g, local):
+    """Triangle counting by the masked product L*L .* L on the R-MAT graph
+    (the paper's triangle-counting experiment): time per count, the
+    masked product's multiplications (sum over stored L_ik of nnz(L_k), from
+    the library's own labels), a CPU baseline (the oracle on the whole graph)
+    and the parity of the count."""
+    import torch
+    import oracle
+    import paper_1804_00695_gb300 as sg
+    G = sg.Csr.from_host(g, "cuda", np.float32)
+    h = sg.Handle(local)
+    total, perm, _ = h.triangles(G, labels=True)
+    perm = perm.cpu().numpy()
+    rows = np.repeat(np.arange(g.nrows), np.diff(g.row_ptr))
+    pr, pc = perm[rows], perm[g.col.astype(np.int64)]
+    low = pc < pr
+    llen = np.bincount(pr[low], minlength=g.nrows)
+    lmults = int(llen[pc[low]].sum())
+    steps, warm = 10, 3
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        h.triangles(G)
+    h.set_timing(True)
+    h.reset_timings()
+    clocks = bench.ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        h.triangles(G)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    tim = h.timings()
+    h.set_timing(False)
+    t0 = time.perf_counter()
+    ref, _ = oracle.triangles(g)
+    dt = time.perf_counter() - t0
+    return {"metric_value": 2 * lmults / (ms / 1e3) / 1e9, "unit": "GFLOP/s (2 x masked-product multiplications/s)",
+            "ms_per_step": ms, "steps": steps, "warmup": warm, "dtype": "int (pattern only)",
+            "config": {"workload": f"triangles of the R-MAT scale {args.rmat_scale} graph (edge factor 16) by "
+                                   "L*L .* L, L the degree-ordered lower triangle", "triangles": total,
+                       "edges": int(g.nnz // 2), "nnz_L": int(low.sum()), "masked_product_mults": lmults},
+            "triangles_per_s": total / (ms / 1e3), "edges_per_s": (g.nnz // 2) / (ms / 1e3),
+            "kernels_ms_per_step": {k: v[2] / steps for k, v in sorted(tim.items())}, "clocks": clk,
+            "cpu_baseline": {"value": 2 * lmults / dt / 1e9, "unit": "GFLOP/s (2 x masked-product multiplications/s)",
+                             "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"the whole graph, sorted-row merges, {dt:.2f} s"},
+            "parity": {"count_exact": total == ref, "oracle_count": ref}}
 
 
 # ---------------------------------------------------------------- chunked
@@ -454,6 +509,8 @@ def run(args, rank, world, local):
     from paper_1804_00695_gb300 import inputs as I
     if args.workload == "rmat20":
         r = measure_rmat(args, I.rmat_symmetric(args.rmat_scale, 16, seed=1), local)
+    elif args.workload == "triangles20":
+        r = measure_triangles(args, I.rmat_symmetric(args.rmat_scale, 16, seed=1), local)
     elif args.workload == "chunked256":
         r = measure_chunked(args, local)
     else:

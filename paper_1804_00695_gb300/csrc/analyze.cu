@@ -71,9 +71,14 @@ __global__ void k_compress_long(int64_t nrows, int64_t ncols, const int64_t *__r
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     bool bad = false, unsorted = false;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
+    // a warp tests 32 rows at once and compresses the long ones among them
+    for (int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; r0 < nrows; r0 += warps * 32) {
+      const int64_t rl = r0 + lane;
+      unsigned longs = __ballot_sync(0xffffffffu, rl < nrows && rp[rl + 1] - rp[rl] > COMPRESS_LONG);
+      while (longs) {
+        const int64_t r = r0 + __ffs(longs) - 1;
+        longs &= longs - 1u;
         const int64_t beg = rp[r], end = rp[r + 1];
-        if (end - beg <= COMPRESS_LONG) continue;
         int cblk = -1;          // block of the run carried from the previous 32 (-1: none)
         unsigned cmask = 0;
         int npairs = 0;         // runs started so far (the carried one included)
@@ -140,6 +145,7 @@ __global__ void k_compress_long(int64_t nrows, int64_t ncols, const int64_t *__r
             if (desc) desc[r] = make_int4((int)(unsigned)(uint64_t)beg, (int)((uint64_t)beg >> 32), len, npairs);
             if (ana) ana[r] = make_int2(len, npairs);
         }
+      }
     }
     unsorted = __any_sync(0xffffffffu, unsorted);
     bad = __any_sync(0xffffffffu, bad);
@@ -155,7 +161,7 @@ int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minma
     k_compress<<<(unsigned)blocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
                                                     ccnt, minmax, desc, ana, err, unsorted);
     c.end();
-    const int64_t wblocks = std::min<int64_t>((M.nrows + 7) / 8, (int64_t)c.nsm * 16);
+    const int64_t wblocks = std::min<int64_t>((M.nrows + 255) / 256, (int64_t)c.nsm * 16);
     c.begin("compress_long", M.nrows);
     k_compress_long<<<(unsigned)wblocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs, ccnt,
                                                         minmax, desc, ana, err, unsorted);
