@@ -423,6 +423,7 @@ def main():
         for name, fn in (("rmat20", lambda: bench_workloads.measure_rmat(args, gen.rmat_graph(), local)),
                          ("triangles20", lambda: bench_workloads.measure_triangles(args, gen.rmat_graph(), local)),
                          ("chunked256", lambda: bench_workloads.measure_chunked(args, local)),
+                         ("placement128", lambda: bench_workloads.measure_placement(args, (a, p, r), local)),
                          ("batched256", lambda: bench_workloads.measure_batched(args, gen.batch_pairs(), local))):
             t0 = time.perf_counter()
             try:

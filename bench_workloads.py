@@ -7,6 +7,8 @@ one of them as a full line.
 * triangles20 - triangles of the same graph by the masked product L*L .* L.
 * chunked256 - C = A*A, A the 27-point Laplacian on 256^3, FP64, operands and
                result in pinned host memory, 4 GB device budget (Section 3.3.1).
+* placement128 - the Galerkin products with A, B, C each in HBM, pinned host
+               or managed memory (the placements of Table 3).
 * batched256 - 256 products A_i*B_i, rows log-uniform in [1024, 65536], 4-32
                random columns per row, FP32: batched forward and backward
                against a per-instance loop on the same GPU.
@@ -496,6 +498,75 @@ def measure_batched(args, pairs, local):
                                        f"{t_cpu:.2f} s"},
             "parity": {"instances": [done[0], done[-1]], "forward_pattern_exact_and_in_tolerance": bool(par_ok),
                        "backward_instance": i0, "backward_in_tolerance": bwd_ok}}
+
+
+# ---------------------------------------------------------------- placements
+PLACEMENTS = (("HBM", "device", "device", "device"), ("A_Pin", "pinned", "device", "device"),
+              ("B_Pin", "device", "pinned", "device"), ("C_Pin", "device", "device", "pinned"),
+              ("HostPin", "pinned", "pinned", "pinned"), ("UVM", "managed", "managed", "managed"))
+
+
+def measure_placement(args, problem, local, steps=3, warmup=2):
+    """The columns of Table 3 (Section 3.3.1) on this GPU: GFLOP/s of the two
+    Galerkin products A*P and R*(AP) (AP the oracle's) with A, B and C each in
+    HBM, pinned host memory (read and written in place over the host link)
+    or managed memory.  Each product is timed with CUDA events over the
+    symbolic and numeric calls into preallocated C arrays of the placement;
+    the first call (cold: page migration for UVM) is reported apart.  Every
+    placement's C is compared with the oracle's whole product."""
+    import torch
+    import oracle
+    import paper_1804_00695_gb300 as sg
+    from paper_1804_00695_gb300 import inputs as I
+    a, p, r = problem
+    t0 = time.perf_counter()
+    ap_o = oracle.spgemm(a, p)
+    ap = I.Csr(a.nrows, p.ncols, ap_o.row_ptr, ap_o.col, ap_o.val)
+    rap_o = oracle.spgemm(r, ap)
+    t_oracle = time.perf_counter() - t0
+    dev = torch.device("cuda", local)
+    h = sg.Handle(local)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for label, x, y, ref in (("A*P", a, p, ap_o), ("R*AP", r, ap, rap_o)):
+        flops = 2 * int(ref.mults.sum())
+        res = {}
+        for name, pa, pb, pc in PLACEMENTS:
+            X, Y = sg.Csr.placed(x, pa, device=dev), sg.Csr.placed(y, pb, device=dev)
+            nnz = ref.nnz
+            Cm = sg.Csr(x.nrows, y.ncols, sg.placed_empty(x.nrows + 1, torch.int64, pc, dev),
+                        sg.placed_empty(nnz, torch.int32, pc, dev), sg.placed_empty(nnz, torch.float64, pc, dev))
+            ms = []
+            for it in range(warmup + steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                _, n2 = h.symbolic(X, Y, out=Cm.row_ptr)
+                h.numeric_into(X, Y, Cm)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                assert n2 == nnz
+                ms.append(e0.elapsed_time(e1))
+            par = _compare_rows(Cm.row_ptr.cpu().numpy(), Cm.col.cpu().numpy(), Cm.val.cpu().numpy(), ref,
+                                TOL["f64"])
+            t = statistics.median(ms[warmup:])
+            res[name] = {"A": pa, "B": pb, "C": pc, "ms": t, "gflops": flops / (t / 1e3) / 1e9,
+                         "first_call_ms": ms[0], "parity": par}
+            del X, Y, Cm
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        base = res["HBM"]["gflops"]
+        for v in res.values():
+            v["vs_hbm"] = v["gflops"] / base
+        out[label] = {"mults": flops // 2, "nnz_C": ref.nnz, "placements": res}
+    return {"config": {"workload": f"placements of Table 3: A*P and R*(AP) of the 27-point {args.grid}^3 "
+                                   f"Galerkin problem, FP64, AP from the oracle",
+                       "steps": steps, "warmup": warmup},
+            "products": out, "oracle_s": t_oracle,
+            "parity": {"all_exact_patterns": all(v["parity"]["pattern_exact"] for o in out.values()
+                                                 for v in o["placements"].values()),
+                       "all_values_in_tolerance": all(v["parity"]["values_in_tolerance"] for o in out.values()
+                                                      for v in o["placements"].values())}}
 
 
 # ---------------------------------------------------------------- one workload as a full line

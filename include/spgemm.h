@@ -271,6 +271,21 @@ SPGEMM_API int spgemm_chunked(spgemm_handle handle, int dtype, const spgemm_csr 
 SPGEMM_API int spgemm_host(spgemm_handle handle, int dtype, const spgemm_csr *A, const spgemm_csr *B,
                            spgemm_csr *C, spgemm_alloc_fn alloc, void *user, int flags, void *stream);
 
+/* Placement of the operands (the comparators of Table 3, Section 3.3.1).
+ * The device calls (spgemm_symbolic, spgemm_numeric, spgemm_backward, the
+ * batched calls, spgemm_triangles) dereference A, B and C through whatever
+ * pointers the caller passes: device memory (the default, "HBM"), pinned
+ * host memory (cudaHostAlloc / cudaHostRegister: read and written in place
+ * over the host link, "Pin" in Table 3), or managed memory (migrated to the
+ * device on demand, "UVM").  The library's own workspace is always device
+ * memory.  A placement changes only where the bytes travel, never the
+ * result.  spgemm_managed_alloc / spgemm_managed_free: managed memory for a
+ * caller placing operands there (cudaMallocManaged, cudaMemAttachGlobal;
+ * the pages start wherever they are first touched).  Errors:
+ * SPGEMM_ERR_NOMEM, SPGEMM_ERR_CUDA. */
+SPGEMM_API int spgemm_managed_alloc(size_t bytes, void **ptr);
+SPGEMM_API int spgemm_managed_free(void *ptr);
+
 /* Triangles of an undirected graph by a masked sparse product (the
  * triangle-counting experiment of Section 4.1, after Wolf et al.): the
  * vertices are relabelled in order of non-decreasing degree, L is the

@@ -16,6 +16,8 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+
+import numpy as np
 from dataclasses import dataclass
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -101,6 +103,8 @@ def load(path: str = LIB_PATH):
         "spgemm_chunked": ([p, i32, p, p, p, ALLOC_FN, p, C.c_size_t, p], i32),
         "spgemm_host": ([p, i32, p, p, p, ALLOC_FN, p, i32, p], i32),
         "spgemm_triangles": ([p, p, C.POINTER(i64), p, p, p], i32),
+        "spgemm_managed_alloc": ([C.c_size_t, C.POINTER(p)], i32),
+        "spgemm_managed_free": ([p], i32),
         "spgemm_backward": ([p, i32, p, p, p, p, p, p], i32),
         "spgemm_batched_symbolic": ([p, i32, p, p, p, C.POINTER(i64), p, p], i32),
         "spgemm_batched_numeric": ([p, i32, i32, p, p, p, p], i32),
@@ -149,6 +153,16 @@ class Csr:
                        self.col.data_ptr() if self.col.numel() else None,
                        self.val.data_ptr() if (self.val is not None and self.val.numel()) else None)
 
+    def dev_desc(self) -> CsrDesc:
+        """desc() for a device call: every array must be device, managed or
+        pinned host memory (the kernels dereference it in place); pageable
+        host memory is refused here rather than faulting on the device."""
+        for t in (self.row_ptr, self.col, self.val):
+            if t is not None and t.device.type == "cpu" and t.numel() and not t.is_pinned():
+                raise ValueError("a device call needs device, managed or pinned host arrays; "
+                                 "got pageable host memory (use Csr.placed or tensor.pin_memory())")
+        return self.desc()
+
     @staticmethod
     def from_host(m, device="cuda", dtype=None) -> "Csr":
         """Copy an ``inputs.Csr`` (numpy) to the device."""
@@ -157,6 +171,13 @@ class Csr:
         return Csr(m.nrows, m.ncols, torch.from_numpy(m.row_ptr).to(device),
                    torch.from_numpy(m.col).to(device), torch.from_numpy(val).to(device))
 
+    @staticmethod
+    def placed(m, placement: str, dtype=None, device="cuda") -> "Csr":
+        """An ``inputs.Csr`` in device, pinned host or managed memory (see
+        placed_tensor); every device call takes it as it is."""
+        val = m.val if dtype is None else m.val.astype(dtype)
+        return Csr(m.nrows, m.ncols, *(placed_tensor(x, placement, device) for x in (m.row_ptr, m.col, val)))
+
     def dtype_code(self) -> int:
         torch = _torch()
         if self.val.dtype == torch.float64:
@@ -164,6 +185,64 @@ class Csr:
         if self.val.dtype == torch.float32:
             return F32
         raise TypeError(f"unsupported value dtype {self.val.dtype}")
+
+
+class ManagedBuffer:
+    """Managed (UVM) memory from spgemm_managed_alloc, freed with the object;
+    exposes __cuda_array_interface__ so torch can view it without a copy."""
+
+    def __init__(self, nbytes: int, typestr: str, count: int):
+        lib = load()
+        self.ptr = C.c_void_p()
+        _check(lib.spgemm_managed_alloc(max(nbytes, 1), C.byref(self.ptr)))
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
+                                         "data": (self.ptr.value or 0, False), "version": 3}
+
+    def __del__(self):
+        if _lib is not None and self.ptr:
+            _lib.spgemm_managed_free(self.ptr)
+            self.ptr = C.c_void_p()
+
+
+def placed_tensor(x, placement: str, device="cuda"):
+    """A copy of numpy array x in device memory ("device"), pinned host
+    memory ("pinned": the device reads and writes it in place) or managed
+    memory ("managed": written here by the host, so its pages start on the
+    host and migrate when the device touches them)."""
+    torch = _torch()
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if placement == "device":
+        return t.to(device)
+    if placement == "pinned":
+        return t.pin_memory()
+    if placement == "managed":
+        buf = ManagedBuffer(t.numel() * t.element_size(), t.numpy().dtype.str, t.numel())
+        if t.numel():
+            C.memmove(buf.ptr.value, t.data_ptr(), t.numel() * t.element_size())
+        out = torch.as_tensor(buf, device=device)
+        out._managed_owner = buf   # keep the allocation alive with the view
+        return out
+    raise ValueError(f"unknown placement {placement!r}")
+
+
+def placed_empty(n: int, dtype, placement: str, device="cuda"):
+    """An uninitialised tensor of n elements with the given placement."""
+    torch = _torch()
+    if placement == "device":
+        return torch.empty(n, dtype=dtype, device=device)
+    if placement == "pinned":
+        return torch.empty(n, dtype=dtype).pin_memory()
+    if placement == "managed":
+        z = np.empty(n, dtype={torch.int64: np.int64, torch.int32: np.int32, torch.float64: np.float64,
+                               torch.float32: np.float32}[dtype])
+        return placed_tensor(z, "managed", device)
+    raise ValueError(f"unknown placement {placement!r}")
+
+
+def _empty_like_placed(t):
+    """An uninitialised tensor like t in t's placement (pinned stays pinned)."""
+    torch = _torch()
+    return torch.empty_like(t).pin_memory() if t.device.type == "cpu" else torch.empty_like(t)
 
 
 @dataclass
@@ -212,44 +291,53 @@ class Handle:
         return self._h
 
     # -- two phases -----------------------------------------------------------
-    def symbolic(self, A: Csr, B: Csr, stream=None):
-        """Row offsets of C = A*B (device int64 tensor) and nnz(C)."""
+    def symbolic(self, A: Csr, B: Csr, stream=None, placement: str = "device", out=None):
+        """Row offsets of C = A*B (int64 tensor in the given placement, or
+        written into `out`, A.nrows + 1 int64 in any placement) and nnz(C)."""
         torch = _torch()
-        rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.row_ptr.device)
+        if out is not None:
+            if out.dtype != torch.int64 or out.numel() != A.nrows + 1:
+                raise ValueError("out must hold A.nrows + 1 int64 offsets")
+            if out.device.type == "cpu" and not out.is_pinned():
+                raise ValueError("out must be device, managed or pinned host memory")
+            rp = out
+        else:
+            rp = placed_empty(A.nrows + 1, torch.int64, placement, torch.device("cuda", self.device))
         nnz = C.c_int64()
-        da, db = A.desc(), B.desc()
+        da, db = A.dev_desc(), B.dev_desc()
         _check(_lib.spgemm_symbolic(self._h, C.byref(da), C.byref(db), rp.data_ptr(), C.byref(nnz),
                                     _stream(stream)))
         return rp, int(nnz.value)
 
-    def numeric(self, A: Csr, B: Csr, row_ptr, nnz: int, stream=None) -> Csr:
-        """Columns (ascending per row) and values of C = A*B."""
+    def numeric(self, A: Csr, B: Csr, row_ptr, nnz: int, stream=None, placement: str = "device") -> Csr:
+        """Columns (ascending per row) and values of C = A*B (in the given placement)."""
         torch = _torch()
-        dev = A.row_ptr.device
-        col = torch.empty(nnz, dtype=torch.int32, device=dev)
-        val = torch.empty(nnz, dtype=A.val.dtype, device=dev)
+        dev = torch.device("cuda", self.device)
+        col = placed_empty(nnz, torch.int32, placement, dev)
+        val = placed_empty(nnz, A.val.dtype, placement, dev)
         c = Csr(A.nrows, B.ncols, row_ptr, col, val)
         self.numeric_into(A, B, c, stream)
         return c
 
     def numeric_into(self, A: Csr, B: Csr, Cm: Csr, stream=None):
-        da, db, dc = A.desc(), B.desc(), Cm.desc()
+        da, db, dc = A.dev_desc(), B.dev_desc(), Cm.dev_desc()
         _check(_lib.spgemm_numeric(self._h, A.dtype_code(), C.byref(da), C.byref(db), C.byref(dc),
                                    _stream(stream)))
 
-    def spgemm(self, A: Csr, B: Csr, stream=None) -> Csr:
-        rp, nnz = self.symbolic(A, B, stream)
-        return self.numeric(A, B, rp, nnz, stream)
+    def spgemm(self, A: Csr, B: Csr, stream=None, placement: str = "device") -> Csr:
+        """C = A*B; C in the given placement ("device", "pinned", "managed")."""
+        rp, nnz = self.symbolic(A, B, stream, placement)
+        return self.numeric(A, B, rp, nnz, stream, placement)
 
     def backward(self, A: Csr, B: Csr, Cm: Csr, dC, need_a: bool = True, need_b: bool = True,
                  stream=None):
         """(dA values on pattern(A), dB values on pattern(B)) for dC given on
         the pattern of C = A*B."""
         torch = _torch()
-        da = torch.empty_like(A.val) if need_a else None
-        db = torch.empty_like(B.val) if need_b else None
+        da = _empty_like_placed(A.val) if need_a else None
+        db = _empty_like_placed(B.val) if need_b else None
         dcm = Csr(Cm.nrows, Cm.ncols, Cm.row_ptr, Cm.col, dC.contiguous())
-        d1, d2, d3 = A.desc(), B.desc(), dcm.desc()
+        d1, d2, d3 = A.dev_desc(), B.dev_desc(), dcm.dev_desc()
         _check(_lib.spgemm_backward(self._h, A.dtype_code(), C.byref(d1), C.byref(d2), C.byref(d3),
                                     da.data_ptr() if da is not None else None,
                                     db.data_ptr() if db is not None else None, _stream(stream)))
@@ -271,7 +359,7 @@ class Handle:
     def row_flops(self, A: Csr, B: Csr, stream=None):
         torch = _torch()
         out = torch.empty(A.nrows, dtype=torch.int64, device=A.row_ptr.device)
-        da, db = A.desc(), B.desc()
+        da, db = A.dev_desc(), B.dev_desc()
         _check(_lib.spgemm_row_flops(self._h, C.byref(da), C.byref(db), out.data_ptr(), _stream(stream)))
         return out
 
@@ -281,7 +369,7 @@ class Handle:
         dev = M.row_ptr.device
         cnt = torch.empty(M.nrows, dtype=torch.int32, device=dev)
         pairs = torch.zeros((max(M.nnz, 1), 2), dtype=torch.int32, device=dev)
-        dm = M.desc()
+        dm = M.dev_desc()
         _check(_lib.spgemm_compress(self._h, C.byref(dm), cnt.data_ptr(), pairs.data_ptr(),
                                     _stream(stream)))
         return cnt, pairs
@@ -394,7 +482,7 @@ class Handle:
         if labels:
             perm = torch.empty(G.nrows, dtype=torch.int64, device=G.row_ptr.device)
             vc = torch.empty(G.nrows, dtype=torch.int64, device=G.row_ptr.device)
-        d = G.desc()
+        d = G.dev_desc()
         _check(_lib.spgemm_triangles(self._h, C.byref(d), C.byref(total), perm.data_ptr() if labels else None,
                                      vc.data_ptr() if labels else None, _stream(stream)))
         return (int(total.value), perm, vc) if labels else int(total.value)
@@ -539,8 +627,8 @@ class Batch:
         self._arrays()
 
     def _arrays(self):
-        self.da = (CsrDesc * max(self.n, 1))(*[a.desc() for a in self.As])
-        self.db = (CsrDesc * max(self.n, 1))(*[b.desc() for b in self.Bs])
+        self.da = (CsrDesc * max(self.n, 1))(*[a.dev_desc() for a in self.As])
+        self.db = (CsrDesc * max(self.n, 1))(*[b.dev_desc() for b in self.Bs])
 
     @property
     def rows(self):
@@ -566,7 +654,7 @@ class Batch:
 
     def numeric_into(self, Cm: Csr, stream=None):
         self._arrays()
-        dc = Cm.desc()
+        dc = Cm.dev_desc()
         _check(_lib.spgemm_batched_numeric(self.h.ptr, self.As[0].dtype_code(), self.n, self.da, self.db,
                                            C.byref(dc), _stream(stream)))
 
@@ -595,7 +683,7 @@ class Batch:
         da = torch.empty(na, dtype=dC.dtype, device=dev) if need_a else None
         db = torch.empty(nb, dtype=dC.dtype, device=dev) if need_b else None
         dcm = Csr(Cm.nrows, Cm.ncols, Cm.row_ptr, Cm.col, dC.contiguous())
-        d = dcm.desc()
+        d = dcm.dev_desc()
         _check(_lib.spgemm_batched_backward(self.h.ptr, self.As[0].dtype_code(), C.byref(d),
                                             da.data_ptr() if da is not None else None,
                                             db.data_ptr() if db is not None else None, _stream(stream)))

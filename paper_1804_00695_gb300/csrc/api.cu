@@ -716,6 +716,23 @@ int spgemm_triangles(spgemm_handle h, const spgemm_csr *A, int64_t *total, int64
     return SPGEMM_OK;
 }
 
+int spgemm_managed_alloc(size_t bytes, void **ptr) {
+    if (!ptr) { set_error("NULL ptr"); return SPGEMM_ERR_ARG; }
+    *ptr = nullptr;
+    cudaError_t e = cudaMallocManaged(ptr, bytes > 0 ? bytes : 1, cudaMemAttachGlobal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocManaged of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return SPGEMM_ERR_NOMEM;
+    }
+    return SPGEMM_OK;
+}
+
+int spgemm_managed_free(void *ptr) {
+    if (ptr) SG_CUDA(cudaFree(ptr));
+    return SPGEMM_OK;
+}
+
 int spgemm_chunked_stats(spgemm_handle h, spgemm_chunk_stats *out) {
     if (!h || !out) { set_error("NULL handle or output"); return SPGEMM_ERR_ARG; }
     const ChunkStats &x = h->cstats;
