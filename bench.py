@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (profiling cases)")
     ap.add_argument("--batch-max", type=int, default=65536, help="largest instance order of the batched workload")
     ap.add_argument("--workload", default="galerkin128",
-                    choices=["galerkin128", "rmat20", "triangles20", "chunked256", "batched256"])
+                    choices=["galerkin128", "rmat20", "triangles20", "chunked256", "batched256", "weak27",
+                             "budget256"])
     ap.add_argument("--no-secondary", action="store_true",
                     help="default line without the R-MAT, chunked and batched workloads")
     return ap.parse_args()
@@ -261,6 +262,7 @@ def main():
         gen = bench_workloads.Inputs(args)
         gen.rmat_graph()
         gen.batch_pairs()
+        gen.families()
 
     import torch
     import paper_1804_00695_gb300 as sg
@@ -424,6 +426,8 @@ def main():
                          ("triangles20", lambda: bench_workloads.measure_triangles(args, gen.rmat_graph(), local)),
                          ("chunked256", lambda: bench_workloads.measure_chunked(args, local)),
                          ("placement128", lambda: bench_workloads.measure_placement(args, (a, p, r), local)),
+                         ("families", lambda: bench_workloads.measure_families(
+                             args, {**gen.families(), "brick3d_27pt": (a, p, r)}, local)),
                          ("batched256", lambda: bench_workloads.measure_batched(args, gen.batch_pairs(), local))):
             t0 = time.perf_counter()
             try:

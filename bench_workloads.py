@@ -9,6 +9,11 @@ one of them as a full line.
                result in pinned host memory, 4 GB device budget (Section 3.3.1).
 * placement128 - the Galerkin products with A, B, C each in HBM, pinned host
                or managed memory (the placements of Table 3).
+* families   - R*A and A*P of the 7-point, 13-point, 27-point and elasticity
+               multigrid families (Section 4's input families).
+* weak27     - (own line only) R*A and A*P of the 27-point family with A of
+               about 1, 2, 4 and 8 GB.
+* budget256  - (own line only) the chunked workload at device budgets 2-32 GB.
 * batched256 - 256 products A_i*B_i, rows log-uniform in [1024, 65536], 4-32
                random columns per row, FP32: batched forward and backward
                against a per-instance loop on the same GPU.
@@ -52,16 +57,29 @@ def _gen_pair(n, s):
     return I.random_square(n, 2 * s, dtype=np.float32), I.random_square(n, 2 * s + 1, dtype=np.float32)
 
 
+def _gen_family(name, n):
+    from paper_1804_00695_gb300 import inputs as I
+    return I.family_problem(name, n)
+
+
+# the multigrid families at about 0.6-0.75 GB of A each (the 27-point one is
+# the default workload's problem)
+FAMILY_SIZES = {"laplace3d_7pt": 200, "bigstar2d_13pt": 2000, "elasticity3d_81": 64}
+# 27-point A of about 1, 2, 4 and 8 GB (324 bytes per interior row)
+WEAK_SIZES = (146, 184, 231, 291)
+
+
 class Inputs:
     """The secondary workloads' inputs, generated in worker processes (spawn)
-    while the caller measures: the R-MAT graph and the batch instances
+    while the caller measures: the R-MAT graph, the batch instances
     (instance i: n_i from the log-uniform sizes, seeds 2(1+i), 2(1+i)+1, as
-    inputs.random_batch)."""
+    inputs.random_batch) and the multigrid families."""
 
-    def __init__(self, args, workers=None):
+    def __init__(self, args, workers=None, families=True):
         from paper_1804_00695_gb300 import inputs as I
         workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
         self.pool = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+        self.fam = {k: self.pool.submit(_gen_family, k, n) for k, n in FAMILY_SIZES.items()} if families else {}
         self.rmat = self.pool.submit(_gen_rmat, args.rmat_scale)
         sizes = I.batch_sizes(args.batch_count, 1024, args.batch_max, 1)
         self.batch = [self.pool.submit(_gen_pair, n, 1 + i) for i, n in enumerate(sizes)]
@@ -71,6 +89,9 @@ class Inputs:
 
     def batch_pairs(self):
         return [f.result() for f in self.batch]
+
+    def families(self):
+        return {k: f.result() for k, f in self.fam.items()}
 
     def close(self):
         self.pool.shutdown(wait=False, cancel_futures=True)
@@ -111,17 +132,17 @@ def _row_block(fl, target_mults, start):
     return start, min(end, len(fl))
 
 
-def _oracle_rows_sample(a, b, fl, start, tol_tag, device_rows, label):
-    """CPU baseline leg: the oracle on a block of rows of about CPU_SAMPLE_S
+def _oracle_rows_sample(a, b, fl, start, tol_tag, device_rows, label, seconds=CPU_SAMPLE_S, probe_mults=2e8):
+    """CPU baseline leg: the oracle on a block of rows of about `seconds`
     seconds (grown from a small probe), timed on all host cores; its output
     is compared with the device rows (device_rows(r0, r1) -> rp, col, val)."""
     import oracle
-    r0, r1 = _row_block(fl, 2e8, start)
+    r0, r1 = _row_block(fl, probe_mults, start)
     t0 = time.perf_counter()
     oracle.spgemm(a, b, r0, r1)
     probe = max(time.perf_counter() - t0, 1e-3)
     rate = max(int(fl[r0:r1].sum()), 1) / probe
-    r0, r1 = _row_block(fl, rate * CPU_SAMPLE_S, start)
+    r0, r1 = _row_block(fl, rate * seconds, start)
     t0 = time.perf_counter()
     ref = oracle.spgemm(a, b, r0, r1)
     dt = time.perf_counter() - t0
@@ -500,6 +521,134 @@ def measure_batched(args, pairs, local):
                        "backward_instance": i0, "backward_in_tolerance": bwd_ok}}
 
 
+# ---------------------------------------------------------------- multigrid families
+def _time_product(h, X, Y, warm, steps, stream):
+    """Median ms of symbolic + numeric (C allocated by the caching allocator
+    as in the default step), CUDA events on the launching stream."""
+    import torch
+    ms = []
+    for it in range(warm + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c = h.spgemm(X, Y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        del c
+    return statistics.median(ms[warm:])
+
+
+def _product_entry(h, x, y, label, local, warm=2, steps=3, cpu_seconds=1.0):
+    """One product of a family: GFLOP/s, % of the HBM-byte roofline of the
+    whole product (symbolic + numeric bytes), an oracle CPU baseline on a
+    block of rows and the parity of that block."""
+    import torch
+    import paper_1804_00695_gb300 as sg
+    X, Y = sg.Csr.from_host(x, "cuda"), sg.Csr.from_host(y, "cuda")
+    stream = torch.cuda.current_stream()
+    c = h.spgemm(X, Y)
+    h.check()
+    crp = c.row_ptr.cpu().numpy()
+
+    def rows(r0, r1):
+        p0, p1 = int(crp[r0]), int(crp[r1])
+        return crp[r0:r1 + 1].copy(), c.col[p0:p1].cpu().numpy(), c.val[p0:p1].cpu().numpy()
+
+    fl = _row_flops(x, y)
+    cpu, par = _oracle_rows_sample(x, y, fl, x.nrows // 2, "f64", rows, label, seconds=cpu_seconds,
+                                   probe_mults=2e7)
+    nnz = c.nnz
+    del c
+    ms = _time_product(h, X, Y, warm, steps, stream)
+    mults = int(fl.sum())
+    allrows = np.ones(x.nrows, dtype=bool)
+    byt = (bench.kernel_bytes(x, y.row_ptr, crp, allrows, 8, True)
+           + bench.kernel_bytes(x, y.row_ptr, crp, allrows, 8, False))
+    hbm, src = _hbm_peak()
+    del X, Y
+    torch.cuda.empty_cache()
+    return {"ms": ms, "gflops": 2 * mults / (ms / 1e3) / 1e9, "mults": mults, "nnz_C": nnz,
+            "rows": x.nrows, "pct_hbm_byte_roofline": 100 * byt / (ms / 1e3) / 1e9 / hbm,
+            "algorithmic_bytes": byt, "peak_source": src, "cpu_baseline": cpu, "parity": par}
+
+
+def measure_families(args, problems, local):
+    """R*A and A*P of every multigrid family (Section 4's input families),
+    reported separately as in the paper; problems: name -> (A, P, R)."""
+    import paper_1804_00695_gb300 as sg
+    h = sg.Handle(local)
+    clocks = bench.ClockSampler(local)
+    clocks.start()
+    out = {}
+    for name, (a, p, r) in problems.items():
+        n = FAMILY_SIZES.get(name, args.grid)
+        out[name] = {"grid": n, "A_rows": a.nrows, "A_nnz": a.nnz, "A_gb": (8 * (a.nrows + 1) + 12 * a.nnz) / 1e9,
+                     "P_nnz": p.nnz,
+                     "R*A": _product_entry(h, r, a, f"{name} R*A", local),
+                     "A*P": _product_entry(h, a, p, f"{name} A*P", local)}
+    clk = clocks.stop()
+    ok = all(v[k]["parity"]["pattern_exact"] and v[k]["parity"]["values_in_tolerance"]
+             for v in out.values() for k in ("R*A", "A*P"))
+    return {"config": {"workload": "R*A and A*P of the multigrid families: 7-point 3D Laplacian, 13-point 2D "
+                                   "biharmonic star, 27-point 3D brick, 3D elasticity (81 per row); smoothed "
+                                   "aggregation P (3 points per dimension, omega 2/3), FP64",
+                       "steps": 3, "warmup": 2},
+            "families": out, "clocks": clk, "parity": {"all_rows_sampled_match": ok}}
+
+
+def measure_weak(args, local):
+    """Throughput against problem size (the paper's growing problems): R*A
+    and A*P of the 27-point family with A of about 1, 2, 4 and 8 GB, inputs
+    generated in worker processes."""
+    import paper_1804_00695_gb300 as sg
+    workers = max(1, min(len(WEAK_SIZES), (os.cpu_count() or 2) - 1))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as pool:
+        futs = {n: pool.submit(_gen_family, "brick3d_27pt", n) for n in WEAK_SIZES}
+        h = sg.Handle(local)
+        clocks = bench.ClockSampler(local)
+        rows = {}
+        for n in WEAK_SIZES:
+            a, p, r = futs.pop(n).result()
+            clocks.start()
+            rows[str(n)] = {"A_gb": (8 * (a.nrows + 1) + 12 * a.nnz) / 1e9, "A_rows": a.nrows,
+                            "R*A": _product_entry(h, r, a, f"27-point {n}^3 R*A", local, cpu_seconds=0.5),
+                            "A*P": _product_entry(h, a, p, f"27-point {n}^3 A*P", local, cpu_seconds=0.5)}
+            rows[str(n)]["clocks"] = clocks.stop()
+            del a, p, r
+    last = rows[str(WEAK_SIZES[-1])]
+    return {"metric_value": last["A*P"]["gflops"], "unit": "GFLOP/s", "ms_per_step": last["A*P"]["ms"],
+            "steps": 3, "warmup": 2, "dtype": "f64",
+            "config": {"workload": "27-point 3D brick family, smoothed aggregation P, FP64: R*A and A*P with A of "
+                                   "about 1, 2, 4 and 8 GB (value: A*P at the largest)", "grids": list(WEAK_SIZES)},
+            "sizes": rows,
+            "parity": {"all_rows_sampled_match": all(v[k]["parity"]["pattern_exact"] and
+                                                     v[k]["parity"]["values_in_tolerance"]
+                                                     for v in rows.values() for k in ("R*A", "A*P"))}}
+
+
+def measure_budget(args, local):
+    """Device-budget sweep of the chunked product (the paper's Chunk8 /
+    Chunk16 runs, Section 4): the chunked workload at several budgets."""
+    from paper_1804_00695_gb300 import inputs as I
+    a = I.laplace3d_27pt(args.chunk_grid)
+    runs = {}
+    for b in (2e9, 4e9, 8e9, 16e9, 32e9):
+        args.budget = b
+        r = measure_chunked(args, local, a)
+        runs[f"{b / 1e9:g}GB"] = {"gflops": r["metric_value"], "ms": r["ms_per_step"],
+                                  "symbolic_ms": r["symbolic_ms"], "link_frac": r["roofline"]["frac"],
+                                  "bytes_copied_over_minimal": r["bytes_copied_over_minimal"],
+                                  "numeric_plan": r["numeric_plan"], "clocks": r["clocks"], "parity": r["parity"]}
+    best = max(runs.values(), key=lambda v: v["gflops"])
+    return {"metric_value": runs["4GB"]["gflops"], "unit": "GFLOP/s", "ms_per_step": runs["4GB"]["ms"],
+            "steps": 2, "warmup": 1, "dtype": "f64",
+            "config": {"workload": f"chunked C = A*A, 27-point 3D Laplacian on {args.chunk_grid}^3, FP64, "
+                                   "operands and C in pinned host memory, device budgets 2-32 GB (value: 4 GB)"},
+            "budgets": runs, "best_gflops": best["gflops"],
+            "parity": {"all_rows_sampled_match": all(v["parity"]["values_in_tolerance"] for v in runs.values())}}
+
+
 # ---------------------------------------------------------------- placements
 PLACEMENTS = (("HBM", "device", "device", "device"), ("A_Pin", "pinned", "device", "device"),
               ("B_Pin", "device", "pinned", "device"), ("C_Pin", "device", "device", "pinned"),
@@ -584,6 +733,10 @@ def run(args, rank, world, local):
         r = measure_triangles(args, I.rmat_symmetric(args.rmat_scale, 16, seed=1), local)
     elif args.workload == "chunked256":
         r = measure_chunked(args, local)
+    elif args.workload == "weak27":
+        r = measure_weak(args, local)
+    elif args.workload == "budget256":
+        r = measure_budget(args, local)
     else:
         r = measure_batched(args, I.random_batch(args.batch_count, 1024, args.batch_max, 1, dtype=np.float32),
                             local)

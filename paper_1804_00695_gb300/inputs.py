@@ -18,6 +18,12 @@ Workloads (stand-ins for the paper's multigrid and graph matrices, Section
   Because A = 27 I - T(x)T(x)T with T the tridiagonal all-ones matrix, and
   D = 26 I, P = (4/13) P_tent + (1/39) (Tp)(x)(Tp)(x)(Tp), so every entry is
   written directly from one-dimensional factors.  The restriction is R = P^T.
+* ``stencil_matrix(name, n)``, ``smoothed_prolongator(name, n)``,
+  ``family_problem(name, n)``: the multigrid families of Section 4 - 7-point
+  3D Laplacian, 13-point 2D biharmonic star ("BigStar2D"), 27-point 3D
+  brick, and 3D elasticity (27-point stencil Kronecker a 3x3 SPD block, 81
+  entries per row) - with smoothed-aggregation prolongators (aggregates of 3
+  points per dimension, omega 2/3) written per stencil offset.
 * ``rmat_symmetric(scale, edge_factor, abcd, seed)``: R-MAT graph with a
   counter-based generator (SplitMix64 finaliser over a counter), self-loops
   dropped, symmetrised, duplicates removed, values 1.0 (float32).
@@ -203,6 +209,178 @@ def galerkin_problem(n: int):
     """(A, P, R) of the Galerkin triple product R*(A*P) on an n^3 grid."""
     a = laplace3d_27pt(n)
     p = galerkin_prolongator(n)
+    return a, p, transpose(p)
+
+
+# ---------------------------------------------------------------- multigrid families
+# Stencil operators on a lexicographic grid (i = x0 + n0*(x1 + n1*x2), x0
+# fastest), boundary rows truncated, and their smoothed-aggregation
+# prolongators P = (I - omega D^-1 A) P_tent with aggregates of 3 points per
+# dimension (agg(x) = x // 3 in each dimension, coarse points ordered the same
+# way).  Block operators (several unknowns per grid point) are the scalar
+# stencil Kronecker a small dense block K, unknown fastest; their P_tent is
+# the scalar one Kronecker the identity of K's order.
+
+def _offsets(d: int, reach: int):
+    """All offsets of a d-dimensional box of half-width reach, as a (k, d) array."""
+    r = np.arange(-reach, reach + 1)
+    g = np.stack(np.meshgrid(*([r] * d), indexing="ij"), axis=-1).reshape(-1, d)
+    return g[:, ::-1].copy()   # column 0 is x0
+
+
+STENCILS = {
+    # name: (dimension, offsets, weights); weights of the 7-point and 27-point
+    # Laplacians (diagonal = number of neighbours, neighbours -1) and of the
+    # 13-point biharmonic star (20 at the centre, -8 at the 4 nearest, 2 at the
+    # 4 diagonal, 1 at the 4 second-nearest points)
+    "laplace3d_7pt": (3, np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]]),
+                      np.array([6.0, -1, -1, -1, -1, -1, -1])),
+    "bigstar2d_13pt": (2, np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0, -1], [1, 1], [1, -1], [-1, 1], [-1, -1],
+                                    [2, 0], [-2, 0], [0, 2], [0, -2]]),
+                       np.array([20.0, -8, -8, -8, -8, 2, 2, 2, 2, 1, 1, 1, 1])),
+    "brick3d_27pt": (3, _offsets(3, 1), None),
+}
+# 3 unknowns per point (displacements), coupled by an SPD block
+ELASTICITY_BLOCK = np.array([[3.0, 1.0, 1.0], [1.0, 3.0, 1.0], [1.0, 1.0, 3.0]])
+
+
+def _stencil_weights(name: str):
+    d, off, w = STENCILS[name]
+    if w is None:   # 27-point: 26 at the centre, -1 elsewhere
+        w = np.where(np.all(off == 0, axis=1), 26.0, -1.0)
+    return d, off, w
+
+
+def _stencil_block(dims, off, r0: int, r1: int):
+    """Offsets sorted by linear displacement (so that columns ascend within a
+    row), their displacements, the grid coordinates of rows [r0, r1) and the
+    (rows x offsets) mask of in-grid neighbours."""
+    dims = np.asarray(dims, dtype=np.int64)
+    stride = np.concatenate([[1], np.cumprod(dims)[:-1]])
+    lin = off @ stride
+    order = np.argsort(lin, kind="stable")
+    rows = np.arange(r0, r1, dtype=np.int64)
+    x = [(rows // stride[k]) % dims[k] for k in range(len(dims))]
+    ok = np.ones((r1 - r0, len(off)), dtype=bool)
+    for k in range(len(dims)):
+        xx = x[k][:, None] + off[order][None, :, k]
+        ok &= (xx >= 0) & (xx < dims[k])
+    return order, lin[order], rows, x, ok
+
+
+def _grid_csr(n, rows, cols, vals, ncols, r0=0):
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows - r0, minlength=n), out=rp[1:])
+    return Csr(n, ncols, rp, cols.astype(np.int32), vals)
+
+
+def _block_kron(m: Csr, block: np.ndarray, zero_drop: bool = False, extra=None):
+    """m Kronecker a dense block (unknown fastest); with extra = (m2_val,
+    block2) the result's values are m.val*block + m2_val*block2 on the same
+    pattern; zero_drop removes entries that are exactly 0."""
+    b = block.shape[0]
+    bc = Csr(b, b, np.arange(0, b * b + 1, b, dtype=np.int64), np.tile(np.arange(b, dtype=np.int32), b),
+             block.reshape(-1).astype(np.float64))
+    if extra is None:
+        out = kron_lex(m, bc)
+    else:
+        out, ex = kron_lex(m, bc, (extra[0],), (extra[1].reshape(-1).astype(np.float64),))
+        out = Csr(out.nrows, out.ncols, out.row_ptr, out.col, out.val + ex[0])
+    if zero_drop:
+        keep = out.val != 0.0
+        rows = np.repeat(np.arange(out.nrows, dtype=np.int64), np.diff(out.row_ptr))[keep]
+        out = _grid_csr(out.nrows, rows, out.col[keep], out.val[keep], out.ncols)
+    return out
+
+
+_ROW_BLOCK = 1 << 20   # rows generated at a time (bounds the temporaries)
+
+
+def stencil_matrix(name: str, n: int) -> Csr:
+    """Operator of a family on an n^d grid: "laplace3d_7pt", "bigstar2d_13pt",
+    "brick3d_27pt" or "elasticity3d_81" (the 27-point stencil Kronecker
+    ELASTICITY_BLOCK: 81 entries per interior row)."""
+    base = "brick3d_27pt" if name == "elasticity3d_81" else name
+    d, off, w = _stencil_weights(base)
+    dims, N = [n] * d, n ** d
+    lens, cols, vals = [], [], []
+    for r0 in range(0, N, _ROW_BLOCK):
+        r1 = min(N, r0 + _ROW_BLOCK)
+        order, lin, rows, _, ok = _stencil_block(dims, off, r0, r1)
+        lens.append(ok.sum(axis=1))
+        cols.append((rows[:, None] + lin[None, :])[ok].astype(np.int32))
+        vals.append(np.broadcast_to(w[order][None, :], ok.shape)[ok])
+    rp = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.concatenate(lens), out=rp[1:])
+    m = Csr(N, N, rp, np.concatenate(cols), np.concatenate(vals))
+    return _block_kron(m, ELASTICITY_BLOCK) if name == "elasticity3d_81" else m
+
+
+def smoothed_prolongator(name: str, n: int, omega: float = 2.0 / 3.0) -> Csr:
+    """P = (I - omega D^-1 A) P_tent of a family (aggregates of 3 points per
+    dimension), written per stencil offset: row i takes, for every in-grid
+    offset o, [o = 0] - omega w_o / d at column agg(i + o) (d the diagonal),
+    duplicates of a column summed and exact zeros dropped.  For the block
+    family: P_tent Kronecker I - (omega / d) (A_scalar P_tent) Kronecker K
+    with d = 26 * K's diagonal."""
+    base = "brick3d_27pt" if name == "elasticity3d_81" else name
+    dd, off, w = _stencil_weights(base)
+    dims = [n] * dd
+    nc = (n + 2) // 3
+    N, NC = n ** dd, nc ** dd
+    diag = float(w[np.all(off == 0, axis=1)][0])
+    block = name == "elasticity3d_81"
+    scale = omega / (diag * ELASTICITY_BLOCK[0, 0]) if block else omega / diag
+    # the aggregates a row reaches lie within one of its own in every
+    # dimension (stencil reach <= 2 < 3 + 1): slot = sum_k (agg_k(col) -
+    # agg_k(row) + 1) 3^k indexes a dense accumulator of 3^d slots per row,
+    # and ascending slots are ascending coarse columns.  agg_k(col) -
+    # agg_k(row) = (x_k mod 3 + o_k) // 3 depends on x_k mod 3 and o_k only.
+    S = 3 ** dd
+    slot_col = np.zeros(S, dtype=np.int64)
+    for k in range(dd):
+        slot_col += ((np.arange(S) // 3 ** k) % 3) * nc ** k
+    lens, cols, es, qs = [], [], [], []
+    for r0 in range(0, N, _ROW_BLOCK):
+        r1 = min(N, r0 + _ROW_BLOCK)
+        order, _, rows, x, ok = _stencil_block(dims, off, r0, r1)
+        o = off[order]
+        slot = np.zeros(ok.shape, dtype=np.int64)
+        base_col = np.zeros(r1 - r0, dtype=np.int64)
+        for k in range(dd):
+            slot += ((x[k] % 3)[:, None] + o[None, :, k]) // 3 * 3 ** k + 3 ** k
+            base_col += (x[k] // 3 - 1) * nc ** k
+        key = (np.arange(r1 - r0, dtype=np.int64)[:, None] * S + slot)[ok]
+        size = (r1 - r0) * S
+        wo = np.broadcast_to(w[order][None, :], ok.shape)[ok]
+        centre = np.broadcast_to(np.all(o == 0, axis=1)[None, :], ok.shape)[ok].astype(np.float64)
+        used = np.bincount(key, minlength=size) > 0
+        e = np.bincount(key, weights=centre, minlength=size)[used]    # P_tent part
+        q = np.bincount(key, weights=wo, minlength=size)[used]        # (A P_tent) part
+        idx = np.nonzero(used)[0]
+        urow, sl = idx // S, idx % S
+        ucol = (base_col[urow] + slot_col[sl]).astype(np.int32)
+        if not block:
+            val = e - scale * q
+            keep = val != 0.0
+            urow, ucol, e, q = urow[keep], ucol[keep], val[keep], None
+        lens.append(np.bincount(urow, minlength=r1 - r0))
+        cols.append(ucol)
+        es.append(e)
+        qs.append(q)
+    rp = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.concatenate(lens), out=rp[1:])
+    s = Csr(N, NC, rp, np.concatenate(cols), np.concatenate(es))
+    if not block:
+        return s
+    kb = ELASTICITY_BLOCK
+    return _block_kron(s, np.eye(kb.shape[0]), zero_drop=True, extra=(-scale * np.concatenate(qs), kb))
+
+
+def family_problem(name: str, n: int):
+    """(A, P, R = P^T) of a multigrid family on an n^d grid."""
+    a = stencil_matrix(name, n)
+    p = smoothed_prolongator(name, n)
     return a, p, transpose(p)
 
 
