@@ -140,6 +140,29 @@ __device__ __forceinline__ void dw_atomic_acc(float2 *v2, float *v3, int slot, f
     atomicAdd(&v3[slot], __fadd_rn(e2, f));
 }
 
+// vals[slot] += v for every lane with `valid`, where vals is private to the
+// warp.  Lanes that hit the same slot first sum their values in lane order
+// (one __match_any_sync, then as many shuffles as the largest group has
+// members), so that one lane per slot writes and the write is a plain
+// load-add-store: no atomic, and no retries when several products of one
+// step meet in one slot.  Called by all 32 lanes.
+__device__ __forceinline__ void warp_acc_f64(double *vals, int slot, bool valid, double v, int lane) {
+    const unsigned grp = __match_any_sync(0xffffffffu, valid ? slot : -1 - lane);
+    const int leader = __ffs(grp) - 1;
+    const int m = __popc(grp);
+    const int maxm = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+    unsigned rest = grp & (grp - 1);   // members after the leader
+    double sum = v;
+    for (int k = 1; k < maxm; k++) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        rest &= rest - 1;
+        const double x = __shfl_sync(0xffffffffu, v, src);
+        if (k < m) sum += x;
+    }
+    if (valid && lane == leader) vals[slot] += sum;
+    __syncwarp();
+}
+
 // Final value of a three-level slot as a double.
 __device__ __forceinline__ double dw3_to_double(float hi, float lo, float lo2) {
     float s, e;
@@ -487,6 +510,85 @@ __device__ __forceinline__ void bitonic(int *k, V *v, int P, int tid, int NT, Sy
     }
 }
 
+// Writes a row's n compacted entries (ck[x], cv[x]) to ccol/cval in
+// ascending column order without sorting the columns: the row's distinct
+// 32-column blocks are gathered in a map (block -> OR of the bit masks, the
+// compression of Section 2.1 applied to the output), only the blocks are
+// sorted, prefix counts of their masks give each block's first rank, and an
+// entry's rank is its block's plus the number of the block's columns below
+// it.  Map of 2^LB slots (bkey, bm, bb: key, mask, first rank), list of at
+// most lcap blocks (lkey, lval: block, its slot).  cnt, fail: two shared
+// ints.  NT threads (tid) take part; sync() orders them.  Returns false,
+// with nothing written, when the blocks do not fit (more than lcap, or a
+// full map): the caller then sorts the columns themselves.
+template <typename Vin, typename Vout, typename Sync>
+__device__ bool write_by_blocks(const int *ck, const Vin *cv, int n, int *bkey, unsigned *bm, int *bb, int LB,
+                                int *lkey, int *lval, int lcap, int *cnt, int *fail, int tid, int NT, Sync sync,
+                                int32_t *ccol, Vout *cval) {
+    const int SB = 1 << LB;
+    for (int u = tid; u < SB; u += NT) {
+        bkey[u] = -1;
+        bm[u] = 0u;
+    }
+    if (tid == 0) {
+        *cnt = 0;
+        *fail = 0;
+    }
+    sync();
+    for (int x = tid; x < n; x += NT) {
+        const int col = ck[x];
+        if (!sym_insert(bkey, bm, LB, col >> 5, 1u << (col & 31))) *fail = 1;
+    }
+    sync();
+    for (int u = tid; u < SB; u += NT) {
+        const int k = bkey[u];
+        if (k >= 0) {
+            const int pos = atomicAdd(cnt, 1);
+            if (pos < lcap) {
+                lkey[pos] = k;
+                lval[pos] = u;
+            }
+        }
+    }
+    sync();
+    const int nb = *cnt;
+    if (*fail || nb > lcap) return false;
+    const int P = next_pow2(nb);
+    for (int k = nb + tid; k < P; k += NT) {
+        lkey[k] = INT_MAX;
+        lval[k] = 0;
+    }
+    sync();
+    bitonic<int>(lkey, lval, P, tid, NT, sync);
+    if (tid < 32) {   // first ranks: exclusive prefix of the masks' counts, in block order
+        int carry = 0;
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            const int k = k0 + tid;
+            const int c = k < nb ? __popc(bm[lval[k]]) : 0;
+            int incl = c;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (tid >= d) incl += y;
+            }
+            if (k < nb) bb[lval[k]] = carry + incl - c;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    sync();
+    const unsigned msk = (unsigned)SB - 1;
+    for (int x = tid; x < n; x += NT) {
+        const int col = ck[x];
+        const int blk = col >> 5;
+        unsigned h = hash_slot(blk, LB);
+        for (int probe = 0; probe < SB && bkey[h] != blk; probe++) h = (h + 1) & msk;
+        const int r = bb[h] + __popc(bm[h] & ((1u << (col & 31)) - 1u));
+        if (bkey[h] != blk || r < 0 || r >= n) continue;   // cannot happen: every block was inserted
+        ccol[r] = col;
+        cval[r] = (Vout)cv[x];
+    }
+    return true;
+}
+
 // Which dense rank accumulator takes a row of bins 3-4 (0: none, the hash
 // maps of k_num_wide do): the smallest whose bitmap covers the row's span
 // of 32-column blocks and whose value array holds its outputs.  Smaller
@@ -761,8 +863,10 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_rank(NumP a, const int4 *__
 // from its prefix count and looks the values up in the map.  Wider rows
 // are compacted and sorted with a bitonic network.
 template <int MODE>
-struct WideSlot {   // bytes per map slot: key + value (+ third level)
-    static constexpr int bytes = MODE == MODE_F32 ? 8 : 16;
+struct WideSlot {   // bytes per map slot: key + value (+ third level); 16 in
+    // every mode, so that the output ordering by blocks (4 ints per slot)
+    // can reuse the map's space
+    static constexpr int bytes = 16;
 };
 
 template <int SMAX, int BW, int WPB, int MODE>
@@ -855,15 +959,18 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             __syncwarp();
             int e = 0;
+            const bool f64 = MODE == MODE_F64 || (MODE == MODE_DW && nat);   // uniform in the warp
             for (int t0 = 0; t0 < total; t0 += 32) {
                 const int tt = t0 + lane;
+                int slot = -1;
+                double pv = 0.0;
                 if (tt < total) {
                     while (pre[e + 1] <= tt) e++;
                     const int64_t q = eq0[e] + (tt - pre[e]);
                     const int col = a.bcol[q];
                     cmin = min(cmin, col);
                     cmax = max(cmax, col);
-                    const int slot = map_slot(keys, L, col);
+                    slot = map_slot(keys, L, col);
                     if (slot < 0) {
                         flag |= DERR_PROBE;
                     } else if (MODE == MODE_F32) {
@@ -873,9 +980,10 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__
                         const float2 a2 = make_float2(__uint_as_float((unsigned)bb), __uint_as_float((unsigned)(bb >> 32)));
                         dw_atomic_acc(v2, v3, slot, dw_mul(a2, a.bsplit[q]));
                     } else {
-                        atomicAdd(&v8[slot], ea[e] * ((const double *)a.bval)[q]);
+                        pv = ea[e] * ((const double *)a.bval)[q];
                     }
                 }
+                if (f64) warp_acc_f64(v8, slot, slot >= 0, pv, lane);
             }
             __syncwarp();
         }
@@ -951,14 +1059,26 @@ __global__ void __launch_bounds__(WPB * 32, 1) k_num_wide(NumP a, const int4 *__
                 flag |= DERR_COUNT;
                 n = min(n, nn);
             }
-            const int P = next_pow2(n);
-            for (int x = n + lane; x < P; x += 32) ck[x] = INT_MAX;
+            // the map's slots are free now: order the output by its blocks
+            using Vout = typename std::conditional<MODE == MODE_F32, float, double>::type;
+            int SB = next_pow2(2 * n);
+            SB = SB < 32 ? 32 : SB;
+            int *tb = (int *)base;
+            const bool done = write_by_blocks<double, Vout>(
+                ck, cv, n, tb, (unsigned *)(tb + SB), tb + 2 * SB, __ffs(SB) - 1, tb + 3 * SB,
+                tb + 3 * SB + SB / 2, SB / 2, ncount, pre, lane, 32, [] { __syncwarp(); }, a.ccol + out,
+                (Vout *)a.cval + out);
             __syncwarp();
-            bitonic<double>(ck, cv, P, lane, 32, [] { __syncwarp(); });
-            for (int x = lane; x < n; x += 32) {
-                a.ccol[out + x] = ck[x];
-                if (MODE == MODE_F32) ((float *)a.cval)[out + x] = (float)cv[x];
-                else ((double *)a.cval)[out + x] = cv[x];
+            if (!done) {
+                const int P = next_pow2(n);
+                for (int x = n + lane; x < P; x += 32) ck[x] = INT_MAX;
+                __syncwarp();
+                bitonic<double>(ck, cv, P, lane, 32, [] { __syncwarp(); });
+                for (int x = lane; x < n; x += 32) {
+                    a.ccol[out + x] = ck[x];
+                    if (MODE == MODE_F32) ((float *)a.cval)[out + x] = (float)cv[x];
+                    else ((double *)a.cval)[out + x] = cv[x];
+                }
             }
         }
         __syncwarp();
@@ -992,6 +1112,11 @@ __device__ __forceinline__ bool map_add(int *keys, V *vals, int L, int limit, in
     return false;
 }
 
+// Slots of the block map that orders a block kernel's output (at most
+// BLOCK_TAB / 2 distinct 32-column blocks per row; rows with more are sorted
+// by columns).
+constexpr int BLOCK_TAB = 2048;
+
 // Bins 4-5: a block per listed row, map of S slots in shared memory; warps
 // take stored a_ik in turn and their lanes walk B_k; atomic accumulation in
 // the value type (FP64 rows accumulate natively).
@@ -1007,7 +1132,8 @@ __global__ void __launch_bounds__(BS) k_num_block(
     V *cv = vals + S;
     int *keys = (int *)(cv + S / 2);
     int *ck = keys + S;
-    __shared__ int nsh;
+    int *btab = ck + S / 2;   // 4 * BLOCK_TAB ints: block map and list
+    __shared__ int nsh, bcnt, bfail;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int flag = 0;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
@@ -1050,13 +1176,23 @@ __global__ void __launch_bounds__(BS) k_num_block(
             flag |= DERR_COUNT;
             n = min(min(n, expect), S / 2);
         }
-        const int P = next_pow2(n);
-        for (int e = n + threadIdx.x; e < P; e += BS) ck[e] = INT_MAX;
+        // order the output by its blocks (a map of BLOCK_TAB slots after the
+        // column map); sort the columns themselves if they span too many
+        const bool done = write_by_blocks<V, V>(ck, cv, n, btab, (unsigned *)(btab + BLOCK_TAB),
+                                                btab + 2 * BLOCK_TAB, __builtin_ctz(BLOCK_TAB),
+                                                btab + 3 * BLOCK_TAB, btab + 3 * BLOCK_TAB + BLOCK_TAB / 2,
+                                                BLOCK_TAB / 2, &bcnt, &bfail, threadIdx.x, BS,
+                                                [] { __syncthreads(); }, ccol + out, cval + out);
         __syncthreads();
-        bitonic<V>(ck, cv, P, threadIdx.x, BS, [] { __syncthreads(); });
-        for (int e = threadIdx.x; e < n; e += BS) {
-            ccol[out + e] = ck[e];
-            cval[out + e] = cv[e];
+        if (!done) {
+            const int P = next_pow2(n);
+            for (int e = n + threadIdx.x; e < P; e += BS) ck[e] = INT_MAX;
+            __syncthreads();
+            bitonic<V>(ck, cv, P, threadIdx.x, BS, [] { __syncthreads(); });
+            for (int e = threadIdx.x; e < n; e += BS) {
+                ccol[out + e] = ck[e];
+                cval[out + e] = cv[e];
+            }
         }
         __syncthreads();
     }
@@ -1445,7 +1581,7 @@ static int run_wide(const NumP &a, const int4 *bdesc, const int2 *spans, const i
 
 template <int BS, int S, typename V>
 static int run_block(const NumP &a, const int32_t *rows, int64_t count, int *err, int b, Ctx &c) {
-    const size_t smem = (size_t)S * (sizeof(V) + 4) * 3 / 2;
+    const size_t smem = (size_t)S * (sizeof(V) + 4) * 3 / 2 + (size_t)BLOCK_TAB * 16;
     SG_TRY(prep(k_num_block<BS, S, V>, smem));
     int64_t blocks = count < (int64_t)c.nsm * 16 ? count : (int64_t)c.nsm * 16;
     c.begin(NUM_LABEL[b], count);
@@ -1542,11 +1678,14 @@ static int run_all(const NumP &a, const spgemm_csr &A, const spgemm_csr &B, cons
                                                                  "numeric.rank1024", c)));
                 SG_TRY((run_rank<RANK_BW3, RANK_NMAX3, 4, MODE>(a, bdesc, sp, r, cnt, 3, st, err,
                                                                  "numeric.rank2048", c)));
+                // the rows left to the maps span more than RANK_BW3 words, so the
+                // maps' own bitmap output (spans up to 32 * BW columns) is kept small
                 if (b <= 3) {
-                    SG_TRY((run_wide<256, 1024, 8, MODE>(a, bdesc, sp, r, cnt, 0, 1, st, err, "numeric.wide3", c)));
+                    SG_TRY((run_wide<256, 64, 8, MODE>(a, bdesc, sp, r, cnt, 0, 1, st, err, "numeric.wide3", c)));
                 } else {
-                    SG_TRY((run_wide<512, 2048, 8, MODE>(a, bdesc, sp, r, cnt, 0, 1, st, err, "numeric.wide4a", c)));
-                    SG_TRY((run_wide<2048, 2048, 4, MODE>(a, bdesc, sp, r, cnt, 257, 1, st, err, "numeric.wide4b", c)));
+                    SG_TRY((run_wide<512, 64, 8, MODE>(a, bdesc, sp, r, cnt, 0, 1, st, err, "numeric.wide4a", c)));
+                    SG_TRY((run_wide<1024, 64, 8, MODE>(a, bdesc, sp, r, cnt, 257, 1, st, err, "numeric.wide4b", c)));
+                    SG_TRY((run_wide<2048, 64, 4, MODE>(a, bdesc, sp, r, cnt, 513, 1, st, err, "numeric.wide4c", c)));
                 }
                 break;
             case 5: SG_TRY((run_block<256, 8192, V>(a, r, cnt, err, b, c))); break;
