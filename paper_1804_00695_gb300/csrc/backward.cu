@@ -6,8 +6,9 @@
 // Both come out of one pass over the same products as the forward product:
 // for each stored a_ik and each stored b_kj, dC_ij is found in row i of C
 // (columns ascending) by binary search; the dA terms of a_ik are summed by
-// the lanes walking B_k, and the dB terms are added atomically into the slot
-// of b_kj (its position in B is the loop index).  No dense intermediate.
+// the lanes walking B_k (a segmented sum across the lanes, one update per
+// a_ik and step), and the dB terms are added atomically into the slot of
+// b_kj (its position in B is the loop index).  No dense intermediate.
 // Rows of C with at most BWD_CAP entries are searched in a copy of their
 // columns in shared memory (a warp per row, products dealt out over the
 // lanes); longer rows are searched in global memory.
@@ -84,22 +85,38 @@ __global__ void __launch_bounds__(BWD_WPB * 32) k_backward_rows(
             int e = 0;
             for (int t0 = 0; t0 < total; t0 += 32) {
                 const int t = t0 + lane;
-                if (t >= total) continue;
-                while (pre[e + 1] <= t) e++;
-                const int64_t q = eq0[e] + (t - pre[e]);
-                const int j = bcol[q];
-                int lo = 0, hi = nc;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cs[mid] < j) lo = mid + 1;
-                    else hi = mid;
+                V term = V(0);
+                const bool live = t < total;
+                if (live) {
+                    while (pre[e + 1] <= t) e++;
+                    const int64_t q = eq0[e] + (t - pre[e]);
+                    const int j = bcol[q];
+                    int lo = 0, hi = nc;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (cs[mid] < j) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    if (lo < nc && cs[lo] == j) {
+                        const V g = dc[c0 + lo];
+                        if (bval) term = g * bval[q];
+                        if (db) atomicAdd(&db[q], ea[e] * g);
+                    } else {
+                        missing = true;
+                    }
                 }
-                if (lo < nc && cs[lo] == j) {
-                    const V g = dc[c0 + lo];
-                    if (bval) atomicAdd(&dacc[e], g * bval[q]);
-                    if (db) atomicAdd(&db[q], ea[e] * g);
-                } else {
-                    missing = true;
+                if (bval) {
+                    // the lanes of one staged a_ik are consecutive: a segmented
+                    // sum over them leaves its dA term in the segment's first
+                    // lane, which alone updates the entry's accumulator
+                    const unsigned grp = __match_any_sync(0xffffffffu, live ? e : -1 - lane);
+                    const int last = 31 - __clz(grp);
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const V y = __shfl_down_sync(0xffffffffu, term, d);
+                        if (lane + d <= last) term += y;
+                    }
+                    if (live && lane == __ffs(grp) - 1) dacc[e] += term;
+                    __syncwarp();
                 }
             }
             __syncwarp();
