@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--batch-max", type=int, default=65536, help="largest instance order of the batched workload")
     ap.add_argument("--workload", default="galerkin128",
                     choices=["galerkin128", "rmat20", "triangles20", "chunked256", "batched256", "weak27",
-                             "budget256"])
+                             "budget256", "density"])
     ap.add_argument("--no-secondary", action="store_true",
                     help="default line without the R-MAT, chunked and batched workloads")
     return ap.parse_args()
@@ -263,6 +263,7 @@ def main():
         gen.rmat_graph()
         gen.batch_pairs()
         gen.families()
+        gen.density()
 
     import torch
     import paper_1804_00695_gb300 as sg
@@ -428,6 +429,7 @@ def main():
                          ("placement128", lambda: bench_workloads.measure_placement(args, (a, p, r), local)),
                          ("families", lambda: bench_workloads.measure_families(
                              args, {**gen.families(), "brick3d_27pt": (a, p, r)}, local)),
+                         ("density", lambda: bench_workloads.measure_density(args, gen.density(), local)),
                          ("batched256", lambda: bench_workloads.measure_batched(args, gen.batch_pairs(), local))):
             t0 = time.perf_counter()
             try:

@@ -11,6 +11,8 @@ one of them as a full line.
                or managed memory (the placements of Table 3).
 * families   - R*A and A*P of the 7-point, 13-point, 27-point and elasticity
                multigrid families (Section 4's input families).
+* density    - Elasticity's R and A times random right-hand sides with
+               delta = 1, 4, 16, 64, 256 entries per row (Table 2).
 * weak27     - (own line only) R*A and A*P of the 27-point family with A of
                about 1, 2, 4 and 8 GB.
 * budget256  - (own line only) the chunked workload at device budgets 4-64 GB.
@@ -62,11 +64,24 @@ def _gen_family(name, n):
     return I.family_problem(name, n)
 
 
+def _gen_density(n, deltas):
+    """Elasticity's A and R on an n^3 grid and a random right-hand side per
+    delta (seed 100 + delta), for the density experiment."""
+    from paper_1804_00695_gb300 import inputs as I
+    a, _, r = I.family_problem("elasticity3d_81", n)
+    return a, r, {d: I.random_rhs(a.ncols, a.ncols, d, seed=100 + d) for d in deltas}
+
+
 # the multigrid families at about 0.6-0.75 GB of A each (the 27-point one is
 # the default workload's problem)
 FAMILY_SIZES = {"laplace3d_7pt": 200, "bigstar2d_13pt": 2000, "elasticity3d_81": 64}
 # 27-point A of about 1, 2, 4 and 8 GB (324 bytes per interior row)
 WEAK_SIZES = (146, 184, 231, 291)
+# density experiment (Table 2): Elasticity on 24^3 (41,472 rows) times random
+# right-hand sides with delta entries per row; at delta = 256 A*RHS has
+# 0.86e9 multiplications and 0.68e9 entries (8 GB in FP64)
+DENSITY_GRID = 24
+DENSITY_DELTAS = (1, 4, 16, 64, 256)
 
 
 class Inputs:
@@ -80,6 +95,7 @@ class Inputs:
         workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
         self.pool = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
         self.fam = {k: self.pool.submit(_gen_family, k, n) for k, n in FAMILY_SIZES.items()} if families else {}
+        self.dens = self.pool.submit(_gen_density, DENSITY_GRID, DENSITY_DELTAS) if families else None
         self.rmat = self.pool.submit(_gen_rmat, args.rmat_scale)
         sizes = I.batch_sizes(args.batch_count, 1024, args.batch_max, 1)
         self.batch = [self.pool.submit(_gen_pair, n, 1 + i) for i, n in enumerate(sizes)]
@@ -92,6 +108,9 @@ class Inputs:
 
     def families(self):
         return {k: f.result() for k, f in self.fam.items()}
+
+    def density(self):
+        return self.dens.result()
 
     def close(self):
         self.pool.shutdown(wait=False, cancel_futures=True)
@@ -132,10 +151,12 @@ def _row_block(fl, target_mults, start):
     return start, min(end, len(fl))
 
 
-def _oracle_rows_sample(a, b, fl, start, tol_tag, device_rows, label, seconds=CPU_SAMPLE_S, probe_mults=2e8):
+def _oracle_rows_sample(a, b, fl, start, tol_tag, device_rows, label, seconds=CPU_SAMPLE_S, probe_mults=2e8,
+                        keep=None):
     """CPU baseline leg: the oracle on a block of rows of about `seconds`
     seconds (grown from a small probe), timed on all host cores; its output
-    is compared with the device rows (device_rows(r0, r1) -> rp, col, val)."""
+    is compared with the device rows (device_rows(r0, r1) -> rp, col, val).
+    `keep` (a dict), if given, receives the oracle rows for later checks."""
     import oracle
     r0, r1 = _row_block(fl, probe_mults, start)
     t0 = time.perf_counter()
@@ -149,6 +170,8 @@ def _oracle_rows_sample(a, b, fl, start, tol_tag, device_rows, label, seconds=CP
     m = int(fl[r0:r1].sum())
     par = _compare_rows(*device_rows(r0, r1), ref, TOL[tol_tag])
     par["rows"] = [int(r0), int(r1)]
+    if keep is not None:
+        keep.update(ref=ref, r0=r0, r1=r1)
     return ({"value": 2 * m / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
              "sample": f"{label}: rows [{r0}, {r1}) of C ({m} multiplications), {dt:.2f} s"}, par)
 
@@ -323,7 +346,7 @@ def _link_bandwidth():
     return out
 
 
-def measure_chunked(args, local, a=None):
+def measure_chunked(args, local, a=None, triple_buffers=True):
     """Chunked C = A*A with operands and C in pinned host memory and a device
     budget: algorithmic GFLOP/s including every copy (symbolic + numeric),
     the fraction of the measured host link, bytes copied against the minimal
@@ -374,7 +397,33 @@ def measure_chunked(args, local, a=None):
         p0, p1 = int(crp[r0]), int(crp[r1])
         return crp[r0:r1 + 1].copy(), Cm.col[p0:p1].numpy(), Cm.val[p0:p1].numpy()
 
-    cpu, par = _oracle_rows_sample(a, a, fl, a.nrows // 2, "f64", rows, f"27-point {n}^3 A*A")
+    kept = {}
+    cpu, par = _oracle_rows_sample(a, a, fl, a.nrows // 2, "f64", rows, f"27-point {n}^3 A*A", keep=kept)
+    triple = None
+    if triple_buffers:
+        # the same step with every streamed operand in three buffers (the
+        # closing discussion of Section 4), into the same C arrays
+        h.set_option(sg.OPT_CHUNK_BUFFERS, 3)
+        t3, st3 = [], None
+        clocks.start()
+        for it in range(steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.chunked_symbolic(A, A, budget, out=Cm.row_ptr)
+            h.chunked_numeric_into(A, A, Cm, budget)
+            dt = time.perf_counter() - t0
+            st3 = h.chunked_stats()
+            if it > 0:
+                t3.append(dt)
+        clk3 = clocks.stop()
+        h.set_option(sg.OPT_CHUNK_BUFFERS, 2)
+        ms3 = 1e3 * statistics.median(t3)
+        p3 = _compare_rows(*rows(kept["r0"], kept["r1"]), kept["ref"], TOL["f64"])
+        triple = {"ms": ms3, "gflops": 2 * mults / (ms3 / 1e3) / 1e9,
+                  "link_frac": minimal / (ms3 / 1e3) / 1e9 / peak,
+                  "bytes_copied_over_minimal": (st3["h2d_bytes"] + st3["d2h_bytes"] + sym["h2d_bytes"]
+                                                + sym["d2h_bytes"]) / minimal,
+                  "numeric_plan": st3, "parity": p3, "vs_double": ms / ms3, "clocks": clk3}
     return {"metric_value": 2 * mults / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "steps": steps,
             "warmup": 1, "dtype": "f64",
             "config": {"workload": f"chunked C = A*A, 27-point 3D Laplacian on {n}^3, FP64, operands and C in "
@@ -387,7 +436,7 @@ def measure_chunked(args, local, a=None):
                                  "the same run; traffic = bytes actually copied (symbolic + numeric)"},
             "bytes_copied_over_minimal": moved / minimal, "link_gbs_measured": link, "numeric_plan": stats,
             "symbolic_plan": sym, "symbolic_ms": 1e3 * statistics.median(sym_times), "clocks": clk,
-            "cpu_baseline": cpu, "parity": par}
+            "cpu_baseline": cpu, "parity": par, "triple_buffering": triple}
 
 
 # ---------------------------------------------------------------- batched
@@ -597,6 +646,30 @@ def measure_families(args, problems, local):
             "families": out, "clocks": clk, "parity": {"all_rows_sampled_match": ok}}
 
 
+def measure_density(args, problem, local):
+    """The right-hand-side density experiment of Section 4 (Table 2):
+    Elasticity's R and A times random right-hand sides with delta entries per
+    row, GFLOP/s and % of the HBM-byte roofline per delta (the paper lists
+    GFLOP/s and cache miss ratios on its two memories)."""
+    import paper_1804_00695_gb300 as sg
+    a, r, rhs = problem
+    h = sg.Handle(local)
+    clocks = bench.ClockSampler(local)
+    clocks.start()
+    rows = {}
+    for d, y in sorted(rhs.items()):
+        rows[str(d)] = {"R*RHS": _product_entry(h, r, y, f"elasticity R*RHS delta {d}", local, cpu_seconds=0.5),
+                        "A*RHS": _product_entry(h, a, y, f"elasticity A*RHS delta {d}", local, cpu_seconds=0.5)}
+    clk = clocks.stop()
+    ok = all(v[k]["parity"]["pattern_exact"] and v[k]["parity"]["values_in_tolerance"]
+             for v in rows.values() for k in ("R*RHS", "A*RHS"))
+    return {"config": {"workload": f"density experiment: Elasticity (81 per row) on {DENSITY_GRID}^3 "
+                                   f"({a.nrows} rows), R and A times random right-hand sides with delta "
+                                   f"entries per row (N(0,1)), FP64", "deltas": list(DENSITY_DELTAS),
+                       "steps": 3, "warmup": 2},
+            "deltas": rows, "clocks": clk, "parity": {"all_rows_sampled_match": ok}}
+
+
 def measure_weak(args, local):
     """Throughput against problem size (the paper's growing problems): R*A
     and A*P of the 27-point family with A of about 1, 2, 4 and 8 GB, inputs
@@ -638,7 +711,7 @@ def measure_budget(args, local):
     # C (30 GB) fit whole
     for b in (4e9, 8e9, 16e9, 32e9, 64e9):
         args.budget = b
-        r = measure_chunked(args, local, a)
+        r = measure_chunked(args, local, a, triple_buffers=False)
         runs[f"{b / 1e9:g}GB"] = {"gflops": r["metric_value"], "ms": r["ms_per_step"],
                                   "symbolic_ms": r["symbolic_ms"], "link_frac": r["roofline"]["frac"],
                                   "bytes_copied_over_minimal": r["bytes_copied_over_minimal"],
@@ -740,6 +813,12 @@ def run(args, rank, world, local):
         r = measure_weak(args, local)
     elif args.workload == "budget256":
         r = measure_budget(args, local)
+    elif args.workload == "density":
+        r = measure_density(args, _gen_density(DENSITY_GRID, DENSITY_DELTAS), local)
+        top = r["deltas"][str(DENSITY_DELTAS[-1])]["A*RHS"]
+        r.update({"metric_value": top["gflops"], "unit": "GFLOP/s", "ms_per_step": top["ms"], "steps": 3,
+                  "warmup": 2, "dtype": "f64"})
+        r["config"]["workload"] += f" (value: A*RHS at delta {DENSITY_DELTAS[-1]})"
     else:
         r = measure_batched(args, I.random_batch(args.batch_count, 1024, args.batch_max, 1, dtype=np.float32),
                             local)

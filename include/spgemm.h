@@ -138,6 +138,14 @@ SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr 
  *  SPGEMM_OPT_LANES_NARROW_SYMBOLIC (0, 4, 8, 16, 32) and
  *    SPGEMM_OPT_LANES_NARROW_NUMERIC (0, 4, 8, 16): lanes per row of the
  *    narrow-row kernels (0 = from the mean length of the rows of A).
+ *  SPGEMM_OPT_CHUNK_BUFFERS (2 or 3, default 2): buffers per streamed
+ *    operand in spgemm_chunked_numeric / spgemm_chunked: 2 = double
+ *    buffering (one part is copied while the other is multiplied), 3 =
+ *    triple buffering (the buffering the paper's conclusion of Section 4
+ *    names: the budget is cut into three segments per operand, so copies
+ *    can run one more part ahead of the multiplications, with parts a
+ *    third smaller).  Results are identical; only the plan (parts, copy
+ *    bytes) and the overlap change.
  * spgemm_autotune picks lanes, small-row cap and slot factor by timing. */
 typedef enum spgemm_option {
     SPGEMM_OPT_F64_NATIVE = 1,
@@ -147,7 +155,8 @@ typedef enum spgemm_option {
     SPGEMM_OPT_SLOT_FACTOR = 5,
     SPGEMM_OPT_NARROW = 6,
     SPGEMM_OPT_LANES_NARROW_SYMBOLIC = 7,
-    SPGEMM_OPT_LANES_NARROW_NUMERIC = 8
+    SPGEMM_OPT_LANES_NARROW_NUMERIC = 8,
+    SPGEMM_OPT_CHUNK_BUFFERS = 9
 } spgemm_option;
 SPGEMM_API int spgemm_set_option(spgemm_handle handle, int option, int64_t value);
 

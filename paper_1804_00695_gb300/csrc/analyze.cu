@@ -70,13 +70,17 @@ __global__ void k_compress_long(int64_t nrows, int64_t ncols, const int64_t *__r
                                 int *unsorted_flag) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     bool bad = false, unsorted = false;
-    // a warp tests 32 rows at once and compresses the long ones among them
-    for (int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; r0 < nrows; r0 += warps * 32) {
-      const int64_t rl = r0 + lane;
+    // a warp tests 32 rows at once and compresses the long ones among them;
+    // the rows a warp tests are `warps` apart (row wg + warps * m), so that
+    // long rows stored next to each other (the heavy rows of a power-law
+    // graph cluster at the low indices) go to different warps
+    for (int64_t m0 = 0; wg + warps * m0 < nrows; m0 += 32) {
+      const int64_t rl = wg + warps * (m0 + lane);
       unsigned longs = __ballot_sync(0xffffffffu, rl < nrows && rp[rl + 1] - rp[rl] > COMPRESS_LONG);
       while (longs) {
-        const int64_t r = r0 + __ffs(longs) - 1;
+        const int64_t r = wg + warps * (m0 + __ffs(longs) - 1);
         longs &= longs - 1u;
         const int64_t beg = rp[r], end = rp[r + 1];
         int cblk = -1;          // block of the run carried from the previous 32 (-1: none)

@@ -83,7 +83,11 @@ struct spgemm_handle_s {
     void *arena = nullptr;
     size_t arena_cap = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev[14] = {};   // [0..11] chunked calls, [12..13] spgemm_host
+    // [0, CHUNK_EVENTS) chunked calls, then the ordering of a chunked call
+    // against the caller's stream (3), then spgemm_host (2)
+    static constexpr int EV_ORDER = CHUNK_EVENTS, EV_HOST = CHUNK_EVENTS + 3;
+    cudaEvent_t ev[CHUNK_EVENTS + 5] = {};
+    int chunk_nbuf = 2;                  // buffers per streamed operand of the chunked numeric call
     std::vector<int64_t> zeros;   // offsets of an empty C (chunked symbolic plan)
     int *host_mm = nullptr;       // pinned, column ranges of A parts (chunked numeric)
     ChunkStats cstats;
@@ -458,7 +462,7 @@ static int side_streams(spgemm_handle h) {
         SG_CUDA(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
         SG_CUDA(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
         for (auto &e : h->ev) SG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        SG_CUDA(cudaMallocHost(&h->host_mm, 4 * sizeof(int)));
+        SG_CUDA(cudaMallocHost(&h->host_mm, 2 * CHUNK_MAX_BUF * sizeof(int)));
     }
     return SPGEMM_OK;
 }
@@ -468,10 +472,10 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
     SG_TRY(side_streams(h));
     // work a previous call left on the side streams (one that returned an
     // error part-way) finishes before this call reuses or frees the arena
-    SG_CUDA(cudaEventRecord(h->ev[8], h->s_in));
-    SG_CUDA(cudaStreamWaitEvent(s, h->ev[8], 0));
-    SG_CUDA(cudaEventRecord(h->ev[9], h->s_out));
-    SG_CUDA(cudaStreamWaitEvent(s, h->ev[9], 0));
+    SG_CUDA(cudaEventRecord(h->ev[h->EV_ORDER + 1], h->s_in));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[h->EV_ORDER + 1], 0));
+    SG_CUDA(cudaEventRecord(h->ev[h->EV_ORDER + 2], h->s_out));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[h->EV_ORDER + 2], 0));
     if (h->arena_cap != budget) {
         if (h->arena) {
             // s now waits for both side streams: nothing queued touches the
@@ -490,15 +494,16 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
         h->arena_cap = budget;
     }
     // work issued before this call on the caller's stream comes first
-    SG_CUDA(cudaEventRecord(h->ev[7], s));
-    SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[7], 0));
-    SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[7], 0));
+    SG_CUDA(cudaEventRecord(h->ev[h->EV_ORDER], s));
+    SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[h->EV_ORDER], 0));
+    SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[h->EV_ORDER], 0));
     env.ctx = &c;
     env.cache = &h->ccache;
     env.arena = h->arena;
     env.s_in = h->s_in;
     env.s_out = h->s_out;
-    for (int k = 0; k < 12; k++) env.ev[k] = h->ev[k];
+    for (int k = 0; k < CHUNK_EVENTS; k++) env.ev[k] = h->ev[k];
+    env.nbuf = h->chunk_nbuf;
     env.err = &h->dstate->err;
     env.zeros = &h->zeros;
     env.host_mm = h->host_mm;
@@ -639,8 +644,8 @@ int spgemm_host(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_cs
     int64_t *crp = c_dev ? C->row_ptr : (int64_t *)(d + oc_rp);
     // patterns on the caller's stream; values on the copy-in stream, after
     // the work already queued on the caller's stream
-    SG_CUDA(cudaEventRecord(h->ev[12], s));
-    SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[12], 0));
+    SG_CUDA(cudaEventRecord(h->ev[h->EV_HOST], s));
+    SG_CUDA(cudaStreamWaitEvent(h->s_in, h->ev[h->EV_HOST], 0));
     SG_CUDA(cudaMemcpyAsync(Ad.row_ptr, A->row_ptr, (size_t)(A->nrows + 1) * 8, cudaMemcpyHostToDevice, s));
     if (A->nnz) SG_CUDA(cudaMemcpyAsync(Ad.col_idx, A->col_idx, (size_t)A->nnz * 4, cudaMemcpyHostToDevice, s));
     if (!b_dev) {
@@ -651,7 +656,7 @@ int spgemm_host(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_cs
         SG_CUDA(cudaMemcpyAsync(Ad.values, A->values, (size_t)A->nnz * vb, cudaMemcpyHostToDevice, h->s_in));
     if (!b_dev && B->nnz)
         SG_CUDA(cudaMemcpyAsync(Bd.values, B->values, (size_t)B->nnz * vb, cudaMemcpyHostToDevice, h->s_in));
-    SG_CUDA(cudaEventRecord(h->ev[13], h->s_in));
+    SG_CUDA(cudaEventRecord(h->ev[h->EV_HOST + 1], h->s_in));
     int64_t nnz = 0;
     const int st_sym = spgemm_symbolic(h, &Ad, &Bd, crp, &nnz, stream);
     if (st_sym != SPGEMM_OK) {
@@ -660,8 +665,8 @@ int spgemm_host(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_cs
     }
     // C's offsets leave while the numeric phase runs
     if (!c_dev) {
-        SG_CUDA(cudaEventRecord(h->ev[12], s));
-        SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[12], 0));
+        SG_CUDA(cudaEventRecord(h->ev[h->EV_HOST], s));
+        SG_CUDA(cudaStreamWaitEvent(h->s_out, h->ev[h->EV_HOST], 0));
         SG_CUDA(cudaMemcpyAsync(C->row_ptr, crp, (size_t)(A->nrows + 1) * 8, cudaMemcpyDeviceToHost, h->s_out));
     }
     int32_t *col = nullptr;
@@ -678,15 +683,15 @@ int spgemm_host(spgemm_handle h, int dtype, const spgemm_csr *A, const spgemm_cs
         Cd.col_idx = (int32_t *)h->hbufc;
         Cd.values = h->hbufc + part((size_t)nnz * 4);
     }
-    SG_CUDA(cudaStreamWaitEvent(s, h->ev[13], 0));
+    SG_CUDA(cudaStreamWaitEvent(s, h->ev[h->EV_HOST + 1], 0));
     SG_TRY(spgemm_numeric(h, dtype, &Ad, &Bd, &Cd, stream));
     if (!c_dev && nnz) {
         SG_CUDA(cudaMemcpyAsync(col, Cd.col_idx, (size_t)nnz * 4, cudaMemcpyDeviceToHost, s));
         SG_CUDA(cudaMemcpyAsync(val, Cd.values, (size_t)nnz * vb, cudaMemcpyDeviceToHost, s));
     }
     if (!c_dev) {
-        SG_CUDA(cudaEventRecord(h->ev[12], h->s_out));
-        SG_CUDA(cudaStreamWaitEvent(s, h->ev[12], 0));
+        SG_CUDA(cudaEventRecord(h->ev[h->EV_HOST], h->s_out));
+        SG_CUDA(cudaStreamWaitEvent(s, h->ev[h->EV_HOST], 0));
     }
     C->nrows = A->nrows;
     C->ncols = B->ncols;
@@ -1001,6 +1006,10 @@ int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
                 return SPGEMM_ERR_ARG;
             }
             h->g_narrow_num = (int)value;
+            return SPGEMM_OK;
+        case SPGEMM_OPT_CHUNK_BUFFERS:
+            if (value != 2 && value != 3) { set_error("chunk buffers must be 2 or 3"); return SPGEMM_ERR_ARG; }
+            h->chunk_nbuf = (int)value;
             return SPGEMM_OK;
         default: set_error("unknown option %d", option); return SPGEMM_ERR_ARG;
     }

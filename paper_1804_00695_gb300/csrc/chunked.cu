@@ -896,10 +896,11 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
         return SPGEMM_ERR_BUDGET;
     }
     // Algorithm 4 on the budget left after the fixed reserve.  The streamed
-    // (inner) operand is double buffered, so if the outer part plus two inner
-    // parts exceed the budget, the inner operand is cut again, finer, with
-    // BinarySearch: the algorithm and the outer parts stay as Algorithm 4
-    // chose them.
+    // (inner) operand is double (or triple) buffered, so if the outer part
+    // plus nb inner parts exceed the budget, the inner operand is cut again,
+    // finer, with BinarySearch: the algorithm and the outer parts stay as
+    // Algorithm 4 chose them.
+    const int nb = env.nbuf >= 3 ? 3 : 2;
     ChunkPlan p;
     const int64_t avail = (int64_t)(budget - reserve) - 16 * 256;
     SG_TRY(plan_chunks(A.row_ptr, A.nrows, C.row_ptr, B.row_ptr, B.nrows, vb, vb, (int64_t)(budget - reserve), p));
@@ -921,20 +922,20 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
         return (mr + 1) * 8 + mb * (int64_t)(4 + vb);
     };
     {
-        // Both operands are double buffered in Algorithm 2 (the next A/C part
-        // comes in while the current one is multiplied and the previous one
-        // goes out), the streamed A/C parts in Algorithm 3.  Parts that do
-        // not fit twice are cut again with BinarySearch (finer parts, same
-        // algorithm).  B parts are also cut to at most an eighth of an A/C
-        // part so that skipping the parts an A part does not reach is fine
-        // grained.
+        // Both operands are double (nb = 3: triple) buffered in Algorithm 2
+        // (the next A/C part comes in while the current one is multiplied
+        // and the previous ones go out), the streamed A/C parts in Algorithm
+        // 3.  Parts that do not fit nb times are cut again with BinarySearch
+        // (finer parts, same algorithm).  B parts are also cut to at most an
+        // eighth of an A/C part so that skipping the parts an A part does not
+        // reach is fine grained.
         const bool alg2 = p.algorithm == 2;
         std::vector<int64_t> &outer_cuts = alg2 ? p.ac_cuts : p.b_cuts;
         std::vector<int64_t> &inner_cuts = alg2 ? p.b_cuts : p.ac_cuts;
         auto outer_sz = [&]() { return alg2 ? buf_ac(outer_cuts) : buf_b(outer_cuts); };
         auto inner_sz = [&]() { return alg2 ? buf_b(inner_cuts) : buf_ac(inner_cuts); };
-        const int nouter = alg2 ? 2 : 1;
-        double olimit = (double)avail * 0.30;
+        const int nouter = alg2 ? nb : 1;
+        double olimit = (double)avail * 0.60 / nb;
         for (int iter = 0; alg2 && outer_sz() * nouter > (int64_t)((double)avail * 0.62); iter++) {
             const bool ok = iter < 40 && cut_rows(A.row_ptr, C.row_ptr, A.nrows, vb, olimit, outer_cuts);
             if (!ok) {
@@ -944,16 +945,16 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             olimit *= 0.85;
         }
         const int64_t outer = outer_sz() * nouter;
-        double limit = (double)(avail - outer) / 2.0;
+        double limit = (double)(avail - outer) / nb;
         if (alg2) limit = std::min(limit, (double)outer / nouter / 8.0);
         bool first = alg2;   // Algorithm 2: always cut B to the fine size
-        for (int iter = 0; first || inner_sz() * 2 + outer > avail; iter++) {
+        for (int iter = 0; first || inner_sz() * nb + outer > avail; iter++) {
             first = false;
             bool cut_ok = limit > 0 && iter < 40 &&
                           (alg2 ? cut_rows(B.row_ptr, nullptr, B.nrows, vb, limit, inner_cuts)
                                 : cut_rows(A.row_ptr, C.row_ptr, A.nrows, vb, limit, inner_cuts));
             if (!cut_ok) {
-                set_error("chunked: budget %zu too small for a part and two double-buffered parts", budget);
+                set_error("chunked: budget %zu too small for a part and %d buffered parts", budget, nb);
                 return SPGEMM_ERR_BUDGET;
             }
             limit *= 0.85;
@@ -968,7 +969,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     // carve the arena
     Arena ar{(char *)env.arena, budget, 0};
     void *gws = gws_bytes ? ar.take(gws_bytes) : nullptr;
-    int *mm = (int *)ar.take(4 * sizeof(int));
+    int *mm = (int *)ar.take(2 * CHUNK_MAX_BUF * sizeof(int));   // column range of each A/C buffer's part
     int64_t max_ac_rows = 0, max_ac_a = 0, max_ac_c = 0, max_b_rows = 0, max_b_nnz = 0;
     for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
         const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1];
@@ -980,21 +981,21 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
         max_b_rows = std::max(max_b_rows, p.b_cuts[t + 1] - p.b_cuts[t]);
         max_b_nnz = std::max(max_b_nnz, B.row_ptr[p.b_cuts[t + 1]] - B.row_ptr[p.b_cuts[t]]);
     }
-    const int nbuf_ac = 2;
-    PartBuf Ab[2], Cb[2], Bb[2];
+    const int nbuf_ac = nb;
+    PartBuf Ab[CHUNK_MAX_BUF], Cb[CHUNK_MAX_BUF], Bb[CHUNK_MAX_BUF];
     bool ok = mm != nullptr;
     for (int u = 0; u < nbuf_ac && ok; u++)
         ok = take_part(ar, Ab[u], max_ac_rows, max_ac_a, vb) && take_part(ar, Cb[u], max_ac_rows, max_ac_c, vb);
-    // Algorithm 2: two byte buffers for the streamed rows of B, as large as
+    // Algorithm 2: nb byte buffers for the streamed rows of B, as large as
     // the budget leaves (at least a fixed part each); a part of B or a window
     // of rows is laid out in them per copy.  Algorithm 3: one fixed part.
-    char *binner[2] = {nullptr, nullptr};
+    char *binner[CHUNK_MAX_BUF] = {nullptr, nullptr, nullptr};
     size_t inner_cap = 0;
     if (p.algorithm == 2) {
         const size_t need_fixed = carve_bytes(max_b_rows, max_b_nnz, vb);
         const size_t left = budget > ar.used + 4096 ? budget - ar.used - 4096 : 0;
-        inner_cap = std::max(need_fixed, (left / 2) & ~(size_t)255);
-        for (int u = 0; u < 2 && ok; u++) {
+        inner_cap = std::max(need_fixed, (left / nb) & ~(size_t)255);
+        for (int u = 0; u < nb && ok; u++) {
             binner[u] = (char *)ar.take(inner_cap);
             ok = binner[u] != nullptr;
         }
@@ -1008,7 +1009,11 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
     stats.device_bytes = (int64_t)ar.used;
     int st = SPGEMM_OK;
     const cudaStream_t si = env.s_in, so = env.s_out;
-    cudaEvent_t *ev = env.ev;   // [0..1] copied-in, [2..3] compute done, [4..5] copied-out
+    // event groups, one event per buffer: rows of B in, rows of B used, C part
+    // out, A part (and the offsets of its C part) in, A part used
+    cudaEvent_t *ev = env.ev;
+    cudaEvent_t *ev_bin = ev, *ev_bused = ev + CHUNK_MAX_BUF, *ev_cout = ev + 2 * CHUNK_MAX_BUF,
+                *ev_ain = ev + 3 * CHUNK_MAX_BUF, *ev_aused = ev + 4 * CHUNK_MAX_BUF;
     int *err = env.err;
     // mode: FMA_* bits (first pass of the C part, one window of B)
     auto fma = [&](const PartBuf &Ap, int64_t rows, int64_t lo, int64_t hi, const PartBuf &Bp,
@@ -1018,10 +1023,9 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                    : launch_fma<float>(Ap, rows, lo, hi, Bp, Cp, true, fma_blocks, slots, gws, err, c, mode);
     };
     if (p.algorithm == 2) {
-        // ev (by buffer slot): [0..1] rows of B in, [2..3] rows of B used,
-        // [4..5] C part out, [6..7] A part and the offsets of its C part in
-        // (and, without recorded ranges, the part's column range in pinned
-        // host memory), [10..11] A part used.  The A buffer and the offsets
+        // Buffer slot j % nb of A/C part j, slot t % nb of the t-th copy of
+        // rows of B.  ev_ain[slot] also covers, without recorded ranges, the
+        // part's column range in pinned host memory.  The A buffer and the offsets
         // of a C buffer are reused once the part's products are done, the
         // entries of a C buffer once they have left the device, so neither
         // waits for the other.  The copy-in stream carries copies only and
@@ -1046,9 +1050,9 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             }
         };
         auto stage_ac = [&](size_t j) -> int {
-            const int slot = (int)(j & 1);
+            const int slot = (int)(j % nb);
             const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
-            if (j >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[10 + slot], 0));
+            if (j >= (size_t)nb) SG_CUDA(cudaStreamWaitEvent(si, ev_aused[slot], 0));
             stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st, false);
             SG_TRY(st);
             // C starts empty: only its offsets come in
@@ -1064,12 +1068,12 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                         Ab[slot].col, an, dmm);
                 SG_CUDA(cudaMemcpyAsync(hmm + 2 * slot, dmm, 8, cudaMemcpyDeviceToHost, si));
             }
-            SG_CUDA(cudaEventRecord(ev[6 + slot], si));
+            SG_CUDA(cudaEventRecord(ev_ain[slot], si));
             return SPGEMM_OK;
         };
         if (nac > 0) SG_TRY(stage_ac(0));
         for (size_t j = 0; j < nac; j++) {
-            const int slot = (int)(j & 1);
+            const int slot = (int)(j % nb);
             const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
             const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0];
             int lo_c, hi_c;
@@ -1078,7 +1082,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             } else {
                 // the host waits for this part's column range only; the
                 // device still has the previous part's products queued
-                SG_CUDA(cudaEventSynchronize(ev[6 + slot]));
+                SG_CUDA(cudaEventSynchronize(ev_ain[slot]));
                 lo_c = hmm[2 * slot];
                 hi_c = hmm[2 * slot + 1];
                 // lo_c == INT_MAX only for a part with no entries (hi_c
@@ -1111,8 +1115,8 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             }
             // the A part and the offsets of its C part, rebased on the compute
             // stream once the C part that used the buffer has left
-            SG_CUDA(cudaStreamWaitEvent(s, ev[6 + slot], 0));
-            if (j >= 2) SG_CUDA(cudaStreamWaitEvent(s, ev[4 + slot], 0));
+            SG_CUDA(cudaStreamWaitEvent(s, ev_ain[slot], 0));
+            if (j >= (size_t)nb) SG_CUDA(cudaStreamWaitEvent(s, ev_cout[slot], 0));
             SG_TRY(rebase_rows(Ab[slot].rp, rows, A.row_ptr[r0], s));
             SG_TRY(rebase_rows(Cb[slot].rp, rows, C.row_ptr[r0], s));
             // One window and no long rows: the single pass writes every entry
@@ -1122,28 +1126,28 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                 SG_CUDA(cudaMemsetAsync(Cb[slot].col, 0xff, (size_t)cn * 4, s));
                 SG_CUDA(cudaMemsetAsync(Cb[slot].val, 0, (size_t)cn * vb, s));
             }
-            // stream the needed rows of B, double buffered
+            // stream the needed rows of B, nb buffers
             for (size_t u = 0; u < need.size(); u++, bcount++) {
-                const int bs = (int)(bcount & 1);
+                const int bs = (int)(bcount % nb);
                 const int64_t b0 = need[u].first, b1 = need[u].second;
                 Bb[bs] = carve(binner[bs], b1 - b0, vb, B.row_ptr[b1] - B.row_ptr[b0]);
-                if (bcount >= 2) SG_CUDA(cudaStreamWaitEvent(si, ev[2 + bs], 0));
+                if (bcount >= (size_t)nb) SG_CUDA(cudaStreamWaitEvent(si, ev_bused[bs], 0));
                 stats.h2d += copy_rows_in(B, b0, b1, vb, Bb[bs].rp, Bb[bs].col, Bb[bs].val, si, &st, false);
                 SG_TRY(st);
-                SG_CUDA(cudaEventRecord(ev[bs], si));
-                SG_CUDA(cudaStreamWaitEvent(s, ev[bs], 0));
+                SG_CUDA(cudaEventRecord(ev_bin[bs], si));
+                SG_CUDA(cudaStreamWaitEvent(s, ev_bin[bs], 0));
                 SG_TRY(rebase_rows(Bb[bs].rp, b1 - b0, B.row_ptr[b0], s));
                 // a recorded range may be stale if A changed after the
                 // symbolic call: a window then checks every column of A
                 const int mode = (u == 0 ? FMA_FRESH : 0) | (window && known_ranges ? FMA_STRICT : 0);
                 SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[bs], Cb[slot], mode));
-                SG_CUDA(cudaEventRecord(ev[2 + bs], s));
+                SG_CUDA(cudaEventRecord(ev_bused[bs], s));
             }
-            SG_CUDA(cudaEventRecord(ev[10 + slot], s));   // A part used, C part complete
+            SG_CUDA(cudaEventRecord(ev_aused[slot], s));   // A part used, C part complete
             // the next A part comes in behind this part's rows of B
             if (j + 1 < nac) SG_TRY(stage_ac(j + 1));
             // finished part of C back to host memory
-            SG_CUDA(cudaStreamWaitEvent(so, ev[10 + slot], 0));
+            SG_CUDA(cudaStreamWaitEvent(so, ev_aused[slot], 0));
             if (cn > 0) {
                 const int64_t p0 = C.row_ptr[r0];
                 SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[slot].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
@@ -1151,22 +1155,22 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                                         cudaMemcpyDeviceToHost, so));
                 stats.d2h += cn * (4 + vb);
             }
-            SG_CUDA(cudaEventRecord(ev[4 + slot], so));
+            SG_CUDA(cudaEventRecord(ev_cout[slot], so));
         }
-        SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
-        SG_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
+        for (int u = 0; u < nb && (size_t)u < nac; u++) SG_CUDA(cudaStreamWaitEvent(s, ev_cout[u], 0));
     } else {
         for (size_t t = 0; t + 1 < p.b_cuts.size(); t++) {
             const int64_t b0 = p.b_cuts[t], b1 = p.b_cuts[t + 1];
-            SG_CUDA(cudaStreamWaitEvent(si, ev[6], 0));
+            if (t > 0) SG_CUDA(cudaStreamWaitEvent(si, ev_bused[0], 0));
             stats.h2d += copy_rows_in(B, b0, b1, vb, Bb[0].rp, Bb[0].col, Bb[0].val, si, &st);
             SG_TRY(st);
             for (size_t j = 0; j + 1 < p.ac_cuts.size(); j++) {
-                const int slot = (int)(j & 1);
+                const size_t jj = t * (p.ac_cuts.size() - 1) + j;   // A/C parts streamed so far
+                const int slot = (int)(jj % nb);
                 const int64_t r0 = p.ac_cuts[j], r1 = p.ac_cuts[j + 1], rows = r1 - r0;
                 const int64_t cn = C.row_ptr[r1] - C.row_ptr[r0], p0 = C.row_ptr[r0];
                 // this buffer's previous C part must have gone out first
-                SG_CUDA(cudaStreamWaitEvent(si, ev[4 + slot], 0));
+                if (jj >= (size_t)nb) SG_CUDA(cudaStreamWaitEvent(si, ev_cout[slot], 0));
                 stats.h2d += copy_rows_in(A, r0, r1, vb, Ab[slot].rp, Ab[slot].col, Ab[slot].val, si, &st);
                 SG_TRY(st);
                 SG_CUDA(cudaMemcpyAsync(Cb[slot].rp, C.row_ptr + r0, (size_t)(rows + 1) * 8, cudaMemcpyHostToDevice, si));
@@ -1184,26 +1188,25 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
                         stats.h2d += cn * (4 + vb);
                     }
                 }
-                SG_CUDA(cudaEventRecord(ev[slot], si));
-                SG_CUDA(cudaStreamWaitEvent(s, ev[slot], 0));
+                SG_CUDA(cudaEventRecord(ev_ain[slot], si));
+                SG_CUDA(cudaStreamWaitEvent(s, ev_ain[slot], 0));
                 SG_TRY(fma(Ab[slot], rows, b0, b1, Bb[0], Cb[slot], t == 0 ? FMA_FRESH : 0));
-                SG_CUDA(cudaEventRecord(ev[2 + slot], s));
-                SG_CUDA(cudaStreamWaitEvent(so, ev[2 + slot], 0));
+                SG_CUDA(cudaEventRecord(ev_aused[slot], s));
+                SG_CUDA(cudaStreamWaitEvent(so, ev_aused[slot], 0));
                 if (cn > 0) {
                     SG_CUDA(cudaMemcpyAsync(C.col_idx + p0, Cb[slot].col, (size_t)cn * 4, cudaMemcpyDeviceToHost, so));
                     SG_CUDA(cudaMemcpyAsync((char *)C.values + (size_t)p0 * vb, Cb[slot].val, (size_t)cn * vb,
                                             cudaMemcpyDeviceToHost, so));
                     stats.d2h += cn * (4 + vb);
                 }
-                SG_CUDA(cudaEventRecord(ev[4 + slot], so));
+                SG_CUDA(cudaEventRecord(ev_cout[slot], so));
             }
             // the next B part may only overwrite the buffer once every use of it is done
-            SG_CUDA(cudaEventRecord(ev[6], s));
+            SG_CUDA(cudaEventRecord(ev_bused[0], s));
         }
-        SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
-        SG_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
+        const size_t streamed = (p.b_cuts.size() - 1) * (p.ac_cuts.size() - 1);
+        for (int u = 0; u < nb && (size_t)u < streamed; u++) SG_CUDA(cudaStreamWaitEvent(s, ev_cout[u], 0));
     }
-    SG_CUDA(cudaStreamWaitEvent(s, ev[4], 0));
     return SPGEMM_OK;
 }
 

@@ -311,15 +311,20 @@ struct ChunkCache {
     std::vector<int2> brange;   // per block of CHUNK_RB rows of A: {min, max} column ({INT_MAX, INT_MIN} if none)
     int64_t max_row = 0;        // largest row of C
 };
+// Events of a chunked call: the numeric call uses five groups of up to
+// CHUNK_MAX_BUF (one per buffer of a group), the symbolic call the first 8.
+constexpr int CHUNK_MAX_BUF = 3;
+constexpr int CHUNK_EVENTS = 5 * CHUNK_MAX_BUF;
 struct ChunkEnv {
     Ctx *ctx = nullptr;
     ChunkCache *cache = nullptr;
     void *arena = nullptr;        // exactly the budget, device
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev[12] = {};
+    cudaEvent_t ev[CHUNK_EVENTS] = {};
+    int nbuf = 2;                 // buffers per streamed operand: 2 (double) or 3 (triple)
     int *err = nullptr;
     std::vector<int64_t> *zeros = nullptr;   // host scratch: offsets of an empty C
-    int *host_mm = nullptr;                  // pinned: column ranges of two A parts
+    int *host_mm = nullptr;                  // pinned: column ranges of the A parts in the buffers
 };
 struct ChunkStats {
     int algorithm = 0, branch = 0;

@@ -424,12 +424,28 @@ def random_square(n: int, seed: int, rmin: int = 4, rmax: int = 32, dtype=np.flo
     """n x n matrix, each row holding a uniform rmin..rmax distinct random
     columns (uniform without replacement: the first distinct ones of a row's
     candidate draws), N(0,1) values (Box-Muller), columns ascending."""
+    return random_rows(n, n, seed, rmin, rmax, dtype)
+
+
+def random_rhs(nrows: int, ncols: int, delta: int, seed: int, dtype=np.float64) -> Csr:
+    """Random right-hand side of the density experiment (Section 4, Table 2):
+    nrows x ncols, every row holding min(delta, ncols) distinct uniform
+    random columns, N(0,1) values."""
+    return random_rows(nrows, ncols, seed, delta, delta, dtype)
+
+
+def random_rows(nrows: int, ncols: int, seed: int, rmin: int, rmax: int, dtype=np.float32) -> Csr:
+    """nrows x ncols matrix, each row holding a uniform rmin..rmax distinct
+    random columns (at most ncols; uniform without replacement: the first
+    distinct ones of the row's candidate draws), N(0,1) values (Box-Muller),
+    columns ascending."""
+    n = nrows
     ncand = rmax + 16
     rows = np.arange(n, dtype=np.uint64)
     rlen = rmin + (uniform01(rows, seed, 1) * (rmax - rmin + 1)).astype(np.int64)
-    rlen = np.minimum(rlen, min(rmax, n))
+    rlen = np.minimum(rlen, min(rmax, ncols))
     cand_ctr = rows[:, None] * _U64(ncand) + np.arange(ncand, dtype=np.uint64)[None, :]
-    cand = (uniform01(cand_ctr, seed, 2) * n).astype(np.int64)
+    cand = (uniform01(cand_ctr, seed, 2) * ncols).astype(np.int64)
     # position of each candidate's first occurrence in its row
     order = np.argsort(cand, axis=1, kind="stable")
     sc = np.take_along_axis(cand, order, axis=1)
@@ -448,7 +464,7 @@ def random_square(n: int, seed: int, rmin: int = 4, rmax: int = 32, dtype=np.flo
         seen = set(cand[i][keep[i]].tolist())
         k = 0
         while len(seen) < rlen[i]:
-            v = int(uniform01(np.array([int(i) * 1024 + k], dtype=np.uint64), seed, 3)[0] * n)
+            v = int(uniform01(np.array([int(i) * 1024 + k], dtype=np.uint64), seed, 3)[0] * ncols)
             k += 1
             if v not in seen:
                 seen.add(v); extra_r.append(i); extra_c.append(v)
@@ -464,7 +480,7 @@ def random_square(n: int, seed: int, rmin: int = 4, rmax: int = 32, dtype=np.flo
     u1 = uniform01(ctr, seed, 4)
     u2 = uniform01(ctr, seed, 5)
     val = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
-    return Csr(n, n, rp, col, val.astype(dtype))
+    return Csr(n, ncols, rp, col, val.astype(dtype))
 
 
 def batch_sizes(count: int, lo: int, hi: int, seed: int = 1) -> list[int]:

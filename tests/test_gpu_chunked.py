@@ -338,3 +338,88 @@ def test_chunked_numeric_bad_columns_without_recorded_ranges():
         for bud in (budget, budget + (1 << 20)):
             c = h.chunked_numeric(sg.HostCsr.from_numpy(a), B, rp_host, ref.nnz, bud)
             check(c, ref, "f64")
+
+
+@pytest.fixture()
+def h3(cuda_lib):
+    """A handle whose chunked calls triple buffer (SPGEMM_OPT_CHUNK_BUFFERS = 3)."""
+    hh = sg.Handle()
+    hh.set_option(sg.OPT_CHUNK_BUFFERS, 3)
+    return hh
+
+
+def test_chunked_triple_buffering_many_parts(h3):
+    """Triple buffering (the budget in three segments per streamed operand,
+    the closing discussion of Section 4): the same product as the oracle on
+    random unsorted operands cut into many parts on both sides, with at
+    least four A/C parts so that every buffer is used and reused."""
+    a = I.random_csr(900, 700, 0.02, 171, shuffle_cols=True)
+    b = I.random_csr(700, 800, 0.03, 172, shuffle_cols=True)
+    ref = oracle.spgemm(a, b)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, b.row_ptr, 8, 2, 2, 2)
+    assert budget is not None
+    ref, st = run_chunked(h3, a, b, budget)
+    assert st["algorithm"] == 2 and st["n_ac"] >= 4 and st["n_b"] >= 2
+
+
+@pytest.mark.parametrize("fresh", [False, True])
+def test_chunked_triple_buffering_banded(h3, fresh):
+    """Banded operand, B windows in three buffers; with recorded column
+    ranges (symbolic call first) and measured ones (fresh handle)."""
+    a = I.laplace3d_27pt(20)
+    ref = oracle.spgemm(a, a)
+    A = sg.HostCsr.from_numpy(a)
+    budget, plan = find_budget(a.row_ptr, ref.row_ptr, a.row_ptr, 8, 2, 3, 2)
+    assert budget is not None
+    if fresh:
+        hh = sg.Handle()
+        hh.set_option(sg.OPT_CHUNK_BUFFERS, 3)
+        import torch
+        c = hh.chunked_numeric(A, A, torch.from_numpy(ref.row_ptr.copy()).pin_memory(), ref.nnz, budget)
+        st = hh.chunked_stats()
+    else:
+        rp, nnz = h3.chunked_symbolic(A, A, max(budget, 1 << 22))
+        c = h3.chunked_numeric(A, A, rp, nnz, budget)
+        st = h3.chunked_stats()
+    check(c, ref, "f64")
+    assert st["algorithm"] == 2 and st["n_ac"] >= 4 and st["device_bytes"] <= budget
+
+
+def test_chunked_triple_buffering_alg3_bytes(h3):
+    """Algorithm 3 (B outer, several parts) with three A/C buffers: partial
+    rows of C go out and come back in across the buffers; the product equals
+    the oracle and the bytes copied follow the same formula as with two."""
+    a = I.random_csr(200, 20000, 0.0005, 83, shuffle_cols=True)
+    b = I.random_csr(20000, 300, 0.033, 84, shuffle_cols=True)
+    ref = oracle.spgemm(a, b)
+    tot = sum(CH.range_bytes(x, 0, len(x) - 1, 8) for x in (a.row_ptr, ref.row_ptr, b.row_ptr))
+    hit = False
+    for frac in np.geomspace(0.2, 0.04, 30):
+        f = int(tot * frac)
+        try:
+            p = sg.plan_chunks(a.row_ptr, ref.row_ptr, b.row_ptr, 8, f)
+        except sg.SpgemmError:
+            continue
+        if p["algorithm"] != 3 or len(p["p_b"]) < 2:
+            continue
+        try:
+            ref, st = run_chunked(h3, a, b, f)
+        except sg.SpgemmError as e:
+            assert e.status == 5
+            continue
+        if st["algorithm"] == 3 and st["n_b"] >= 2:
+            h2d, d2h = expected_bytes(st, a, b, ref.row_ptr, ref.nnz)
+            assert st["h2d_bytes"] == h2d and st["d2h_bytes"] == d2h
+            hit = True
+            break
+    assert hit
+
+
+def test_chunked_buffers_option_values(cuda_lib):
+    hh = sg.Handle()
+    for v in (2, 3):
+        hh.set_option(sg.OPT_CHUNK_BUFFERS, v)
+    for v in (0, 1, 4):
+        with pytest.raises(sg.SpgemmError) as ei:
+            hh.set_option(sg.OPT_CHUNK_BUFFERS, v)
+        assert ei.value.status == 1

@@ -121,3 +121,31 @@ def test_oracle_products_dense(name):
     assert np.allclose(cd, rd @ ad @ pd, rtol=0, atol=1e-11)
     # the coarse operator of a symmetric A is symmetric
     assert np.allclose(cd, cd.T, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("delta", [1, 4, 16, 64, 256])
+def test_random_rhs_rows(delta):
+    """Right-hand sides of the density experiment (Table 2): every row holds
+    exactly min(delta, ncols) distinct columns, ascending and in range; the
+    columns are spread evenly over the matrix and the values are N(0,1)."""
+    nrows, ncols = 700, 3000
+    m = I.random_rhs(nrows, ncols, delta, seed=11)
+    assert (m.nrows, m.ncols) == (nrows, ncols)
+    lens = np.diff(m.row_ptr)
+    assert np.all(lens == min(delta, ncols))
+    for i in range(0, nrows, 37):
+        c = m.col[m.row_ptr[i]:m.row_ptr[i + 1]]
+        assert np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < ncols
+    # columns: each tenth of the range receives about a tenth of the entries
+    hist = np.bincount(m.col.astype(np.int64) * 10 // ncols, minlength=10) / m.nnz
+    assert np.all(np.abs(hist - 0.1) < 0.1 * (0.5 if m.nnz >= 10000 else 1.0))
+    if m.nnz >= 10000:
+        assert abs(m.val.mean()) < 0.05 and abs(m.val.std() - 1.0) < 0.05
+
+
+def test_random_rhs_more_than_ncols():
+    """delta above the number of columns gives full rows."""
+    m = I.random_rhs(40, 30, 64, seed=3)
+    assert np.all(np.diff(m.row_ptr) == 30)
+    for i in range(m.nrows):
+        assert np.array_equal(m.col[m.row_ptr[i]:m.row_ptr[i + 1]], np.arange(30))
