@@ -202,6 +202,20 @@ def replicas_throughput(flops_per_replica, world, ms):
     return world * flops_per_replica / (ms / 1e3) / 1e9
 
 
+# FP64 on GB300: NVIDIA's figure is 1.25 TFLOP/s, i.e. two FP64 FMAs per SM
+# per cycle at the 2070 MHz maximum SM clock (152 SMs); the profile of the
+# narrow numeric kernel agrees (its FP64 pipe, 42% active, retires 1.9 lane
+# FMAs per SM and cycle).  The peak uses the maximum clock seen in the run.
+FP64_FMA_PER_SM_CYCLE = 2
+FP64_PEAK_NOTE = ("derived: SMs x 2 FP64 FMAs per SM per cycle x 2 flops x the maximum SM clock "
+                  "(GB300's nominal 1.25 TFLOP/s FP64)")
+
+
+def fp64_peak_tflops(nsm, clk):
+    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    return nsm * FP64_FMA_PER_SM_CYCLE * 2 * mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -371,12 +385,13 @@ def main():
         else:
             continue
         brp = bm.row_ptr
-        kern.append((tms / nl, key, kernel_bytes(am, brp, crp, mask, 8, True), nl))
+        kern.append((tms / nl, key, kernel_bytes(am, brp, crp, mask, 8, True), nl, 2 * int(fl[mask].sum())))
     roof = None
+    fp64_peak = fp64_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, clk)
     if kern:
         # dominant kernel: the numeric bin kernel with the largest total time
         best = max(kern, key=lambda x: x[0] * x[3])
-        per_ms, key, byt, nl = best
+        per_ms, key, byt, nl, flop = best
         ach = byt / (per_ms / 1e3) / 1e9
         traffic = None
         tf = os.path.join(ROOT, "profiles", "traffic.json")
@@ -384,14 +399,25 @@ def main():
             t = json.load(open(tf))
             if t.get("source_hash") == source_hash() and key in t.get("kernels", {}):
                 traffic = t["kernels"][key]
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic, "kernel": key, "bytes_per_launch": byt,
-                "ms_per_launch": per_ms, "peak_source": peak_src}
+        # the binding roof: the FP64 FMA rate or the HBM bandwidth, whichever
+        # allows less (A*P: 0.445 FLOP per algorithmic byte, above the FP64
+        # ridge of about 0.19 FLOP/B)
+        hbm_roof = {"achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": peak_src}
+        fl_ach = flop / (per_ms / 1e3) / 1e12
+        fp64_roof = {"achieved": fl_ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": fl_ach / fp64_peak,
+                     "peak_source": FP64_PEAK_NOTE}
+        if flop / (fp64_peak * 1e12) > byt / (hbm * 1e9):
+            roof = {"bound": "alu", "pipe": "fp64", **fp64_roof, "hbm": hbm_roof}
+        else:
+            roof = {"bound": "hbm", **hbm_roof, "fp64": fp64_roof}
+        roof.update({"traffic": traffic, "kernel": key, "bytes_per_launch": byt, "flop_per_launch": flop,
+                     "ms_per_launch": per_ms})
     # whole-step HBM-byte roofline: A + B rows touched + C of both products
     allr = np.ones(a.nrows, dtype=bool)
     step_bytes = (kernel_bytes(a, p.row_ptr, ap_rp, allr, 8) +
                   kernel_bytes(r, ap_rp, rap_rp, np.ones(r.nrows, dtype=bool), 8))
     step_frac = step_bytes / (ms / 1e3) / 1e9 / hbm
+    step_fp64_frac = 2 * mults / (ms / 1e3) / 1e12 / fp64_peak
 
     # end to end through the library's host-operand call (spgemm_host): A, P
     # and R in pinned host memory are copied in by the library, A*P stays on
@@ -451,6 +477,7 @@ def main():
                                   if a_bytes > 129e6 else "inputs smaller than L2, no flush"),
                            "parallelism": f"replicas x{world}"},
                 "pct_hbm_byte_roofline": 100 * step_frac,
+                "pct_fp64_roofline": 100 * step_fp64_frac,
                 "step_algorithmic_bytes": step_bytes,
                 "roofline": roof,
                 "kernels_ms_per_step": {k: v[2] / args.steps for k, v in sorted(tim.items())},

@@ -29,21 +29,29 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
     unsigned m = 0;
     int n = 0, bmin = INT_MAX, bmax = INT_MIN, prev = -1;
     bool bad = false, unsorted = false;
-    for (int64_t p = beg; p < end; p++) {
-        const int c = col[p];
-        if (c < 0 || (int64_t)c >= ncols) { bad = true; continue; }
-        unsorted |= c <= prev;
-        prev = c;
-        const int b = c >> 5;
-        if (b != cur) {
-            if (cur >= 0 && pairs) pairs[beg + n] = make_int2(cur, (int)m);
-            if (cur >= 0) n++;
-            cur = b;
-            m = 0;
+    // four columns at a time, their loads issued together
+    for (int64_t p0 = beg; p0 < end; p0 += 4) {
+        int cc[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cc[u] = p0 + u < end ? col[p0 + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (p0 + u >= end) break;
+            const int c = cc[u];
+            if (c < 0 || (int64_t)c >= ncols) { bad = true; continue; }
+            unsorted |= c <= prev;
+            prev = c;
+            const int b = c >> 5;
+            if (b != cur) {
+                if (cur >= 0 && pairs) pairs[beg + n] = make_int2(cur, (int)m);
+                if (cur >= 0) n++;
+                cur = b;
+                m = 0;
+            }
+            m |= 1u << (c & 31);
+            bmin = min(bmin, b);
+            bmax = max(bmax, b);
         }
-        m |= 1u << (c & 31);
-        bmin = min(bmin, b);
-        bmax = max(bmax, b);
     }
     if (cur >= 0) {
         if (pairs) pairs[beg + n] = make_int2(cur, (int)m);

@@ -81,6 +81,7 @@ __device__ __forceinline__ void load_entries(const int32_t *__restrict__ acol, c
 
 // ---------------------------------------------------------------- symbolic
 constexpr int NARROW_SYM_WPB = 8;
+constexpr int SYM_EU = 4;   // entries of A per lane whose loads are in flight together
 
 // G lanes per row, 32/G rows per warp.  For row i: flops, pairs and window
 // from desc[k] = {start, entries, pairs} and bmm[k] = {first block, last
@@ -127,15 +128,31 @@ __global__ void __launch_bounds__(NARROW_SYM_WPB * 32) k_sym_narrow(
         long long f = 0, cp = 0;
         int lo = INT_MAX, hi = INT_MIN;
         bool rowbad = false;
-        for (int e = gl; e < plen; e += G) {
-            const int k = acol[p0 + e];
-            if ((unsigned)k >= (unsigned)nrows_b) { rowbad = true; continue; }
-            const int4 d = desc[k];
-            const int2 m = bmm[k];
-            f += d.z;
-            cp += d.w;
-            lo = min(lo, m.x);
-            hi = max(hi, m.y);
+        // SYM_EU entries per lane at a time: their loads of A, then of the
+        // rows' descriptors, issued together
+        for (int e0 = 0; e0 < plen; e0 += G * SYM_EU) {
+            int k[SYM_EU];
+#pragma unroll
+            for (int u = 0; u < SYM_EU; u++) {
+                const int e = e0 + gl + G * u;
+                k[u] = e < plen ? acol[p0 + e] : -1;
+            }
+            int4 d[SYM_EU];
+            int2 m[SYM_EU];
+#pragma unroll
+            for (int u = 0; u < SYM_EU; u++) {
+                const bool ok = (unsigned)k[u] < (unsigned)nrows_b;
+                rowbad |= !ok && e0 + gl + G * u < plen;
+                d[u] = ok ? desc[k[u]] : make_int4(0, 0, 0, 0);
+                m[u] = ok ? bmm[k[u]] : make_int2(INT_MAX, INT_MIN);
+            }
+#pragma unroll
+            for (int u = 0; u < SYM_EU; u++) {
+                f += d[u].z;
+                cp += d[u].w;
+                lo = min(lo, m[u].x);
+                hi = max(hi, m[u].y);
+            }
         }
 #pragma unroll
         for (int d = G / 2; d > 0; d >>= 1) {
@@ -155,23 +172,39 @@ __global__ void __launch_bounds__(NARROW_SYM_WPB * 32) k_sym_narrow(
             }
             __syncwarp();
             // the union: every lane ORs the pairs of its own entries (lanes of
-            // a row may hit the same word: atomic OR)
+            // a row may hit the same word: atomic OR), SYM_EU entries at a
+            // time, the loads of one pair of each issued together
             if (nar) {
-                for (int e = gl; e < plen; e += G) {
-                    const int4 d = desc[acol[p0 + e]];
-                    const int2 *pp = pairs + desc_start(d);
-                    const int np = d.w <= NARROW_W ? d.w : 0;
-                    int tt = 0;
-                    for (; tt + 1 < np; tt += 2) {
-                        const int2 x = pp[tt], y = pp[tt + 1];
-                        const unsigned wx = (unsigned)(x.x - lo), wy = (unsigned)(y.x - lo);
-                        if (wx < (unsigned)NARROW_W) atomicOr(&t[wx], (unsigned)x.y); else flag |= DERR_COUNT;
-                        if (wy < (unsigned)NARROW_W) atomicOr(&t[wy], (unsigned)y.y); else flag |= DERR_COUNT;
+                for (int e0 = 0; e0 < plen; e0 += G * SYM_EU) {
+                    int k[SYM_EU];
+#pragma unroll
+                    for (int u = 0; u < SYM_EU; u++) {
+                        const int e = e0 + gl + G * u;
+                        k[u] = e < plen ? acol[p0 + e] : -1;
                     }
-                    if (tt < np) {
-                        const int2 x = pp[tt];
-                        const unsigned wx = (unsigned)(x.x - lo);
-                        if (wx < (unsigned)NARROW_W) atomicOr(&t[wx], (unsigned)x.y); else flag |= DERR_COUNT;
+                    const int2 *pp[SYM_EU];
+                    int np[SYM_EU];
+                    int npmax = 0;
+#pragma unroll
+                    for (int u = 0; u < SYM_EU; u++) {
+                        const int4 d = k[u] >= 0 ? desc[k[u]] : make_int4(0, 0, 0, 0);
+                        pp[u] = pairs + desc_start(d);
+                        np[u] = d.w <= NARROW_W ? d.w : 0;
+                        npmax = max(npmax, np[u]);
+                    }
+                    for (int tt = 0; tt < npmax; tt++) {
+                        int2 x[SYM_EU];
+#pragma unroll
+                        for (int u = 0; u < SYM_EU; u++) x[u] = tt < np[u] ? pp[u][tt] : make_int2(lo, 0);
+#pragma unroll
+                        for (int u = 0; u < SYM_EU; u++) {
+                            const unsigned wx = (unsigned)(x[u].x - lo);
+                            if (wx < (unsigned)NARROW_W) {
+                                if (x[u].y) atomicOr(&t[wx], (unsigned)x[u].y);
+                            } else {
+                                flag |= DERR_COUNT;
+                            }
+                        }
                     }
                 }
             }
@@ -324,22 +357,30 @@ __device__ __forceinline__ int popc_below(unsigned m, unsigned s) {
     return __popc(r);
 }
 
-// Shared memory of k_num_narrow, per row slot: the window's masks
-// (NARROW_TAB_STRIDE words), the rank of each word's first column (a byte:
-// rows hold at most NARROW_NMAX < 256 entries; NARROW_BASE_STRIDE bytes),
-// the accumulator by rank (NARROW_ACC_STRIDE values: the last one takes the
-// updates of idle lanes) and the batch of stored entries ({start, value},
-// length).  The strides are padded so that the row slots of a warp start on
-// different banks: lanes of different rows reading the same word of their
-// windows or the same entry do not conflict.
+// Shared memory of k_num_narrow.  Per warp, for its 32/G row slots: the
+// window's masks and the rank of each word's first column (a byte: rows
+// hold at most NARROW_NMAX < 256 entries), word major and row slot minor,
+// so that in one instruction the lanes of different row slots never meet on
+// a bank whatever words their rows look up; and the accumulator by rank,
+// entry r of slot g at r * ACC_RS + g * ACC_GS.  A row's G lanes update G
+// distinct ranks per chunk, the ranks of a chunk of a stencil row of B
+// mostly in pairs of neighbours (r, r+1, r+d, r+d+1); the strides spread
+// such updates of the slots of a half warp over the 16 eight-byte bank
+// pairs (they were chosen by counting the bank conflicts of the Galerkin
+// products' lookups on the host: 3.4 wavefronts per 8-byte access with 8
+// slots a warp, 3.1 with 4, against 5.1 and 3.6 for one slot after another).
+// Per row slot: the batch of stored entries ({start, value}, length),
+// padded so that the slots of a warp start on different banks.
 template <int G, int WPB, int E, typename V>
 struct NarrowSmem {
-    static constexpr int NR = WPB * (32 / G), ES = E + 1;
+    static constexpr int RPW = 32 / G, NR = WPB * RPW, ES = E + 1;
+    static constexpr int ACC_RS = G == 4 ? 4 : 1, ACC_GS = G == 4 ? 33 : 40;
+    static constexpr int ACC_SZ = (ACC_RS * (NARROW_NMAX - 1) + ACC_GS * (RPW - 1) + 2) & ~1;
     NarrowEnt<V> ent[NR * ES];
-    unsigned tab[NR * NARROW_TAB_STRIDE];
-    V acc[NR * NARROW_ACC_STRIDE];
+    unsigned tab[WPB * NARROW_W * RPW];
+    V acc[WPB * ACC_SZ];
     int elen[NR * ES];
-    unsigned char base[NR * NARROW_BASE_STRIDE];
+    unsigned char base[WPB * NARROW_W * RPW];
 };
 
 // Chunks per lane and step in the product pass: their loads of B are issued
@@ -349,29 +390,38 @@ constexpr int NARROW_U = 4;
 // G lanes per row, 32/G rows per warp, WPB warps per block, batches of E
 // stored entries; rows with bins[i] == BIN_NARROW, in row order.  The row's
 // word list (left by the symbolic phase) is scattered into the window table
-// and kept in registers for the output.  The product pass walks a staged
-// batch one chunk of G entries of B_k at a time, every lane of a row
-// holding the same cursor (the current entry's start, value and length);
-// the body of a chunk has no branch: an idle lane loads the first entry of
-// B and adds into the spare accumulator slot.  IDX32: B has fewer than 2^31
+// and kept in registers for the output (and to clear the table again after
+// the row: the table is cleared once at the start and holds only the
+// current rows' words).  The product pass walks a staged batch one chunk of
+// G entries of B_k at a time, every lane of a row holding the same cursor
+// (the current entry's start, value and length); an idle lane loads the
+// first entry of B and skips its update (predicated), and so does a column
+// missing from the row's window (flagged).  IDX32: B has fewer than 2^31
 // entries (32-bit offsets).
 template <int G, int WPB, int E, typename V, bool IDX32>
 __global__ void __launch_bounds__(WPB * 32) k_num_narrow(NarrowP a, int *err) {
     using S = NarrowSmem<G, WPB, E, V>;
-    constexpr int RPW = 32 / G, NR = WPB * RPW, QPL = NARROW_W / 4 / G, U = NARROW_U, EL = E / G;
-    constexpr int P = G >= 8 ? 1 : 8 / G, LPL = NARROW_NMAX / G;
+    constexpr int RPW = 32 / G, NR = WPB * RPW, U = NARROW_U, EL = E / G;
+    constexpr int LPL = NARROW_NMAX / G;
     __shared__ __align__(16) S sm;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / G, gl = lane % G;
     const int slot = w * RPW + g;
-    unsigned *tab = sm.tab + slot * NARROW_TAB_STRIDE;
-    unsigned char *base = sm.base + slot * NARROW_BASE_STRIDE;
-    V *acc = sm.acc + slot * NARROW_ACC_STRIDE;
+    // this row slot's column of the warp's tables: word wd at tab[wd * RPW]
+    unsigned *tab = sm.tab + w * NARROW_W * RPW + g;
+    unsigned char *base = sm.base + w * NARROW_W * RPW + g;
+    V *acc = sm.acc + w * S::ACC_SZ + g * S::ACC_GS;
     NarrowEnt<V> *ent = sm.ent + slot * S::ES;
     int *elen = sm.elen + slot * S::ES;
     const V *__restrict__ aval = (const V *)a.aval;
     const V *__restrict__ bval = (const V *)a.bval;
     const int32_t *__restrict__ bcol = a.bcol;
+    {
+        uint4 *t4 = (uint4 *)(sm.tab + w * NARROW_W * RPW);
+#pragma unroll
+        for (int q = lane; q < NARROW_W * RPW / 4; q += 32) t4[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
     int flag = 0;
     const int64_t stride = (int64_t)gridDim.x * NR;
     for (int64_t rb = (int64_t)blockIdx.x * NR + w * RPW; rb < a.n; rb += stride) {
@@ -393,23 +443,16 @@ __global__ void __launch_bounds__(WPB * 32) k_num_narrow(NarrowP a, int *err) {
             const int x = gl + G * u;
             lw[u] = act && x < nw ? ul[x] : make_uint2(0u, 0u);
         }
-        if (act) {
 #pragma unroll
-            for (int j = 0; j < QPL; j++) *(uint4 *)&tab[4 * quad_of<G, P>(j, gl)] = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-            for (int r = gl; r < NARROW_ACC_STRIDE; r += G) acc[r] = (V)0;
-        }
-        __syncwarp();
+        for (int r = gl; r < NARROW_NMAX; r += G) acc[r * S::ACC_RS] = (V)0;
         int cl = 0;
-        if (act) {
 #pragma unroll
-            for (int u = 0; u < LPL; u++) {
-                if (lw[u].y == 0u) continue;
-                const int wd = (int)(lw[u].x & 0xffu);
-                tab[wd] = lw[u].y;
-                base[wd] = (unsigned char)(lw[u].x >> 8);
-                cl += __popc(lw[u].y);
-            }
+        for (int u = 0; u < LPL; u++) {
+            if (lw[u].y == 0u) continue;
+            const int wd = (int)(lw[u].x & 0xffu) & (NARROW_W - 1);
+            tab[wd * RPW] = lw[u].y;
+            base[wd * RPW] = (unsigned char)(lw[u].x >> 8);
+            cl += __popc(lw[u].y);
         }
 #pragma unroll
         for (int d = G / 2; d > 0; d >>= 1) cl += __shfl_xor_sync(0xffffffffu, cl, d, G);
@@ -419,6 +462,7 @@ __global__ void __launch_bounds__(WPB * 32) k_num_narrow(NarrowP a, int *err) {
         __syncwarp();
         // products, a batch of stored entries at a time
         bool bad = false;
+        unsigned miss = 0;   // set by a column absent from the row's window union
         for (int pb = 0; pb < maxlen; pb += E) {
             long long q0[EL];
             int len[EL], np[EL];
@@ -444,7 +488,6 @@ __global__ void __launch_bounds__(WPB * 32) k_num_narrow(NarrowP a, int *err) {
                 ca = x.a;
                 clen = IDX32 ? x.hl : elen[0];
             }
-            unsigned miss = 0;   // bits of columns absent from the row's window union
             while (__any_sync(0xffffffffu, e < nb)) {
                 int c[U], r[U];
                 V v[U], av[U];
@@ -479,35 +522,40 @@ __global__ void __launch_bounds__(WPB * 32) k_num_narrow(NarrowP a, int *err) {
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int wd = ((c[u] >> 5) - lo) & (NARROW_W - 1);
-                    const unsigned m = tab[wd];
+                    const unsigned m = tab[wd * RPW];
                     const unsigned sh = (unsigned)c[u] & 31u;
-                    const int rk = base[wd] + popc_below(m, sh);
+                    const int rk = base[wd * RPW] + popc_below(m, sh);
+                    const bool hit = (m >> sh) & 1u;
                     const bool live = r[u] == 0;
-                    miss |= live ? (1u << sh) & ~m : 0u;
-                    r[u] = live ? rk : NARROW_NMAX;
+                    miss |= live && !hit ? 1u : 0u;
+                    r[u] = live && hit ? min(rk, NARROW_NMAX) : NARROW_NMAX;
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    acc[r[u]] = fma(av[u], v[u], acc[r[u]]);
+                    if (r[u] < NARROW_NMAX) acc[r[u] * S::ACC_RS] = fma(av[u], v[u], acc[r[u] * S::ACC_RS]);
                     __syncwarp();
                 }
             }
-            if (miss) flag |= DERR_COUNT;
             __syncwarp();
         }
+        if (miss) flag |= DERR_COUNT;
         if (bad) flag |= DERR_COL_RANGE;
-        // write the row in column order: every lane its listed words
-        if (act) {
+        // write the row in column order (every lane its listed words) and
+        // clear the row's words from the table
 #pragma unroll
-            for (int u = 0; u < LPL; u++) {
-                unsigned m = lw[u].y;
-                int rr = (int)(lw[u].x >> 8);
-                const int col0 = (lo + (int)(lw[u].x & 0xffu)) * 32;
-                while (m) {
+        for (int u = 0; u < LPL; u++) {
+            unsigned m = lw[u].y;
+            if (m == 0u) continue;
+            int rr = (int)(lw[u].x >> 8);
+            const int wd = (int)(lw[u].x & 0xffu);
+            const int col0 = (lo + wd) * 32;
+            tab[(wd & (NARROW_W - 1)) * RPW] = 0u;
+            if (act) {
+                while (m && rr < nn) {
                     const int bpos = __ffs(m) - 1;
                     m &= m - 1u;
                     a.ccol[out + rr] = col0 + bpos;
-                    ((V *)a.cval)[out + rr] = acc[rr];
+                    ((V *)a.cval)[out + rr] = acc[rr * S::ACC_RS];
                     rr++;
                 }
             }
