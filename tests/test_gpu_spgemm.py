@@ -359,3 +359,62 @@ def test_compression_long_rows(h):
             r1 = runs[t + 1] if t + 1 < len(runs) else len(c)
             assert got[t, 0] == bl[r0]
             assert got[t, 1] == np.bitwise_or.reduce((np.uint64(1) << (c[r0:r1] % 32).astype(np.uint64))).astype(np.uint32)
+
+
+@pytest.mark.parametrize("mean_len", [8, 40])
+def test_compression_row_lengths(h, mean_len):
+    """Matrices whose rows average a dozen or more entries: sorted rows of
+    lengths around the four-column load steps and the 32-entry steps of the
+    long-row kernel (empty, 1, 15, 16, 17, 31, 32, 33, 65, 128, and rows
+    longer than 128 left to the warp-per-row kernel) with dense runs across
+    block edges, against the canonical compression; the same rows permuted,
+    against the runs of equal blocks in storage order; then a product
+    through these descriptors."""
+    rng = np.random.default_rng(mean_len)
+    lens = [0, 1, 15, 16, 17, 31, 32, 33, 65, 128, 129, 300]
+    nrow = 400
+    row_len = np.array([lens[(i // 8) % len(lens)] if i % 8 == 0 else int(rng.integers(mean_len - 4, mean_len + 5))
+                        for i in range(nrow)])
+    ncols = 20000
+    rows, cols = [], []
+    for i, L in enumerate(row_len):
+        if L == 0:
+            continue
+        dense = np.arange(L // 2) + 40 * (i % 7) + 3          # runs spanning block edges
+        sparse = 3000 + rng.choice(ncols - 3000, size=L - L // 2, replace=False)
+        c = np.unique(np.concatenate([dense, sparse]))
+        rows += [i] * len(c)
+        cols += c.tolist()
+    key = np.array(rows, dtype=np.int64) * ncols + np.array(cols, dtype=np.int64)
+    b = I.Csr(nrow, ncols, np.concatenate([[0], np.cumsum(np.bincount(key // ncols, minlength=nrow))]).astype(np.int64),
+              (key % ncols).astype(np.int32), np.ones(len(key)))
+    cnt, pairs = h.compress(to_dev(b))
+    rp, blk, mask = oracle.compress_rows(b)
+    cnt = cnt.cpu().numpy()
+    pairs = pairs.cpu().numpy().view(np.uint32)
+    assert np.array_equal(cnt, np.diff(rp))
+    for k in range(b.nrows):
+        got = pairs[b.row_ptr[k]:b.row_ptr[k] + cnt[k]]
+        assert np.array_equal(got[:, 0], blk[rp[k]:rp[k + 1]].astype(np.uint32))
+        assert np.array_equal(got[:, 1], mask[rp[k]:rp[k + 1]])
+    order = np.lexsort((I.uniform01(np.arange(b.nnz, dtype=np.uint64), 23),
+                        np.repeat(np.arange(nrow), np.diff(b.row_ptr))))
+    bu = I.Csr(nrow, ncols, b.row_ptr, b.col[order], b.val)
+    cnt2, pairs2 = h.compress(to_dev(bu))
+    cnt2 = cnt2.cpu().numpy(); pairs2 = pairs2.cpu().numpy().view(np.uint32)
+    for k in range(bu.nrows):
+        c = bu.col[bu.row_ptr[k]:bu.row_ptr[k + 1]].astype(np.int64)
+        if len(c) == 0:
+            assert cnt2[k] == 0
+            continue
+        bl = c >> 5
+        runs = np.concatenate([[0], np.nonzero(bl[1:] != bl[:-1])[0] + 1])
+        assert cnt2[k] == len(runs)
+        got = pairs2[bu.row_ptr[k]:bu.row_ptr[k] + cnt2[k]]
+        for t, r0 in enumerate(runs):
+            r1 = runs[t + 1] if t + 1 < len(runs) else len(c)
+            assert got[t, 0] == bl[r0]
+            assert got[t, 1] == np.bitwise_or.reduce((np.uint64(1) << (c[r0:r1] % 32).astype(np.uint64))).astype(np.uint32)
+    # and the product through these descriptors
+    a = I.random_csr(150, nrow, 0.03, 29, shuffle_cols=True)
+    assert_matches(h.spgemm(to_dev(a), to_dev(bu)), oracle.spgemm(a, bu), "f64")
