@@ -59,7 +59,7 @@ typedef enum spgemm_status {
     SPGEMM_ERR_INDEX = 3,        /* column index out of range, or offsets/counts overflow */
     SPGEMM_ERR_NOMEM = 4,        /* a device or pinned allocation failed */
     SPGEMM_ERR_BUDGET = 5,       /* chunked: budget below the minimum working set */
-    SPGEMM_ERR_TIMEOUT = 6,      /* a bounded wait ran out */
+    SPGEMM_ERR_TIMEOUT = 6,      /* a host wait ran out (SPGEMM_OPT_WAIT_LIMIT_MS) */
     SPGEMM_ERR_CUDA = 7,         /* a CUDA runtime call failed */
     SPGEMM_ERR_NOT_SYMBOLIC = 8, /* numeric called without a matching symbolic */
     SPGEMM_ERR_INTERNAL = 9      /* a device-side bound was exceeded (hash probe limit) */
@@ -146,6 +146,13 @@ SPGEMM_API int spgemm_numeric(spgemm_handle handle, int dtype, const spgemm_csr 
  *    can run one more part ahead of the multiplications, with parts a
  *    third smaller).  Results are identical; only the plan (parts, copy
  *    bytes) and the overlap change.
+ *  SPGEMM_OPT_WAIT_LIMIT_MS (>= 0, default 0 = no limit): the longest the
+ *    host waits inside a call for the device (the counts of
+ *    spgemm_symbolic, the state read by spgemm_check, the column range of a
+ *    part in spgemm_chunked_numeric).  A wait that runs out returns
+ *    SPGEMM_ERR_TIMEOUT; the work already queued keeps running, so the
+ *    caller synchronises its stream before it reuses or frees the call's
+ *    buffers, and runs spgemm_symbolic again before spgemm_numeric.
  * spgemm_autotune picks lanes, small-row cap and slot factor by timing. */
 typedef enum spgemm_option {
     SPGEMM_OPT_F64_NATIVE = 1,
@@ -156,7 +163,8 @@ typedef enum spgemm_option {
     SPGEMM_OPT_NARROW = 6,
     SPGEMM_OPT_LANES_NARROW_SYMBOLIC = 7,
     SPGEMM_OPT_LANES_NARROW_NUMERIC = 8,
-    SPGEMM_OPT_CHUNK_BUFFERS = 9
+    SPGEMM_OPT_CHUNK_BUFFERS = 9,
+    SPGEMM_OPT_WAIT_LIMIT_MS = 10
 } spgemm_option;
 SPGEMM_API int spgemm_set_option(spgemm_handle handle, int option, int64_t value);
 

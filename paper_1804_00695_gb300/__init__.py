@@ -27,6 +27,7 @@ F32, F64 = 0, 1
 NBINS = 8
 OPT_F64_NATIVE, OPT_LANES_NUMERIC, OPT_LANES_SYMBOLIC, OPT_SMALL_CAP, OPT_SLOT_FACTOR = 1, 2, 3, 4, 5
 OPT_NARROW, OPT_LANES_NARROW_SYMBOLIC, OPT_LANES_NARROW_NUMERIC, OPT_CHUNK_BUFFERS = 6, 7, 8, 9
+OPT_WAIT_LIMIT_MS = 10
 BIN_NARROW = 7
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_DIM", 3: "ERR_INDEX", 4: "ERR_NOMEM", 5: "ERR_BUDGET",
           6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_NOT_SYMBOLIC", 9: "ERR_INTERNAL"}

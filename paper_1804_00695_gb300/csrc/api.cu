@@ -1,8 +1,10 @@
 // C ABI: handle, workspace and the two phases of Section 2.1.
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 #include "internal.cuh"
 
@@ -88,6 +90,7 @@ struct spgemm_handle_s {
     static constexpr int EV_ORDER = CHUNK_EVENTS, EV_HOST = CHUNK_EVENTS + 3;
     cudaEvent_t ev[CHUNK_EVENTS + 5] = {};
     int chunk_nbuf = 2;                  // buffers per streamed operand of the chunked numeric call
+    int64_t wait_ms = 0;                 // limit of the host's waits (0: none)
     std::vector<int64_t> zeros;   // offsets of an empty C (chunked symbolic plan)
     int *host_mm = nullptr;       // pinned, column ranges of A parts (chunked numeric)
     ChunkStats cstats;
@@ -168,10 +171,43 @@ static int check_csr(const spgemm_csr *m, const char *name, bool need_vals) {
     return SPGEMM_OK;
 }
 
+template <typename Q>
+static int poll_until(Q query, int64_t wait_ms, const char *what) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = query();
+        if (e == cudaSuccess) return SPGEMM_OK;
+        if (e != cudaErrorNotReady) {
+            set_error("%s: %s", what, cudaGetErrorString(e));
+            return SPGEMM_ERR_CUDA;
+        }
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(wait_ms)) {
+            set_error("%s: the device work did not finish within %lld ms", what, (long long)wait_ms);
+            return SPGEMM_ERR_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+int sg::host_wait_stream(cudaStream_t s, int64_t wait_ms, const char *what) {
+    if (wait_ms <= 0) {
+        SG_CUDA(cudaStreamSynchronize(s));
+        return SPGEMM_OK;
+    }
+    return poll_until([s] { return cudaStreamQuery(s); }, wait_ms, what);
+}
+
+int sg::host_wait_event(cudaEvent_t e, int64_t wait_ms, const char *what) {
+    if (wait_ms <= 0) {
+        SG_CUDA(cudaEventSynchronize(e));
+        return SPGEMM_OK;
+    }
+    return poll_until([e] { return cudaEventQuery(e); }, wait_ms, what);
+}
+
 static int fetch_state(spgemm_handle h, cudaStream_t s) {
     SG_CUDA(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    SG_CUDA(cudaStreamSynchronize(s));
-    return SPGEMM_OK;
+    return host_wait_stream(s, h->wait_ms, "waiting for the device state");
 }
 
 static int device_errors(int err) {
@@ -504,6 +540,7 @@ static int chunk_env(spgemm_handle h, size_t budget, cudaStream_t s, ChunkEnv &e
     env.s_out = h->s_out;
     for (int k = 0; k < CHUNK_EVENTS; k++) env.ev[k] = h->ev[k];
     env.nbuf = h->chunk_nbuf;
+    env.wait_ms = h->wait_ms;
     env.err = &h->dstate->err;
     env.zeros = &h->zeros;
     env.host_mm = h->host_mm;
@@ -1010,6 +1047,10 @@ int spgemm_set_option(spgemm_handle h, int option, int64_t value) {
         case SPGEMM_OPT_CHUNK_BUFFERS:
             if (value != 2 && value != 3) { set_error("chunk buffers must be 2 or 3"); return SPGEMM_ERR_ARG; }
             h->chunk_nbuf = (int)value;
+            return SPGEMM_OK;
+        case SPGEMM_OPT_WAIT_LIMIT_MS:
+            if (value < 0) { set_error("wait limit must be >= 0 ms"); return SPGEMM_ERR_ARG; }
+            h->wait_ms = value;
             return SPGEMM_OK;
         default: set_error("unknown option %d", option); return SPGEMM_ERR_ARG;
     }

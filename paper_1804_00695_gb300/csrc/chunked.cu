@@ -1082,7 +1082,7 @@ int chunked_numeric(ChunkEnv &env, int dtype, const spgemm_csr &A, const spgemm_
             } else {
                 // the host waits for this part's column range only; the
                 // device still has the previous part's products queued
-                SG_CUDA(cudaEventSynchronize(ev_ain[slot]));
+                SG_TRY(host_wait_event(ev_ain[slot], env.wait_ms, "chunked numeric (column range of a part)"));
                 lo_c = hmm[2 * slot];
                 hi_c = hmm[2 * slot + 1];
                 // lo_c == INT_MAX only for a part with no entries (hi_c

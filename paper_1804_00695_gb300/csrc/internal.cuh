@@ -315,6 +315,13 @@ struct ChunkCache {
 // CHUNK_MAX_BUF (one per buffer of a group), the symbolic call the first 8.
 constexpr int CHUNK_MAX_BUF = 3;
 constexpr int CHUNK_EVENTS = 5 * CHUNK_MAX_BUF;
+// Host waits of the library (for a count, a copied-back state or a part's
+// column range): wait_ms <= 0 waits as long as it takes; otherwise the wait
+// polls and gives up after wait_ms milliseconds with SPGEMM_ERR_TIMEOUT (the
+// queued device work keeps running).
+int host_wait_stream(cudaStream_t s, int64_t wait_ms, const char *what);
+int host_wait_event(cudaEvent_t e, int64_t wait_ms, const char *what);
+
 struct ChunkEnv {
     Ctx *ctx = nullptr;
     ChunkCache *cache = nullptr;
@@ -322,6 +329,7 @@ struct ChunkEnv {
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev[CHUNK_EVENTS] = {};
     int nbuf = 2;                 // buffers per streamed operand: 2 (double) or 3 (triple)
+    int64_t wait_ms = 0;          // limit of the host's waits (0: none)
     int *err = nullptr;
     std::vector<int64_t> *zeros = nullptr;   // host scratch: offsets of an empty C
     int *host_mm = nullptr;                  // pinned: column ranges of the A parts in the buffers

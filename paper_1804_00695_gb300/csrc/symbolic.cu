@@ -40,6 +40,17 @@ struct SymFirstLayout {
 // costs one load and one insertion.  Insertions are atomic (CAS on the key,
 // OR on the mask).  A row whose map fills up is marked crp[i+1] = -1 and
 // counted in its second-pass bin.
+// True when the analysis left no row for the first pass (every row empty,
+// of the widest bin or narrow: the histogram of the analysis, complete
+// before this kernel starts on the same stream); the kernel then returns
+// at once instead of reading every row's bin.
+__device__ __forceinline__ bool first_pass_empty(const DevState *st) {
+    long long m = 0;
+#pragma unroll
+    for (int b = 1; b < BIN_HUGE; b++) m += *(volatile const long long *)&st->sym_hist[b];
+    return m == 0;
+}
+
 template <int G>
 __global__ void __launch_bounds__(256) k_sym_first(
     int64_t n, const uint8_t *__restrict__ bins, const int64_t *__restrict__ arp,
@@ -59,6 +70,7 @@ __global__ void __launch_bounds__(256) k_sym_first(
     int *pre = reg + Lay::o_pre;
     const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
     const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
+    if (first_pass_empty(st)) return;
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
         const int64_t i = base + g;
         const int b = i < n ? bins[i] : 0;
@@ -173,6 +185,7 @@ __global__ void __launch_bounds__(256) k_sym_first_strided(
     int *pre = reg + Lay::o_pre;
     const unsigned lmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1);
     const int64_t stride = (int64_t)gridDim.x * WPB * RPW;
+    if (first_pass_empty(st)) return;
     for (int64_t base = ((int64_t)blockIdx.x * WPB + w) * RPW; base < n; base += stride) {
         const int64_t i = base + g;
         const int b = i < n ? bins[i] : 0;
