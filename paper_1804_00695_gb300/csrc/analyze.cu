@@ -14,29 +14,54 @@ namespace sg {
 // alongside: desc = {first entry (int64), entries, pairs} for the product
 // kernels, ana = {entries, pairs} for the analysis, and the row's first and
 // last block (minmax) for the span tests.
+//
+// A warp takes 32 consecutive rows.  When their entries together number at
+// most COMPRESS_STAGE, the warp first copies them into shared memory with
+// coalesced loads (a lane's row alone is a short run of addresses 32 rows
+// apart from its neighbours' in one load instruction), and every lane then
+// reads its row from there; otherwise every lane loads its own row.
 constexpr int64_t COMPRESS_LONG = 128;   // rows longer than this take a warp each
+constexpr int COMPRESS_STAGE = 1024;     // staged entries per warp
+constexpr int COMPRESS_WPB = 8;
 
-__global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp,
-                           const int32_t *__restrict__ col, int2 *__restrict__ pairs,
-                           int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
-                           int4 *__restrict__ desc, int2 *__restrict__ ana, int *err,
-                           int *unsorted_flag) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const int64_t beg = rp[r], end = rp[r + 1];
-    if (end - beg > COMPRESS_LONG) return;   // k_compress_long
+__global__ void __launch_bounds__(COMPRESS_WPB * 32) k_compress(
+    int64_t nrows, int64_t ncols, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+    int2 *__restrict__ pairs, int32_t *__restrict__ ccnt, int2 *__restrict__ minmax, int4 *__restrict__ desc,
+    int2 *__restrict__ ana, int *err, int *unsorted_flag, int *long_flag) {
+    __shared__ int stage_all[COMPRESS_WPB * COMPRESS_STAGE];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *stage = stage_all + w * COMPRESS_STAGE;
+    const int64_t r0 = ((int64_t)blockIdx.x * COMPRESS_WPB + w) * 32;
+    if (r0 >= nrows) return;
+    const int64_t r = r0 + lane;
+    const bool live = r < nrows;
+    const int64_t beg = live ? rp[r] : 0, end = live ? rp[r + 1] : 0;
+    const int64_t rlast = min(r0 + 32, nrows);
+    const int64_t wbeg = __shfl_sync(0xffffffffu, beg, 0);
+    const int64_t wend = rp[rlast];
+    const bool staged = wend - wbeg <= COMPRESS_STAGE;
+    if (staged) {
+        const int span = (int)(wend - wbeg);
+        for (int x = lane; x < span; x += 32) stage[x] = col[wbeg + x];
+    }
+    __syncwarp();
+    const bool lng = end - beg > COMPRESS_LONG;   // k_compress_long
+    if (lng && long_flag) *long_flag = 1;
+    if (!live || lng) return;
+    const int *src = staged ? stage + (beg - wbeg) : col + beg;
+    const int len = (int)(end - beg);
     int cur = -1;
     unsigned m = 0;
     int n = 0, bmin = INT_MAX, bmax = INT_MIN, prev = -1;
     bool bad = false, unsorted = false;
     // four columns at a time, their loads issued together
-    for (int64_t p0 = beg; p0 < end; p0 += 4) {
+    for (int p0 = 0; p0 < len; p0 += 4) {
         int cc[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) cc[u] = p0 + u < end ? col[p0 + u] : 0;
+        for (int u = 0; u < 4; u++) cc[u] = p0 + u < len ? src[p0 + u] : 0;
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            if (p0 + u >= end) break;
+            if (p0 + u >= len) break;
             const int c = cc[u];
             if (c < 0 || (int64_t)c >= ncols) { bad = true; continue; }
             unsorted |= c <= prev;
@@ -59,7 +84,6 @@ __global__ void k_compress(int64_t nrows, int64_t ncols, const int64_t *__restri
     }
     if (ccnt) ccnt[r] = n;
     if (minmax) minmax[r] = make_int2(bmin, bmax);
-    const int len = (int)(end - beg);
     if (desc) desc[r] = make_int4((int)(unsigned)(uint64_t)beg, (int)((uint64_t)beg >> 32), len, n);
     if (ana) ana[r] = make_int2(len, n);
     if (bad) atomicOr(err, DERR_COL_RANGE);
@@ -75,7 +99,9 @@ __global__ void k_compress_long(int64_t nrows, int64_t ncols, const int64_t *__r
                                 const int32_t *__restrict__ col, int2 *__restrict__ pairs,
                                 int32_t *__restrict__ ccnt, int2 *__restrict__ minmax,
                                 int4 *__restrict__ desc, int2 *__restrict__ ana, int *err,
-                                int *unsorted_flag) {
+                                int *unsorted_flag, const int *long_flag) {
+    // k_compress found no long row (the flag is cleared before it runs)
+    if (long_flag && *(volatile const int *)long_flag == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -166,17 +192,18 @@ __global__ void k_compress_long(int64_t nrows, int64_t ncols, const int64_t *__r
 }
 
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
-                    int2 *ana, int *err, Ctx &c, int *unsorted) {
+                    int2 *ana, int *err, Ctx &c, int *unsorted, int *long_flag) {
     if (M.nrows == 0) return SPGEMM_OK;
-    int64_t blocks = (M.nrows + 255) / 256;
+    int64_t blocks = (M.nrows + COMPRESS_WPB * 32 - 1) / (COMPRESS_WPB * 32);
     c.begin("compress", M.nrows);
-    k_compress<<<(unsigned)blocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
-                                                    ccnt, minmax, desc, ana, err, unsorted);
+    k_compress<<<(unsigned)blocks, COMPRESS_WPB * 32, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs,
+                                                    ccnt, minmax, desc, ana, err, unsorted, long_flag);
     c.end();
-    const int64_t wblocks = std::min<int64_t>((M.nrows + 255) / 256, (int64_t)c.nsm * 16);
+    // one resident wave (it returns at once when no row is long)
+    const int64_t wblocks = std::min<int64_t>((M.nrows + 255) / 256, resident_blocks(k_compress_long, 256, c.nsm));
     c.begin("compress_long", M.nrows);
     k_compress_long<<<(unsigned)wblocks, 256, 0, c.s>>>(M.nrows, M.ncols, M.row_ptr, M.col_idx, pairs, ccnt,
-                                                        minmax, desc, ana, err, unsorted);
+                                                        minmax, desc, ana, err, unsorted, long_flag);
     c.end();
     SG_CUDA(cudaGetLastError());
     return SPGEMM_OK;

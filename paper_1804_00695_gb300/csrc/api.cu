@@ -369,7 +369,7 @@ int spgemm_symbolic(spgemm_handle h, const spgemm_csr *A, const spgemm_csr *B, i
         const double mean_pairs = mean_alen * ((double)B->nnz / (double)(B->nrows > 0 ? B->nrows : 1)) * 0.6;
         const int gs = h->g_symbolic ? h->g_symbolic : lanes_for(mean_pairs / 64.0);
         SG_TRY(launch_compress(*B, pairs, ccnt, minmax, desc, ana, &h->dstate->err, c,
-                               &h->dstate->b_unsorted));
+                               &h->dstate->b_unsorted, &h->dstate->long_rows));
         h->sym_narrow_used = h->narrow;
         if (h->narrow) {
             // analysis and the narrow rows' counts in one pass; the first

@@ -44,7 +44,7 @@ struct DevState {          // lives in device memory, one per handle
     long long max_row_nnz;   // largest row of C (numeric binning)
     long long flops_total;   // products of the whole product (analysis)
     int b_unsorted;          // some row of B has columns out of ascending order
-    int pad2;
+    int long_rows;           // the compression met rows for its warp-per-row pass
     long long max_alen;      // longest row of A (analysis)
     unsigned long long triangles;   // spgemm_triangles: the count
 };
@@ -106,6 +106,18 @@ constexpr long long NARROW_PAIRS = 4096;
 constexpr int NARROW_TAB_STRIDE = NARROW_W + 4;
 constexpr int NARROW_BASE_STRIDE = NARROW_W + 4;
 constexpr int NARROW_ACC_STRIDE = NARROW_NMAX + 1;
+
+// Blocks of `kern` that fit on all SMs at once (at least one per SM): the
+// kernels that stride over their rows run one resident wave.
+template <typename K>
+static inline int64_t resident_blocks(K kern, int threads, int nsm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return (int64_t)per_sm * nsm;
+}
 
 // Adds this warp's per-bin row counts (bins held by the lanes where `has`)
 // to a shared histogram with one ballot per bin.
@@ -177,8 +189,11 @@ struct Ctx {
 // desc[k] = {row_ptr[k] low, high 32 bits, entries, pairs};
 // ana[k] = {entries, pairs}.  Any output may be NULL.
 // `unsorted` (may be null) is set to 1 if a row of M is not strictly ascending.
+// `long_flag` (may be null; device, cleared by the caller before the call)
+// is set to 1 if a row is long enough for the warp-per-row pass, which
+// otherwise returns at once; with null that pass tests every row.
 int launch_compress(const spgemm_csr &M, int2 *pairs, int32_t *ccnt, int2 *minmax, int4 *desc,
-                    int2 *ana, int *err, Ctx &c, int *unsorted = nullptr);
+                    int2 *ana, int *err, Ctx &c, int *unsorted = nullptr, int *long_flag = nullptr);
 __device__ __forceinline__ int64_t desc_start(int4 d) {
     return (int64_t)(((uint64_t)(unsigned)d.y << 32) | (uint64_t)(unsigned)d.x);
 }

@@ -290,18 +290,6 @@ __global__ void __launch_bounds__(NARROW_SYM_WPB * 32) k_sym_narrow(
     }
 }
 
-// Blocks of `kern` that fit on all SMs at once (at least one per SM): the
-// narrow kernels stride over the rows with one resident wave.
-template <typename K>
-static int64_t resident_blocks(K kern, int threads, int nsm) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    return (int64_t)per_sm * nsm;
-}
-
 template <int G>
 static int run_sym_narrow(const spgemm_csr &A, const spgemm_csr &B, const int4 *desc, const int2 *bmm,
                           const int2 *pairs, int64_t *flops, uint8_t *bins, int64_t *crp, int32_t *nlo,
@@ -363,29 +351,38 @@ __device__ __forceinline__ int popc_below(unsigned m, unsigned s) {
 // so that in one instruction the lanes of different row slots never meet on
 // a bank whatever words their rows look up; and the accumulator by rank,
 // entry r of slot g at r * ACC_RS + g * ACC_GS.  A row's G lanes update G
-// distinct ranks per chunk, the ranks of a chunk of a stencil row of B
-// mostly in pairs of neighbours (r, r+1, r+d, r+d+1); the strides spread
-// such updates of the slots of a half warp over the 16 eight-byte bank
-// pairs (they were chosen by counting the bank conflicts of the Galerkin
-// products' lookups on the host: 3.4 wavefronts per 8-byte access with 8
-// slots a warp, 3.1 with 4, against 5.1 and 3.6 for one slot after another).
-// Per row slot: the batch of stored entries ({start, value}, length),
-// padded so that the slots of a warp start on different banks.
-template <int G, int WPB, int E, typename V>
+// distinct ranks per chunk.  With four lanes a row, the slots lie 34
+// eight-byte words apart (ranks adjacent within a slot): 270 words a warp,
+// small enough for six blocks of four warps an SM (the earlier stride of
+// four words per rank and 33 per slot spread a stencil row's neighbouring
+// ranks over more banks, but its 356 words a warp left room for five
+// blocks; on the 128^3 Galerkin A*P the sixth block gains more than the
+// extra conflicts cost).
+// Per row slot: the batch of stored entries ({start, value}, length; the
+// lengths apart only when B has 2^31 entries or more), padded so that the
+// slots of a warp start on different banks.
+template <int G, int WPB, int E, typename V, bool IDX32>
 struct NarrowSmem {
     static constexpr int RPW = 32 / G, NR = WPB * RPW, ES = E + 1;
-    static constexpr int ACC_RS = G == 4 ? 4 : 1, ACC_GS = G == 4 ? 33 : 40;
+    static constexpr int ACC_RS = 1, ACC_GS = G == 4 ? 34 : 40;
     static constexpr int ACC_SZ = (ACC_RS * (NARROW_NMAX - 1) + ACC_GS * (RPW - 1) + 2) & ~1;
     NarrowEnt<V> ent[NR * ES];
     unsigned tab[WPB * NARROW_W * RPW];
     V acc[WPB * ACC_SZ];
-    int elen[NR * ES];
+    int elen[IDX32 ? 1 : NR * ES];
     unsigned char base[WPB * NARROW_W * RPW];
 };
 
 // Chunks per lane and step in the product pass: their loads of B are issued
-// before any of their updates.
-constexpr int NARROW_U = 4;
+// before any of their updates (three: with four, the registers of the
+// four-lane kernel leave room for five blocks an SM instead of six).
+constexpr int NARROW_U = 3;
+
+// Blocks an SM of the four-lane kernel: six (24 warps; 80 registers a
+// thread, 37.8 KB of shared memory a block).  The other lane counts leave
+// the register count to the compiler (a minimum of 0 blocks): with eight
+// lanes it takes 64 registers, eight blocks an SM.
+constexpr int NARROW_MINB4 = 6;
 
 // G lanes per row, 32/G rows per warp, WPB warps per block, batches of E
 // stored entries; rows with bins[i] == BIN_NARROW, in row order.  The row's
@@ -399,8 +396,8 @@ constexpr int NARROW_U = 4;
 // missing from the row's window (flagged).  IDX32: B has fewer than 2^31
 // entries (32-bit offsets).
 template <int G, int WPB, int E, typename V, bool IDX32>
-__global__ void __launch_bounds__(WPB * 32) k_num_narrow(NarrowP a, int *err) {
-    using S = NarrowSmem<G, WPB, E, V>;
+__global__ void __launch_bounds__(WPB * 32, G == 4 ? NARROW_MINB4 : 0) k_num_narrow(NarrowP a, int *err) {
+    using S = NarrowSmem<G, WPB, E, V, IDX32>;
     constexpr int RPW = 32 / G, NR = WPB * RPW, U = NARROW_U, EL = E / G;
     constexpr int LPL = NARROW_NMAX / G;
     __shared__ __align__(16) S sm;

@@ -513,7 +513,11 @@ static int run_first(const spgemm_csr &A, const uint8_t *bins, const int4 *desc,
                      int64_t *crp, DevState *st, Ctx &c) {
     constexpr int GPB = 256 / G;   // rows per block: 8 warps x 32/G rows
     int64_t blocks = (A.nrows + GPB - 1) / GPB;
-    const int64_t cap = (int64_t)c.nsm * 8 * 4;
+    // one resident wave striding over the rows: when the analysis left this
+    // pass no row, every block returns at once, and a wave costs one round
+    // of block launches where 32 blocks an SM cost several
+    const int64_t cap = G <= 8 ? resident_blocks(k_sym_first_strided<G>, 256, c.nsm)
+                               : resident_blocks(k_sym_first<G>, 256, c.nsm);
     blocks = blocks < cap ? blocks : cap;
     c.begin("symbolic.first", A.nrows);
     if (G <= 8)
