@@ -423,7 +423,10 @@ SPGEMM_API int spgemm_bin_of(int64_t keys, int64_t flops);
 
 /* Instrumentation.  spgemm_launch_count: kernels launched through this
  * handle since it was created.  spgemm_set_timing(h, 1) brackets every
- * kernel launch with CUDA events on its stream; spgemm_timings synchronises
+ * kernel launch with CUDA events on its stream, spgemm_set_timing(h, 2) only
+ * the launches of the numeric phase (labels "numeric..."), whose events then
+ * add less host work to a timed sequence of calls, and
+ * spgemm_set_timing(h, 0) none (other modes: SPGEMM_ERR_ARG); spgemm_timings synchronises
  * on those events and returns per-kernel totals (label "<phase>.<kernel>",
  * launches, rows processed, milliseconds) accumulated since the last
  * spgemm_reset_timings; *count = number of labels (up to cap written). */

@@ -501,8 +501,10 @@ class Handle:
         _check(_lib.spgemm_launch_count(self._h, C.byref(n)))
         return int(n.value)
 
-    def set_timing(self, on: bool = True):
-        _check(_lib.spgemm_set_timing(self._h, 1 if on else 0))
+    def set_timing(self, on=True):
+        """True / 1: events around every kernel; 2: numeric-phase kernels only;
+        False / 0: off."""
+        _check(_lib.spgemm_set_timing(self._h, int(on)))
 
     def timings(self) -> dict:
         """{label: (launches, rows, ms)} accumulated since the last reset."""

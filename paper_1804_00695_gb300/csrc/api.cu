@@ -23,7 +23,9 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 void Ctx::begin(const char *label, long long rows) {
     if (launches) (*launches)++;
+    open = false;
     if (!timing || !recs || *nrec >= cap) return;
+    if (timing == 2 && strncmp(label, "numeric", 7) != 0) return;
     TimingRec &r = recs[*nrec];
     if (!r.e0) {
         if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) {
@@ -34,13 +36,13 @@ void Ctx::begin(const char *label, long long rows) {
     r.label = label;
     r.rows = rows;
     cudaEventRecord(r.e0, s);
+    open = true;
 }
 
 void Ctx::end() {
-    if (!timing || !recs || *nrec >= cap) return;
-    TimingRec &r = recs[*nrec];
-    if (!r.e0) return;
-    cudaEventRecord(r.e1, s);
+    if (!open) return;
+    open = false;
+    cudaEventRecord(recs[*nrec].e1, s);
     (*nrec)++;
 }
 
@@ -116,7 +118,7 @@ struct spgemm_handle_s {
     spgemm_csr lastA{}, lastB{}, lastC{};
     // launch counting and CUDA-event timing
     long long launches = 0;
-    bool timing = false;
+    int timing = 0;
     std::vector<TimingRec> recs;
     int nrec = 0;
     std::vector<TimingAgg> agg;
@@ -1086,7 +1088,8 @@ int spgemm_compress(spgemm_handle h, const spgemm_csr *M, int32_t *count, uint32
 
 int spgemm_set_timing(spgemm_handle h, int on) {
     if (!h) { set_error("handle is NULL"); return SPGEMM_ERR_ARG; }
-    h->timing = on != 0;
+    if (on < 0 || on > 2) { set_error("bad timing mode %d", on); return SPGEMM_ERR_ARG; }
+    h->timing = on;
     if (h->timing && h->recs.empty()) h->recs.resize(8192, TimingRec{nullptr, 0, nullptr, nullptr});
     return SPGEMM_OK;
 }

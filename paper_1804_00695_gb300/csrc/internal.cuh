@@ -172,7 +172,8 @@ struct Ctx {
     cudaStream_t s = nullptr;
     int nsm = 0;
     long long *launches = nullptr;
-    bool timing = false;
+    int timing = 0;                // 0 off, 1 every kernel, 2 numeric-phase kernels only
+    bool open = false;             // begin() recorded the current pair's first event
     TimingRec *recs = nullptr;     // handle-owned ring of event pairs
     int *nrec = nullptr;
     int cap = 0;

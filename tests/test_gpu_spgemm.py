@@ -218,6 +218,27 @@ def test_medium_rows_every_span(h, ncols, small_cap):
     assert any(l.startswith(want) for l in labels), labels
 
 
+def test_timing_modes(h):
+    """Timing mode 2 brackets only the numeric-phase launches with events,
+    mode 1 every launch; the product is the same either way."""
+    a, p, _ = I.galerkin_problem(10)
+    ref = oracle_product(a, p, np.float64)
+    got = {}
+    try:
+        for mode in (1, 2):
+            h.set_timing(mode)
+            h.reset_timings()
+            c = run(h, a, p)
+            assert_matches(c, ref, "f64")
+            got[mode] = set(h.timings())
+    finally:
+        h.set_timing(False)
+    assert all(l.startswith("numeric") for l in got[2]) and "numeric.narrow" in got[2], got[2]
+    assert got[2] < got[1] and any(l.startswith("symbolic") for l in got[1]), got[1]
+    with pytest.raises(sg.SpgemmError):
+        h.set_timing(3)
+
+
 def test_window_long_and_short_b_rows(h):
     """Rows with more than 4096 outputs over sorted B whose rows are short
     (walked by one thread per a_ik, a few entries per window) or long (more
