@@ -457,7 +457,9 @@ def main():
     a_bytes = 8 * (a.nrows + 1) + 12 * a.nnz
     secondary = None
     if gen is not None:
-        # the other BASELINE workloads, measured on this GPU after the default one
+        # the other workloads (graph product, triangles, chunked, placements,
+        # multigrid families, density, batched), measured on this GPU after the
+        # default one
         del A, P, R, AP, RAP, h1, h2, Ah, Ph, Rh, o
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
