@@ -17,9 +17,10 @@ namespace sg {
 //
 // A warp takes 32 consecutive rows.  When their entries together number at
 // most COMPRESS_STAGE, the warp first copies them into shared memory with
-// coalesced loads (a lane's row alone is a short run of addresses 32 rows
-// apart from its neighbours' in one load instruction), and every lane then
-// reads its row from there; otherwise every lane loads its own row.
+// coalesced asynchronous copies (a lane's row alone is a short run of
+// addresses 32 rows apart from its neighbours' in one load instruction), and
+// every lane then reads its row from there; otherwise every lane loads its
+// own row.
 constexpr int64_t COMPRESS_LONG = 128;   // rows longer than this take a warp each
 constexpr int COMPRESS_STAGE = 1024;     // staged entries per warp
 constexpr int COMPRESS_WPB = 8;
@@ -41,8 +42,15 @@ __global__ void __launch_bounds__(COMPRESS_WPB * 32) k_compress(
     const int64_t wend = rp[rlast];
     const bool staged = wend - wbeg <= COMPRESS_STAGE;
     if (staged) {
+        // asynchronous copies global -> shared (cp.async, 4 bytes a lane and
+        // step: coalesced, no registers held while they are in flight); each
+        // lane waits for its own, the warp barrier then publishes them all
         const int span = (int)(wend - wbeg);
-        for (int x = lane; x < span; x += 32) stage[x] = col[wbeg + x];
+        for (int x = lane; x < span; x += 32) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(stage + x);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(col + wbeg + x) : "memory");
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
     __syncwarp();
     const bool lng = end - beg > COMPRESS_LONG;   // k_compress_long
