@@ -1,5 +1,5 @@
 """The roofline numerator of the bench line: bench.kernel_bytes for the
-Galerkin A*P product against the byte count that follows from the
+Galerkin products A*P and R*(AP) against the byte counts that follow from the
 closed-form sizes (CSR offsets 8 B per row, 4 B column + 8 B value per
 entry; every row of P is reached), evaluated from 1D aggregate counts."""
 import numpy as np
@@ -38,3 +38,39 @@ def test_kernel_bytes_matches_closed_form():
     np.cumsum(lens, out=ap_rp[1:])
     allr = np.ones(a.nrows, dtype=bool)
     assert bench.kernel_bytes(a, p.row_ptr, ap_rp, allr, 8) == _ap_bytes(n)
+
+
+def _rap_bytes(n):
+    """R*(AP): R's offsets and entries (R = P^T: one row per aggregate, nnz(P)
+    entries), every row of AP (each fine point lies in an aggregate, so R
+    reaches all of them), RAP's offsets and entries (tridiagonal in each
+    dimension over the m = ceil(n/3) aggregates: (3m - 2)^3 entries)."""
+    m = -(-n // 3)
+    nnz_p = _aggs_reached(n, 1) ** 3
+    nnz_ap = _aggs_reached(n, 2) ** 3
+    nnz_rap = (3 * m - 2) ** 3
+    return 8 * m ** 3 + 12 * nnz_p + 8 * n ** 3 + 12 * nnz_ap + 8 * m ** 3 + 12 * nnz_rap
+
+
+def test_step_bytes_at_128():
+    """The whole Galerkin step's roofline numerator (the bench line's
+    step_algorithmic_bytes): A*P plus R*(AP) at 128^3."""
+    assert _rap_bytes(128) == 468179492
+    assert _ap_bytes(128) + _rap_bytes(128) == 1612976324
+
+
+def test_kernel_bytes_rap_matches_closed_form():
+    import oracle
+    n = 24
+    a, p, r = I.galerkin_problem(n)
+    ap = oracle.spgemm(a, p)
+    rap = oracle.spgemm(r, I.Csr(a.nrows, p.ncols, ap.row_ptr, ap.col, ap.val))
+    m = -(-n // 3)
+    c = np.arange(m)
+    one_d = np.where((c == 0) | (c == m - 1), 2, 3)     # aggregates c-1, c, c+1 that exist
+    lens = np.einsum("k,j,i->kji", one_d, one_d, one_d).reshape(-1)
+    rap_rp = np.zeros(m ** 3 + 1, dtype=np.int64)
+    np.cumsum(lens, out=rap_rp[1:])
+    assert np.array_equal(rap_rp, rap.row_ptr)        # the closed-form pattern is the product's
+    allr = np.ones(r.nrows, dtype=bool)
+    assert bench.kernel_bytes(r, ap.row_ptr, rap_rp, allr, 8) == _rap_bytes(n)
