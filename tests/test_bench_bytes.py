@@ -74,3 +74,40 @@ def test_kernel_bytes_rap_matches_closed_form():
     assert np.array_equal(rap_rp, rap.row_ptr)        # the closed-form pattern is the product's
     allr = np.ones(r.nrows, dtype=bool)
     assert bench.kernel_bytes(r, ap.row_ptr, rap_rp, allr, 8) == _rap_bytes(n)
+
+
+def test_narrow_rows_rule():
+    """bench.narrow_numeric_rows (which rows' bytes the narrow kernel's
+    roofline counts): every row of both Galerkin products is narrow; a row
+    whose B rows span more than 128 blocks of 32 columns, one with more than
+    32 outputs and one with more than 8192 products are not."""
+    import oracle
+    n = 24
+    a, p, r = I.galerkin_problem(n)
+    ap = oracle.spgemm(a, p)
+    apc = I.Csr(a.nrows, p.ncols, ap.row_ptr, ap.col, ap.val)
+    rap = oracle.spgemm(r, apc)
+    assert bench.narrow_numeric_rows(a, p, ap.row_ptr, bench.row_flops_np(a, p.row_ptr)).all()
+    assert bench.narrow_numeric_rows(r, apc, rap.row_ptr, bench.row_flops_np(r, ap.row_ptr)).all()
+
+    def csr(rows, ncols):
+        rp = np.concatenate([[0], np.cumsum([len(x) for x in rows])]).astype(np.int64)
+        col = np.array([c for x in rows for c in x], dtype=np.int32)
+        return I.Csr(len(rows), ncols, rp, col, np.ones(len(col)))
+
+    ncols = 40000
+    # B: row 0 = column 0; row 1 = column 128*32 - 1 (block 127); row 2 = column 128*32 (block 128);
+    # row 3 = 33 columns; row 4 = 9000 columns in blocks 0..281 (not used alone)
+    b = csr([[0], [128 * 32 - 1], [128 * 32], list(range(100, 133)), list(range(9000))], ncols)
+    a2 = csr([[0, 1], [0, 2], [3], [0]], 5)
+    res = oracle.spgemm(a2, b)
+    got = bench.narrow_numeric_rows(a2, b, res.row_ptr, bench.row_flops_np(a2, b.row_ptr))
+    assert got.tolist() == [True, False, False, True]
+    # products above 8192 alone: three entries of A on a B row of 4000 columns
+    # (blocks 0..124: inside the window, 375 pairs), the output count given as 32
+    b3 = csr([list(range(4000))], ncols)
+    a3 = csr([[0, 0, 0]], 1)     # repeated column only for the count's sake (the oracle is not run)
+    fl = bench.row_flops_np(a3, b3.row_ptr)
+    assert fl.tolist() == [12000]
+    assert not bench.narrow_numeric_rows(a3, b3, np.array([0, 32]), fl)[0]
+    assert bench.narrow_numeric_rows(a3, b3, np.array([0, 32]), np.array([8192]))[0]
